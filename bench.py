@@ -1,0 +1,412 @@
+"""Benchmark of the multi-resolution rendering path (arXiv 1906.04576) on one GB300.
+
+One step = one frame through the whole method (edges -> masks -> work lists ->
+sub-images -> Eq. (1) blend) via mrr_render, with the G-buffer resident in HBM.
+The metric is full-resolution-equivalent Mpixels/s (W*H per frame time), reported
+beside the plain full-resolution kernel (mrr_render_full) on the same frame, the
+RMSE between the two, p50/p99 frame times, the roofline of the dominant kernel
+(the work-list shading kernel), an end-to-end figure through mrr_render_host (host
+G-buffer in, host image out), and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+N > 1 (under torchrun): independent replicas, each rank renders its own seeded frames;
+value = all ranks' pixels / the slowest rank's time ("replicas only": the method has
+no cross-GPU exchange).  L2 is flushed (a 256 MiB write) before every timed step,
+outside the timed events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "full-res-equiv Mpix/s multires vs plain full-res at RMSE<=1e-2; p50/p99 frame ms"
+FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def pct(vals, q):
+    s = sorted(vals)
+    if not s:
+        return float("nan")
+    k = (len(s) - 1) * q
+    lo, hi = math.floor(k), math.ceil(k)
+    return s[lo] + (s[hi] - s[lo]) * (k - lo)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(cfg, n_nonsky, n_sky):
+    """Bytes the shading kernel must move per launch by definition of the effect:
+    per non-sky texel its depth + normal, every sample's gathers and the store; per sky
+    texel its depth and the store."""
+    half = cfg.get("precision", "fp32") == "fp16"
+    nb = 8 if half else 16
+    eff = cfg["effect"]
+    if eff == "ssao":
+        per, store = 4 + nb + cfg["samples"] * 4, (2 if half else 4)
+    elif eff == "ssgi":
+        per, store = 4 + nb + cfg["samples"] * (4 + nb + 8), (8 if half else 16)
+    else:
+        per, store = 4 + (cfg["blocker_samples"] + cfg["pcf_samples"]) * (2 if half else 4), (2 if half else 4)
+    return n_nonsky * (per + store) + n_sky * (4 + store)
+
+
+def workload_config(mrr, sg, name):
+    wl = dict(sg.WORKLOADS[name])
+    W, H = wl["width"], wl["height"]
+    eff = wl["effect"]
+    kw = {}
+    if eff in ("ssao", "ssgi"):
+        kw.update(kernel=sg.hemisphere_kernel(wl["samples"]), radius=wl["radius"], samples=wl["samples"])
+    else:
+        kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
+                  pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED),
+                  blocker_samples=wl["blocker_samples"], pcf_samples=wl["pcf_samples"])
+    if eff == "ssgi":
+        kw["precision"] = "fp16"
+    cfg = mrr.default_config(eff, wl["levels"], W, H, **kw)
+    return wl, cfg
+
+
+def make_frame(sg, wl, seed):
+    return sg.gbuffer(seed, wl["width"], wl["height"], wl["n_boxes"], wl["n_spheres"],
+                      shadow_size=wl.get("shadow_size", 0))
+
+
+def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=60):
+    """The oracle, as it stands, rendering whole frames of the workload on the host cores
+    until about budget_s seconds of CPU work have been spent."""
+    import oracle as orc
+    fr = make_frame(sg, wl, 0)
+    eff = wl["effect"]
+    kw = {}
+    if eff in ("ssao", "ssgi"):
+        kw.update(kernel=sg.hemisphere_kernel(wl["samples"]), samples=wl["samples"], radius=wl["radius"])
+    else:
+        kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
+                  pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED))
+    cfg = orc.default_config(eff, wl["levels"], **kw)
+    orc.render(fr, cfg, "f32")   # warm-up (page-in, thread pool)
+    n, t0 = 0, time.perf_counter()
+    times = []
+    while n < max_frames and (time.perf_counter() - t0) < budget_s or n < 2:
+        t = time.perf_counter()
+        orc.render(fr, cfg, "f32")
+        times.append(time.perf_counter() - t)
+        n += 1
+    total = sum(times)
+    return {"value": round(n * wl["width"] * wl["height"] / total / 1e6, 4), "unit": "Mpix/s",
+            "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{n} whole {wl['width']}x{wl['height']} frames of {name} (float oracle, OpenMP over rows)",
+            "seconds": round(total, 3)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same workload, metric and unit, on host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import scenegen as sg
+    import oracle as orc
+    sg.build()
+    orc.build()
+    wl = dict(sg.WORKLOADS[args.workload])
+    fr = make_frame(sg, wl, 0)
+    eff = wl["effect"]
+    kw = {}
+    if eff in ("ssao", "ssgi"):
+        kw.update(kernel=sg.hemisphere_kernel(wl["samples"]), samples=wl["samples"], radius=wl["radius"])
+    else:
+        kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
+                  pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED))
+    cfg = orc.default_config(eff, wl["levels"], **kw)
+    for _ in range(max(1, min(args.warmup, 3))):
+        orc.render(fr, cfg, "f32")
+    t = time.perf_counter()
+    orc.render(fr, cfg, "f32")
+    est = time.perf_counter() - t
+    budget = 150.0
+    steps = args.steps if args.steps * est <= budget else max(3, int(budget / est))
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        orc.render(fr, cfg, "f32")
+        times.append((time.perf_counter() - t) * 1e3)
+    W, H = wl["width"], wl["height"]
+    total_s = sum(times) / 1e3
+    value = steps * W * H / total_s / 1e6
+    sample = f"{steps} whole {W}x{H} frames (float oracle, OpenMP over rows)"
+    if steps != args.steps:
+        sample += f"; {args.steps} requested, capped at {budget:.0f} s of CPU work"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / steps, 4),
+            "p50_ms": round(pct(times, 0.5), 4), "p99_ms": round(pct(times, 0.99), 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "width": W, "height": H,
+                                            "effect": eff, "levels": wl["levels"]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": orc.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="ssao64_1080p")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_1906_04576_gb300 as mrr
+    import scenegen as sg
+
+    wl, cfg = workload_config(mrr, sg, args.workload)
+    W, H = wl["width"], wl["height"]
+    prec = cfg["precision"]
+    fr = make_frame(sg, wl, rank)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr, prec)
+    out = mrr.alloc_output(ctx, W, H)
+    full = mrr.alloc_output(ctx, W, H)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for s, e in ev:
+            flush.zero_()
+            s.record(stream)
+            fn()
+            e.record(stream)
+        barrier()
+        return [s.elapsed_time(e) for s, e in ev]
+
+    render = lambda: mrr.mrr_render(ctx, dev, out, stream)
+    render_full = lambda: mrr.mrr_render_full(ctx, dev, full, stream)
+    for _ in range(args.warmup):
+        render()
+        render_full()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local].strip() if vis else torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    l0 = mrr.mrr_kernel_launches()
+    t_multi = timed(render, args.steps)
+    launches = mrr.mrr_kernel_launches() - l0
+    t_full = timed(render_full, args.steps)
+
+    # dominant kernel: the work-list shading launch of the same frame, timed alone with
+    # CUDA events on the launching stream
+    edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    levels = mrr.alloc_levels(W, H, cfg["num_levels"], with_label=False)
+    subs = mrr.alloc_subimages(ctx, W, H)
+    mrr.mrr_edges(ctx, dev, edges, stream)
+    mrr.mrr_masks(ctx, edges, levels, stream)
+    kev = []
+    for _ in range(max(10, args.steps // 4)):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        mrr.mrr_shade_levels(ctx, dev, levels, subs, stream)
+        e.record(stream)
+        kev.append((s, e))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    k_ms = statistics.mean(s.elapsed_time(e) for s, e in kev)
+
+    # e2e: host G-buffer in, host image out, through mrr_render_host
+    host = mrr.pin_frame(fr, prec)
+    out_h = torch.empty(tuple(out.shape), dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        mrr.mrr_render_host(ctx, host, out_h, stream)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(10, args.steps // 2)
+    for _ in range(e2e_steps):
+        mrr.mrr_render_host(ctx, host, out_h, stream)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    h2d = host.depth.numel() * 4 + host.normal.numel() * host.normal.element_size()
+    if cfg["effect"] == "ssgi":
+        h2d += host.color.numel() * 2
+    if host.shadow_map is not None:
+        h2d += host.shadow_map.numel() * host.shadow_map.element_size()
+    d2h = out_h.numel() * 4
+
+    # quality gate: RMSE of the multi-resolution image against full-resolution shading
+    mrr.mrr_render(ctx, dev, out, stream)
+    mrr.mrr_render_full(ctx, dev, full, stream)
+    torch.cuda.synchronize()
+    diff = (out - full)[..., :3] if out.dim() == 3 else (out - full)
+    rmse = float(torch.sqrt(torch.mean(diff.double() ** 2)).item())
+
+    counts = levels.counts.cpu().tolist()
+    depth_host = fr.depth
+    n_sky = n_all = 0
+    for i in range(cfg["num_levels"]):
+        if not cfg["enabled"][i] or counts[i] == 0:
+            continue
+        wlst = levels.worklist[i][: counts[i]].cpu().numpy().view("uint32")
+        qy, qx = wlst >> 16, wlst & 0xFFFF
+        o = 0 if i == 0 else (1 << (i - 1))
+        sy = (qy.astype("int64") << i) + o
+        sx = (qx.astype("int64") << i) + o
+        sy[sy > H - 1] = H - 1
+        sx[sx > W - 1] = W - 1
+        n_sky += int((depth_host[sy, sx] >= fr.cam.far).sum())
+        n_all += counts[i]
+    alg = algorithmic_bytes(cfg, n_all - n_sky, n_sky)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (k_ms * 1e-3) / 1e9
+
+    sum_multi = max_over_ranks(sum(t_multi))
+    sum_full = max_over_ranks(sum(t_full))
+    px = world * args.steps * W * H
+    value = px / (sum_multi * 1e-3) / 1e6
+    full_value = px / (sum_full * 1e-3) / 1e6
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sum_multi / args.steps, 5),
+            "p50_ms": round(pct(t_multi, 0.5), 5), "p99_ms": round(pct(t_multi, 0.99), 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-storage/f32" if prec == "fp16" else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "width": W, "height": H, "effect": cfg["effect"],
+                       "samples": cfg.get("samples"), "levels": cfg["num_levels"], "precision": prec,
+                       "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, seed = rank",
+                       "l2": "flushed (256 MiB write) before every timed step, outside the events",
+                       "parallelism": f"replicas x{world}"},
+            "full_res": {"value": round(full_value, 3), "unit": "Mpix/s", "p50_ms": round(pct(t_full, 0.5), 5),
+                         "p99_ms": round(pct(t_full, 0.99), 5)},
+            "speedup_vs_full_res": round(value / full_value, 4),
+            "rmse_vs_full_res": rmse,
+            "shaded_texels": n_all, "shaded_fraction": round(n_all / (W * H), 5),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "shade_levels_kernel", "kernel_ms": round(k_ms, 5),
+                         "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs"},
+            "e2e": {"value": round(world * e2e_steps * W * H / e2e_s / 1e6, 3), "unit": "Mpix/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "api": "mrr_render_host (pinned host buffers, copies and sync inside)"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(sg, wl, args.workload)
+        print(json.dumps(line), flush=True)
+    mrr.mrr_destroy(ctx)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * mrr.h -- C ABI of libmrr, a CUDA (sm_103a) implementation of the multi-resolution
+ * rendering method of Besenthal, Maisch and Ropinski, "Multi-Resolution Rendering for
+ * Computationally Expensive Lighting Effects" (arXiv 1906.04576).
+ *
+ * The method (Sec. 3) has three steps, and the entry points follow them:
+ *   1. masks   (Sec. 3.1, Sec. 4.1): mrr_edges, mrr_masks
+ *   2. render the sub-images at their resolutions where their masks allow
+ *              (Sec. 3.2, Sec. 4.1): mrr_shade_level
+ *   3. blend   (Sec. 3.3, Sec. 4.2, Eq. (1)): mrr_upsample_merge
+ * mrr_render runs all three for one frame; mrr_render_full is the naive
+ * full-resolution rendering the paper compares against (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev, and every pointer inside mrr_gbuffer / mrr_levels, are CUDA
+ *    device pointers owned by the caller; the library never frees them.  Host pointers
+ *    are named *_host or documented as host.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls only enqueue work on it and return; nothing synchronises except mrr_wait
+ *    and mrr_render_host.
+ *  - Arguments are validated before anything is launched: a bad argument returns
+ *    MRR_EINVAL and launches nothing.  A CUDA failure returns MRR_ECUDA.  The text of
+ *    the last failure is available from mrr_last_error(ctx).  No C++ exception
+ *    crosses this ABI.
+ *  - Level i (0 = full resolution) has scale 2^-i; it is the paper's sub-image i+1
+ *    (Sec. 4.2: "c_1 is the full resolution image").  W_i = ceil(W / 2^i),
+ *    H_i = ceil(H / 2^i).  Level texel q covers the full-resolution block
+ *    [2^i q, 2^i (q+1)) and is evaluated at the pixel s_i(q) = min(2^i q + o_i, W-1),
+ *    o_0 = 0, o_i = 2^(i-1).
+ *  - Images are row-major, row 0 at the top, with no padding between rows.
+ *  - A context is used by one host thread at a time, except mrr_submit, mrr_poll and
+ *    mrr_wait, which are thread-safe.
+ */
+#ifndef MRR_H
+#define MRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRR_MAX_LEVELS 4
+#define MRR_MAX_SAMPLES 256     /* hemisphere samples (SSAO, SSGI) */
+#define MRR_MAX_TAPS 128        /* PCSS blocker-search and filter taps, each */
+
+typedef enum {
+  MRR_OK = 0,
+  MRR_EINVAL = 1,        /* invalid argument; nothing was launched */
+  MRR_ENOMEM = 2,        /* device or host allocation failed */
+  MRR_ECUDA = 3,         /* a CUDA call failed; see mrr_last_error */
+  MRR_EBUSY = 4,         /* serving queue full / no free slot */
+  MRR_ETIMEDOUT = 5,     /* mrr_wait timed out, or a bounded device-side wait gave up */
+  MRR_EUNSUPPORTED = 6   /* valid request this build does not support */
+} mrr_status;
+
+/* The three lighting effects of Sec. 2.4 / Sec. 4. */
+typedef enum { MRR_SSAO = 0, MRR_SSM = 1, MRR_SSGI = 2 } mrr_effect;
+
+/* Storage precision.  MRR_FP32: normals float4, shadow map float, sub-images float.
+ * MRR_FP16: normals half4, shadow map half, sub-images half; depth stays float and all
+ * arithmetic stays in float either way.  The SSGI direct-light colour is half4 in both. */
+typedef enum { MRR_FP32 = 0, MRR_FP16 = 1 } mrr_precision;
+
+/* Per-context configuration.  Table 1 of the paper gives sigma2 / weight per effect. */
+typedef struct mrr_config {
+  mrr_effect effect;
+  mrr_precision precision;
+  int num_levels;                 /* L in 1..MRR_MAX_LEVELS; the coarsest level must be enabled */
+  float sigma2[MRR_MAX_LEVELS];   /* Gaussian variance of level i's mask blur, in level texels */
+  float weight[MRR_MAX_LEVELS];   /* w_i of Eq. (1) */
+  int enabled[MRR_MAX_LEVELS];    /* 0 = level not used (Sec. 4: SSGI skips the 1/2 level) */
+  float depth_rel;                /* depth edge: |2nd difference| > depth_rel * depth */
+  float normal_cos;               /* normal edge: n_p . n_q < normal_cos */
+  int force_level0;               /* 1: every pixel at level 0 (a_0 = 1, S_0 = 1) */
+  int samples;                    /* hemisphere samples N (SSAO, SSGI), <= MRR_MAX_SAMPLES */
+  float radius;                   /* sampling radius r (view-space units) */
+  float ao_bias;                  /* SSAO depth bias */
+  float gi_min_dist2;             /* SSGI squared-distance clamp */
+  const float* kernel;            /* host, samples x 4 floats: tangent-frame hemisphere kernel; copied */
+  int blocker_samples;            /* PCSS blocker-search taps, <= MRR_MAX_TAPS */
+  int pcf_samples;                /* PCSS filter taps, <= MRR_MAX_TAPS */
+  const float* blocker_taps;      /* host, blocker_samples x 2 floats in the unit disk; copied */
+  const float* pcf_taps;          /* host, pcf_samples x 2 floats in the unit disk; copied */
+  float light_size;               /* side of the square area light (world units) */
+  float shadow_bias;              /* light-depth bias */
+  int max_width, max_height;      /* largest frame mrr_render / mrr_masks will see (sizes pools) */
+} mrr_config;
+
+/* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the
+ * tangent of half the vertical field of view, near and far.  View space is
+ * (right, up, -forward).  Linear depth is the distance along forward. */
+typedef struct mrr_camera {
+  float eye[3], right[3], up[3], forward[3];
+  float tan_half_fov, near_plane, far_plane;
+} mrr_camera;
+
+/* One frame's G-buffer (Sec. 3.1: "the information available in the G-Buffer"). */
+typedef struct mrr_gbuffer {
+  int width, height;
+  const float* depth;       /* device [H][W] linear view depth; sky pixels hold cam.far_plane */
+  const void* normal;       /* device [H][W] view-space unit normal: float4 (FP32) / half4 (FP16) */
+  const void* color;        /* device [H][W] half4 direct light (SSGI only; else may be NULL) */
+  const void* shadow_map;   /* device [S][S] linear light depth: float (FP32) / half (FP16); SSM only */
+  int shadow_size;          /* S */
+  mrr_camera cam;
+  mrr_camera light;         /* SSM only: the light's camera (square frustum) */
+} mrr_gbuffer;
+
+/* Per-level mask buffers (caller-owned device memory), written by mrr_masks. */
+typedef struct mrr_levels {
+  int num_levels;                       /* must equal the context's num_levels */
+  int width[MRR_MAX_LEVELS];            /* W_i (width[0] = W) */
+  int height[MRR_MAX_LEVELS];           /* H_i */
+  float* alpha[MRR_MAX_LEVELS];         /* [H_i][W_i] blurred mask a_i in [0,1] */
+  uint8_t* stencil[MRR_MAX_LEVELS];     /* [H_i][W_i] S_i in {0,1} */
+  uint32_t* worklist[MRR_MAX_LEVELS];   /* capacity W_i*H_i entries (y << 16) | x, row-major */
+  uint32_t* counts;                     /* [MRR_MAX_LEVELS] entries written per list (device) */
+  uint8_t* label;                       /* [H][W] owning level of each pixel, or NULL */
+} mrr_levels;
+
+typedef struct mrr_ctx mrr_ctx;
+
+/* Level dimensions (pure helper, no context): W_i = ceil(W/2^i), H_i = ceil(H/2^i).
+ * MRR_EINVAL for W or H outside [1, 16384] or level outside [0, MRR_MAX_LEVELS). */
+mrr_status mrr_level_dims(int width, int height, int level, int* level_width, int* level_height);
+
+/* Create a context: validates cfg, copies its sample tables (hemisphere kernel,
+ * disk taps) and computes the Gaussian weights of each level (Sec. 3.1, Table 1):
+ * radius R_i = ceil(3 sigma_i), weights exp(-k^2 / (2 sigma_i^2)) normalised over
+ * [-R_i, R_i] in double and rounded to float.  Allocates the device pools that
+ * mrr_render uses for frames up to max_width x max_height on the current device.
+ * *out receives the context (NULL on failure). */
+mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out);
+
+/* Free the context and its pools.  The caller must ensure no work using them is
+ * still in flight (synchronise the streams it used).  NULL is ignored. */
+void mrr_destroy(mrr_ctx* ctx);
+
+/* Sec. 3.1: the edge image.  edges_dev [H][W] gets 1 at a non-sky pixel that
+ *  (a) has a sky 4-neighbour, or (b) whose second difference of depth along x or y
+ *  exceeds depth_rel * depth (an axis counts only with both neighbours in the image),
+ *  or (c) whose normal's dot product with an in-image non-sky 4-neighbour's is below
+ *  normal_cos (first derivative of the normals), or (d) for MRR_SSM, whose one-sample
+ *  hard shadow differs from an in-image non-sky 4-neighbour's; else 0.  Sky pixels
+ *  are 0.  Edge maps are combined by maximum (Sec. 3.1). */
+mrr_status mrr_edges(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* edges_dev, void* stream);
+
+/* Sec. 3.1 + Sec. 4.1: the masks of every level from the edge image [H][W] with
+ * W = lv->width[0], H = lv->height[0] (at most the context's max size).  For each
+ * enabled level i below the coarsest: D_i = maximum of the edge image over each
+ * texel's block, a_i = Gaussian blur of D_i (sigma_i^2, horizontal then vertical, zero
+ * outside the level), S_i = [a_i > 0] OR-ed with every set texel of the previous
+ * enabled finer level inside the block (inclusive nesting, Fig. 2/3).  The coarsest
+ * level has a = 1, S = 1; disabled levels a = 0, S = 0.  Then the work lists: the
+ * texels with S_i = 1 in row-major order, counts[i] = their number (left on the
+ * device), and label[p] = the finest enabled level whose stencil covers p. */
+mrr_status mrr_masks(mrr_ctx* ctx, const uint8_t* edges_dev, const mrr_levels* lv, void* stream);
+
+/* Sec. 3.2 / Sec. 4.1: render sub-image `level` only where its mask allows: for every
+ * texel q in lv->worklist[level] (count lv->counts[level], read on the device),
+ * c_level_dev[q] = the context's effect evaluated at full-resolution pixel s_i(q)
+ * from the full-resolution G-buffer.  Other texels are not written.  c_level_dev is
+ * [H_i][W_i] of float (FP32) / half (FP16), 4 per texel (rgb + 0) for MRR_SSGI. */
+mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const mrr_levels* lv,
+                           void* c_level_dev, void* stream);
+
+/* mrr_shade_level for every enabled level in ONE launch (the launch mrr_render makes):
+ * a persistent grid strides over the concatenated work lists, whose lengths it reads
+ * from lv->counts on the device.  c_levels_dev[i] as in mrr_shade_level (NULL for
+ * disabled levels). */
+mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv, void* const* c_levels_dev,
+                            void* stream);
+
+/* Sec. 4.2 and Eq. (1): upsample every enabled sub-image to full resolution and blend
+ * them from the coarsest to the finest: a_i is interpolated bilinearly, c_i bilinearly
+ * over rendered taps only (weights renormalised), alpha = min(w_i a_i, 1) and
+ * c' = c_i alpha + c' (1 - alpha), starting from c' = the coarsest sub-image.
+ * c_levels_dev[i] as in mrr_shade_level (NULL for disabled levels).  out_dev is
+ * [H][W] float, or [H][W] float4 (rgb + 0) for MRR_SSGI. */
+mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,
+                              void* stream);
+
+/* The whole method for one frame on one stream: edges, masks, work lists, all
+ * sub-images, blend -- using the context's pools for every intermediate.  Frames up to
+ * the context's max size.  out_dev as in mrr_upsample_merge. */
+mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream);
+
+/* Naive full-resolution rendering (the paper's comparison, Sec. 5): the effect at
+ * every pixel.  out_dev as in mrr_upsample_merge. */
+mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream);
+
+/* mrr_render from host memory: copies the G-buffer planes named by g (host pointers,
+ * pinned for full speed) into the context's device pools on `stream`, renders, copies
+ * the result to out_host and synchronises the stream before returning. */
+mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* g_host, float* out_host, void* stream);
+
+/* Number of kernels this library has launched in this process (all contexts), for
+ * accounting of GPU work in benchmarks. */
+uint64_t mrr_kernel_launches(void);
+
+/* Text of the last failure on this context ("" if none); valid until the next call. */
+const char* mrr_last_error(mrr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRR_H */

@@ -1,0 +1,422 @@
+"""Python binding of libmrr, the CUDA (sm_103a) multi-resolution rendering library.
+
+Argument marshalling only: every stage runs in libmrr's kernels.  PyTorch supplies
+device memory and streams.  The functions carry the C names of include/mrr.h:
+
+    mrr_create(cfg) -> Context          mrr_destroy(ctx)
+    mrr_edges(ctx, frame, edges)        mrr_masks(ctx, edges, levels)
+    mrr_shade_level(ctx, level, frame, levels, c)
+    mrr_shade_levels(ctx, frame, levels, c_list)
+    mrr_upsample_merge(ctx, levels, c_list, out)
+    mrr_render(ctx, frame, out)         mrr_render_full(ctx, frame, out)
+    mrr_render_host(ctx, host_frame, out_host)
+    mrr_level_dims(W, H, level)         mrr_last_error(ctx)
+    mrr_kernel_launches()
+
+Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
+``python -m paper_1906_04576_gb300._build``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmrr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmrr.so not built at {LIB_PATH}; run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MRR_OK, MRR_EINVAL, MRR_ENOMEM, MRR_ECUDA, MRR_EBUSY, MRR_ETIMEDOUT, MRR_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["MRR_OK", "MRR_EINVAL", "MRR_ENOMEM", "MRR_ECUDA", "MRR_EBUSY", "MRR_ETIMEDOUT",
+                "MRR_EUNSUPPORTED"]
+MRR_SSAO, MRR_SSM, MRR_SSGI = 0, 1, 2
+MRR_FP32, MRR_FP16 = 0, 1
+MAX_LEVELS, MAX_SAMPLES, MAX_TAPS = 4, 256, 128
+EFFECTS = {"ssao": MRR_SSAO, "ssm": MRR_SSM, "ssgi": MRR_SSGI}
+
+F4 = ctypes.c_float * 4
+I4 = ctypes.c_int * 4
+
+
+class mrr_config(ctypes.Structure):
+    _fields_ = [
+        ("effect", ctypes.c_int), ("precision", ctypes.c_int), ("num_levels", ctypes.c_int),
+        ("sigma2", F4), ("weight", F4), ("enabled", I4),
+        ("depth_rel", ctypes.c_float), ("normal_cos", ctypes.c_float), ("force_level0", ctypes.c_int),
+        ("samples", ctypes.c_int), ("radius", ctypes.c_float), ("ao_bias", ctypes.c_float),
+        ("gi_min_dist2", ctypes.c_float), ("kernel", ctypes.POINTER(ctypes.c_float)),
+        ("blocker_samples", ctypes.c_int), ("pcf_samples", ctypes.c_int),
+        ("blocker_taps", ctypes.POINTER(ctypes.c_float)), ("pcf_taps", ctypes.POINTER(ctypes.c_float)),
+        ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float),
+        ("max_width", ctypes.c_int), ("max_height", ctypes.c_int),
+    ]
+
+
+class mrr_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("forward", ctypes.c_float * 3), ("tan_half_fov", ctypes.c_float),
+                ("near_plane", ctypes.c_float), ("far_plane", ctypes.c_float)]
+
+
+class mrr_gbuffer(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("depth", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p), ("color", ctypes.c_void_p), ("shadow_map", ctypes.c_void_p),
+                ("shadow_size", ctypes.c_int), ("cam", mrr_camera), ("light", mrr_camera)]
+
+
+class mrr_levels(ctypes.Structure):
+    _fields_ = [("num_levels", ctypes.c_int), ("width", I4), ("height", I4),
+                ("alpha", ctypes.c_void_p * 4), ("stencil", ctypes.c_void_p * 4),
+                ("worklist", ctypes.c_void_p * 4), ("counts", ctypes.c_void_p), ("label", ctypes.c_void_p)]
+
+
+_vp = ctypes.c_void_p
+_lib.mrr_level_dims.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]
+_lib.mrr_create.argtypes = [ctypes.POINTER(mrr_config), ctypes.POINTER(_vp)]
+_lib.mrr_destroy.argtypes = [_vp]
+_lib.mrr_destroy.restype = None
+_lib.mrr_last_error.argtypes = [_vp]
+_lib.mrr_last_error.restype = ctypes.c_char_p
+_lib.mrr_edges.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+_lib.mrr_masks.argtypes = [_vp, _vp, ctypes.POINTER(mrr_levels), _vp]
+_lib.mrr_shade_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp]
+_lib.mrr_upsample_merge.argtypes = [_vp, ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp, _vp]
+_lib.mrr_shade_levels.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp]
+_lib.mrr_kernel_launches.argtypes = []
+_lib.mrr_kernel_launches.restype = ctypes.c_uint64
+_lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+_lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+_lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+for _fn in ("mrr_level_dims", "mrr_create", "mrr_edges", "mrr_masks", "mrr_shade_level", "mrr_shade_levels",
+            "mrr_upsample_merge",
+            "mrr_render", "mrr_render_full", "mrr_render_host"):
+    getattr(_lib, _fn).restype = ctypes.c_int
+
+
+class MrrError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+@dataclass
+class Context:
+    handle: int
+    config: dict
+    _keep: list = field(default_factory=list)
+
+    @property
+    def channels(self) -> int:
+        return 4 if self.config["effect"] == "ssgi" else 1
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.mrr_destroy(h)
+            except Exception:
+                pass
+            self.handle = 0
+
+
+def _check(ctx, st):
+    if st != MRR_OK:
+        msg = _lib.mrr_last_error(ctx.handle if ctx is not None else None)
+        raise MrrError(st, msg.decode() if msg else "")
+
+
+def mrr_level_dims(width: int, height: int, level: int):
+    wi, hi = ctypes.c_int(), ctypes.c_int()
+    st = _lib.mrr_level_dims(width, height, level, ctypes.byref(wi), ctypes.byref(hi))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_level_dims")
+    return wi.value, hi.value
+
+
+def make_config(cfg: dict) -> tuple[mrr_config, list]:
+    """mrr_config from a dict (keys as in the C struct; effect as 'ssao'/'ssm'/'ssgi')."""
+    import numpy as np
+    c = mrr_config()
+    keep = []
+    c.effect = EFFECTS[cfg["effect"]]
+    c.precision = MRR_FP16 if cfg.get("precision", "fp32") == "fp16" else MRR_FP32
+    c.num_levels = cfg["num_levels"]
+    for i in range(4):
+        c.sigma2[i] = cfg["sigma2"][i]
+        c.weight[i] = cfg["weight"][i]
+        c.enabled[i] = int(cfg["enabled"][i])
+    c.depth_rel = cfg.get("depth_rel", 0.05)
+    c.normal_cos = cfg.get("normal_cos", 0.9)
+    c.force_level0 = int(cfg.get("force_level0", 0))
+
+    def table(name, n_key, cols):
+        arr = cfg.get(name)
+        if arr is None:
+            return None, 0
+        a = np.ascontiguousarray(arr, dtype=np.float32).reshape(-1, cols)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.shape[0]
+
+    c.kernel, n = table("kernel", "samples", 4)
+    c.samples = n
+    c.radius = cfg.get("radius", 0.5)
+    c.ao_bias = cfg.get("ao_bias", 0.0125)
+    c.gi_min_dist2 = cfg.get("gi_min_dist2", 0.01)
+    c.blocker_taps, c.blocker_samples = table("blocker_taps", "blocker_samples", 2)
+    c.pcf_taps, c.pcf_samples = table("pcf_taps", "pcf_samples", 2)
+    c.light_size = cfg.get("light_size", 0.5)
+    c.shadow_bias = cfg.get("shadow_bias", 0.03)
+    c.max_width = cfg["max_width"]
+    c.max_height = cfg["max_height"]
+    return c, keep
+
+
+def mrr_create(cfg: dict) -> Context:
+    c, keep = make_config(cfg)
+    h = _vp()
+    st = _lib.mrr_create(ctypes.byref(c), ctypes.byref(h))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_create")
+    return Context(h.value, dict(cfg))
+
+
+def mrr_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        _lib.mrr_destroy(ctx.handle)
+        ctx.handle = 0
+
+
+def mrr_last_error(ctx: Context) -> str:
+    return _lib.mrr_last_error(ctx.handle).decode()
+
+
+def _camera(cam) -> mrr_camera:
+    m = mrr_camera()
+    for k in range(3):
+        m.eye[k], m.right[k], m.up[k], m.forward[k] = cam.eye[k], cam.right[k], cam.up[k], cam.forward[k]
+    m.tan_half_fov, m.near_plane, m.far_plane = cam.tan_half_fov, cam.near, cam.far
+    return m
+
+
+@dataclass
+class DeviceFrame:
+    """A G-buffer resident on the device (torch tensors) plus its cameras."""
+    width: int
+    height: int
+    depth: torch.Tensor                   # float32 [H][W]
+    normal: torch.Tensor                  # float32 [H][W][4] or float16 [H][W][4]
+    cam: object
+    color: torch.Tensor | None = None     # float16 [H][W][4]
+    shadow_map: torch.Tensor | None = None  # float32 / float16 [S][S]
+    light: object = None
+
+    def struct(self) -> mrr_gbuffer:
+        g = mrr_gbuffer()
+        g.width, g.height = self.width, self.height
+        g.depth = _ptr(self.depth)
+        g.normal = _ptr(self.normal)
+        g.color = _ptr(self.color)
+        g.shadow_map = _ptr(self.shadow_map)
+        g.shadow_size = 0 if self.shadow_map is None else self.shadow_map.shape[0]
+        g.cam = _camera(self.cam)
+        if self.light is not None:
+            g.light = _camera(self.light)
+        return g
+
+
+def upload_frame(frame, precision: str = "fp32", device="cuda") -> DeviceFrame:
+    """Copy a scenegen.Frame to the device in the storage format of `precision`."""
+    ndt = torch.float16 if precision == "fp16" else torch.float32
+    depth = torch.from_numpy(frame.depth).to(device)
+    normal = torch.from_numpy(frame.normal).to(device=device, dtype=ndt)
+    color = torch.from_numpy(frame.color).to(device=device, dtype=torch.float16)
+    sm = None
+    if frame.shadow_map is not None:
+        sm = torch.from_numpy(frame.shadow_map).to(device=device, dtype=ndt)
+    return DeviceFrame(frame.width, frame.height, depth, normal.contiguous(), frame.cam, color.contiguous(), sm,
+                       frame.light)
+
+
+@dataclass
+class Levels:
+    """Caller-owned per-level mask buffers (mrr_levels) as torch tensors."""
+    num_levels: int
+    dims: list
+    alpha: list
+    stencil: list
+    worklist: list
+    counts: torch.Tensor
+    label: torch.Tensor | None
+
+    def struct(self) -> mrr_levels:
+        lv = mrr_levels()
+        lv.num_levels = self.num_levels
+        for i in range(self.num_levels):
+            lv.width[i], lv.height[i] = self.dims[i]
+            lv.alpha[i] = _ptr(self.alpha[i])
+            lv.stencil[i] = _ptr(self.stencil[i])
+            lv.worklist[i] = _ptr(self.worklist[i])
+        lv.counts = _ptr(self.counts)
+        lv.label = _ptr(self.label)
+        return lv
+
+
+def alloc_levels(width: int, height: int, num_levels: int, with_label: bool = True, device="cuda") -> Levels:
+    dims = [mrr_level_dims(width, height, i) for i in range(num_levels)]
+    alpha = [torch.empty((h, w), dtype=torch.float32, device=device) for (w, h) in dims]
+    stencil = [torch.empty((h, w), dtype=torch.uint8, device=device) for (w, h) in dims]
+    worklist = [torch.empty((h * w,), dtype=torch.int32, device=device) for (w, h) in dims]
+    counts = torch.zeros((MAX_LEVELS,), dtype=torch.int32, device=device)
+    label = torch.empty((height, width), dtype=torch.uint8, device=device) if with_label else None
+    return Levels(num_levels, dims, alpha, stencil, worklist, counts, label)
+
+
+def alloc_subimages(ctx: Context, width: int, height: int, device="cuda") -> list:
+    dt = torch.float16 if ctx.config.get("precision", "fp32") == "fp16" else torch.float32
+    out = []
+    for i in range(ctx.config["num_levels"]):
+        w, h = mrr_level_dims(width, height, i)
+        shape = (h, w, 4) if ctx.channels == 4 else (h, w)
+        out.append(torch.full(shape, float("nan"), dtype=dt, device=device) if ctx.config["enabled"][i] else None)
+    return out
+
+
+def alloc_output(ctx: Context, width: int, height: int, device="cuda") -> torch.Tensor:
+    shape = (height, width, 4) if ctx.channels == 4 else (height, width)
+    return torch.empty(shape, dtype=torch.float32, device=device)
+
+
+def mrr_edges(ctx: Context, frame: DeviceFrame, edges: torch.Tensor, stream=None) -> None:
+    g = frame.struct()
+    _check(ctx, _lib.mrr_edges(ctx.handle, ctypes.byref(g), _ptr(edges), _stream(stream)))
+
+
+def mrr_masks(ctx: Context, edges: torch.Tensor, levels: Levels, stream=None) -> None:
+    lv = levels.struct()
+    _check(ctx, _lib.mrr_masks(ctx.handle, _ptr(edges), ctypes.byref(lv), _stream(stream)))
+
+
+def mrr_shade_level(ctx: Context, level: int, frame: DeviceFrame, levels: Levels, c: torch.Tensor,
+                    stream=None) -> None:
+    g, lv = frame.struct(), levels.struct()
+    _check(ctx, _lib.mrr_shade_level(ctx.handle, level, ctypes.byref(g), ctypes.byref(lv), _ptr(c),
+                                     _stream(stream)))
+
+
+def mrr_shade_levels(ctx: Context, frame: DeviceFrame, levels: Levels, c_list: list, stream=None) -> None:
+    g, lv = frame.struct(), levels.struct()
+    arr = (_vp * MAX_LEVELS)(*[(_ptr(c) if c is not None else None) for c in c_list])
+    _check(ctx, _lib.mrr_shade_levels(ctx.handle, ctypes.byref(g), ctypes.byref(lv), arr, _stream(stream)))
+
+
+def mrr_kernel_launches() -> int:
+    return int(_lib.mrr_kernel_launches())
+
+
+def mrr_upsample_merge(ctx: Context, levels: Levels, c_list: list, out: torch.Tensor, stream=None) -> None:
+    lv = levels.struct()
+    arr = (_vp * MAX_LEVELS)(*[(_ptr(c) if c is not None else None) for c in c_list])
+    _check(ctx, _lib.mrr_upsample_merge(ctx.handle, ctypes.byref(lv), arr, _ptr(out), _stream(stream)))
+
+
+def mrr_render(ctx: Context, frame: DeviceFrame, out: torch.Tensor, stream=None) -> None:
+    g = frame.struct()
+    _check(ctx, _lib.mrr_render(ctx.handle, ctypes.byref(g), _ptr(out), _stream(stream)))
+
+
+def mrr_render_full(ctx: Context, frame: DeviceFrame, out: torch.Tensor, stream=None) -> None:
+    g = frame.struct()
+    _check(ctx, _lib.mrr_render_full(ctx.handle, ctypes.byref(g), _ptr(out), _stream(stream)))
+
+
+@dataclass
+class HostFrame:
+    """A G-buffer in (pinned) host memory, for mrr_render_host."""
+    width: int
+    height: int
+    depth: torch.Tensor
+    normal: torch.Tensor
+    cam: object
+    color: torch.Tensor | None = None
+    shadow_map: torch.Tensor | None = None
+    light: object = None
+
+    def struct(self) -> mrr_gbuffer:
+        g = mrr_gbuffer()
+        g.width, g.height = self.width, self.height
+        g.depth = self.depth.data_ptr()
+        g.normal = self.normal.data_ptr()
+        g.color = None if self.color is None else self.color.data_ptr()
+        g.shadow_map = None if self.shadow_map is None else self.shadow_map.data_ptr()
+        g.shadow_size = 0 if self.shadow_map is None else self.shadow_map.shape[0]
+        g.cam = _camera(self.cam)
+        if self.light is not None:
+            g.light = _camera(self.light)
+        return g
+
+
+def pin_frame(frame, precision: str = "fp32") -> HostFrame:
+    ndt = torch.float16 if precision == "fp16" else torch.float32
+    pin = lambda a, dt=None: (torch.from_numpy(a) if dt is None else torch.from_numpy(a).to(dt)).contiguous().pin_memory()
+    sm = None if frame.shadow_map is None else pin(frame.shadow_map, ndt)
+    return HostFrame(frame.width, frame.height, pin(frame.depth), pin(frame.normal, ndt), frame.cam,
+                     pin(frame.color, torch.float16), sm, frame.light)
+
+
+def mrr_render_host(ctx: Context, frame: HostFrame, out_host: torch.Tensor, stream=None) -> None:
+    g = frame.struct()
+    _check(ctx, _lib.mrr_render_host(ctx.handle, ctypes.byref(g), out_host.data_ptr(), _stream(stream)))
+
+
+# Table 1 of the paper: (sigma_i^2, w_i) of sub-images 1..4 (full, 1/2, 1/4, 1/8 resolution)
+# per effect; SSGI does not use the second sub-image (Sec. 4).
+TABLE1 = {
+    "ssao": [(0.924, 100.0), (1.848, 50.0), (3.696, 20.0), (0.0, 1.0)],
+    "ssm": [(0.924, 1000.0), (1.848, 1000.0), (3.696, 1000.0), (0.0, 1.0)],
+    "ssgi": [(0.924, 1000.0), None, (0.924, 100.0), (0.0, 1.0)],
+}
+
+
+def default_config(effect: str, num_levels: int, max_width: int, max_height: int, **kw) -> dict:
+    """A configuration dict with Table 1's variances and weights (with three levels the
+    coarsest row is used for the third) and this library's defaults for the rest."""
+    rows = TABLE1[effect]
+    if num_levels == 3:
+        rows = [rows[0], rows[1], rows[3]]
+    sigma2, weight, enabled = [0.0] * 4, [0.0] * 4, [0] * 4
+    for i, row in enumerate(rows[:num_levels]):
+        if row is not None:
+            sigma2[i], weight[i] = row
+            enabled[i] = 1
+    cfg = dict(effect=effect, precision="fp32", num_levels=num_levels, sigma2=sigma2, weight=weight,
+               enabled=enabled, depth_rel=0.05, normal_cos=0.9, force_level0=0, radius=0.5, ao_bias=0.0125,
+               gi_min_dist2=0.01, light_size=0.5, shadow_bias=0.03, max_width=max_width, max_height=max_height)
+    cfg.update(kw)
+    return cfg

@@ -1,0 +1,626 @@
+// api.cu -- the C ABI of libmrr (include/mrr.h): argument validation, the host-side
+// constants of each stage and the launches.  No exception crosses the ABI; every
+// failure is a status code plus a message kept on the context.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mrr_internal.cuh"
+
+using namespace mrr;
+
+struct mrr_ctx {
+  mrr_config cfg;
+  float4 kernel[MRR_MAX_SAMPLES];
+  float2 btaps[MRR_MAX_TAPS], ptaps[MRR_MAX_TAPS];
+  float gauss[MRR_MAX_LEVELS][16];
+  int R[MRR_MAX_LEVELS];
+  int shade_grid = 0;
+  std::string err;
+  // pools of mrr_render / mrr_masks, sized for max_width x max_height
+  int pool_W = 0, pool_H = 0;
+  uint8_t* edges = nullptr;
+  float* alpha[MRR_MAX_LEVELS] = {};
+  uint8_t* stencil[MRR_MAX_LEVELS] = {};
+  uint32_t* worklist[MRR_MAX_LEVELS] = {};
+  void* cbuf[MRR_MAX_LEVELS] = {};
+  uint32_t* counts = nullptr;
+  uint32_t* chunk_counts = nullptr;
+  size_t chunk_cap = 0;
+  // pools of mrr_render_host
+  float* h_depth = nullptr;
+  void* h_normal = nullptr;
+  void* h_color = nullptr;
+  void* h_smap = nullptr;
+  size_t h_smap_bytes = 0;
+  float* h_out = nullptr;
+};
+
+namespace {
+
+constexpr int MAX_DIM = 16384;
+
+mrr_status fail(mrr_ctx* ctx, mrr_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+#define MRR_CUDA(ctx, call)                                                                           \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail((ctx), MRR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+inline int level_dim(int n, int i) { return (n + (1 << i) - 1) >> i; }
+inline int channels(const mrr_config& c) { return c.effect == MRR_SSGI ? 4 : 1; }
+inline size_t cbytes(const mrr_config& c) {
+  return (size_t)channels(c) * (c.precision == MRR_FP16 ? 2 : 4);
+}
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Pinhole constants in double from the float camera, rounded once to float:
+// t_x = tan_half * (W / H); ax = 2 t_x / W, bx = t_x, kx = W / (2 t_x);
+// ay = 2 tan_half / H, by = tan_half, ky = H / (2 tan_half).
+ViewC make_view(int W, int H, const mrr_camera& c) {
+  const double th = c.tan_half_fov;
+  const double tx = th * ((double)W / (double)H);
+  ViewC v;
+  v.W = W;
+  v.H = H;
+  v.ax = (float)(2.0 * tx / (double)W);
+  v.bx = (float)tx;
+  v.kx = (float)((double)W / (2.0 * tx));
+  v.ay = (float)(2.0 * th / (double)H);
+  v.by = (float)th;
+  v.ky = (float)((double)H / (2.0 * th));
+  v.nearp = c.near_plane;
+  v.farp = c.far_plane;
+  return v;
+}
+
+LightC make_light(const mrr_gbuffer& g) {
+  LightC L;
+  for (int k = 0; k < 3; ++k) {
+    L.ce[k] = g.cam.eye[k];
+    L.cr[k] = g.cam.right[k];
+    L.cu[k] = g.cam.up[k];
+    L.cf[k] = g.cam.forward[k];
+    L.le[k] = g.light.eye[k];
+    L.lr[k] = g.light.right[k];
+    L.lu[k] = g.light.up[k];
+    L.lf[k] = g.light.forward[k];
+  }
+  L.tl = g.light.tan_half_fov;
+  L.kl = (float)((double)g.shadow_size / (2.0 * (double)g.light.tan_half_fov));
+  L.nearp = g.light.near_plane;
+  L.farp = g.light.far_plane;
+  L.S = g.shadow_size;
+  return L;
+}
+
+// Truncated Gaussian of Sec. 3.1: R = ceil(3 sigma), weights exp(-k^2 / (2 sigma^2))
+// normalised over [-R, R] in double (ascending k), rounded once to float.
+int gauss_weights(double sigma2, float* g) {
+  const int R = (int)std::ceil(3.0 * std::sqrt(sigma2));
+  double e[16];
+  double sum = 0.0;
+  for (int k = -R; k <= R; ++k) {
+    e[k + R] = std::exp(-(double)(k * k) / (2.0 * sigma2));
+    sum += e[k + R];
+  }
+  for (int k = 0; k <= 2 * R; ++k) g[k] = (float)(e[k] / sum);
+  return R;
+}
+
+mrr_status check_gbuffer(mrr_ctx* ctx, const mrr_gbuffer* g, bool need_device_align = true) {
+  if (!g) return fail(ctx, MRR_EINVAL, "gbuffer is NULL");
+  if (g->width < 1 || g->height < 1 || g->width > MAX_DIM || g->height > MAX_DIM)
+    return fail(ctx, MRR_EINVAL, "frame size %dx%d outside [1, %d]", g->width, g->height, MAX_DIM);
+  if (!g->depth || !g->normal) return fail(ctx, MRR_EINVAL, "depth and normal planes are required");
+  if (need_device_align && !aligned(g->normal, ctx->cfg.precision == MRR_FP16 ? 8 : 16))
+    return fail(ctx, MRR_EINVAL, "normal plane is not aligned to its element size");
+  if (!(g->cam.tan_half_fov > 0.f) || !(g->cam.near_plane > 0.f) || !(g->cam.far_plane > g->cam.near_plane))
+    return fail(ctx, MRR_EINVAL, "camera needs tan_half_fov > 0 and 0 < near < far");
+  if (ctx->cfg.effect == MRR_SSGI) {
+    if (!g->color) return fail(ctx, MRR_EINVAL, "SSGI needs the direct-light colour plane");
+    if (need_device_align && !aligned(g->color, 8)) return fail(ctx, MRR_EINVAL, "colour plane not 8-byte aligned");
+  }
+  if (ctx->cfg.effect == MRR_SSM) {
+    if (!g->shadow_map || g->shadow_size < 1 || g->shadow_size > MAX_DIM)
+      return fail(ctx, MRR_EINVAL, "SSM needs a shadow map of side 1..%d", MAX_DIM);
+    if (!(g->light.tan_half_fov > 0.f) || !(g->light.near_plane > 0.f))
+      return fail(ctx, MRR_EINVAL, "light camera needs tan_half_fov > 0 and near > 0");
+  }
+  return MRR_OK;
+}
+
+ShadeParams make_shade_params(const mrr_ctx* ctx, const mrr_gbuffer& g) {
+  ShadeParams p;
+  const mrr_config& c = ctx->cfg;
+  p.effect = c.effect;
+  p.v = make_view(g.width, g.height, g.cam);
+  if (c.effect == MRR_SSM) p.L = make_light(g);
+  else std::memset(&p.L, 0, sizeof p.L);
+  p.samples = c.samples;
+  p.radius = c.radius;
+  p.ao_bias = c.ao_bias;
+  p.gi_min_dist2 = c.gi_min_dist2;
+  p.light_half = c.light_size * 0.5f;
+  p.shadow_bias = c.shadow_bias;
+  p.nb = c.blocker_samples;
+  p.np = c.pcf_samples;
+  std::memcpy(p.kernel, ctx->kernel, sizeof p.kernel);
+  std::memcpy(p.btaps, ctx->btaps, sizeof p.btaps);
+  std::memcpy(p.ptaps, ctx->ptaps, sizeof p.ptaps);
+  return p;
+}
+
+FrameIn make_frame_in(const mrr_gbuffer& g) {
+  FrameIn in;
+  in.depth = g.depth;
+  in.normal = g.normal;
+  in.color = reinterpret_cast<const half4*>(g.color);
+  in.smap = g.shadow_map;
+  return in;
+}
+
+mrr_status check_levels(mrr_ctx* ctx, const mrr_levels* lv, bool need_lists) {
+  if (!lv) return fail(ctx, MRR_EINVAL, "levels is NULL");
+  const mrr_config& c = ctx->cfg;
+  if (lv->num_levels != c.num_levels)
+    return fail(ctx, MRR_EINVAL, "levels->num_levels %d != context num_levels %d", lv->num_levels, c.num_levels);
+  const int W = lv->width[0], H = lv->height[0];
+  if (W < 1 || H < 1 || W > MAX_DIM || H > MAX_DIM) return fail(ctx, MRR_EINVAL, "bad level-0 size %dx%d", W, H);
+  for (int i = 0; i < c.num_levels; ++i) {
+    if (lv->width[i] != level_dim(W, i) || lv->height[i] != level_dim(H, i))
+      return fail(ctx, MRR_EINVAL, "level %d is %dx%d, expected %dx%d", i, lv->width[i], lv->height[i],
+                  level_dim(W, i), level_dim(H, i));
+    if (c.enabled[i] && (!lv->alpha[i] || !lv->stencil[i] || (need_lists && !lv->worklist[i])))
+      return fail(ctx, MRR_EINVAL, "level %d buffers missing", i);
+  }
+  if (!lv->counts) return fail(ctx, MRR_EINVAL, "levels->counts is NULL");
+  return MRR_OK;
+}
+
+mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cudaStream_t s) {
+  const mrr_config& c = ctx->cfg;
+  const int W = lv->width[0], H = lv->height[0];
+  int prev = -1;
+  for (int i = 0; i < c.num_levels; ++i) {
+    MaskLevel m;
+    std::memset(&m, 0, sizeof m);
+    m.level = i;
+    m.Wi = lv->width[i];
+    m.Hi = lv->height[i];
+    if (!c.enabled[i]) {
+      if (!lv->alpha[i] || !lv->stencil[i]) continue;  // nothing to clear
+      m.mode = 2;
+    } else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) {
+      m.mode = 1;
+    } else {
+      m.mode = 0;
+      m.R = ctx->R[i];
+      std::memcpy(m.g, ctx->gauss[i], sizeof m.g);
+      if (prev >= 0) {
+        m.prev = lv->stencil[prev];
+        m.prev_W = lv->width[prev];
+        m.prev_H = lv->height[prev];
+        m.prev_shift = i - prev;
+      }
+    }
+    m.alpha = lv->alpha[i];
+    m.stencil = lv->stencil[i];
+    MRR_CUDA(ctx, launch_mask_level(m, E, W, H, s));
+    if (c.enabled[i]) prev = i;
+  }
+  // work lists of every enabled level in one two-pass compaction
+  CompactParams cp;
+  std::memset(&cp, 0, sizeof cp);
+  int nchunks = 0;
+  for (int i = 0; i < c.num_levels; ++i) {
+    if (!c.enabled[i]) {
+      cp.zero_mask |= 1 << i;
+      continue;
+    }
+    const int l = cp.nlev++;
+    cp.level_of[l] = i;
+    cp.chunk_begin[l] = nchunks;
+    cp.Wi[l] = lv->width[i];
+    cp.Hi[l] = lv->height[i];
+    cp.stencil[l] = lv->stencil[i];
+    cp.list[l] = lv->worklist[i];
+    nchunks += (int)(((size_t)lv->width[i] * lv->height[i] + COMPACT_CHUNK - 1) / COMPACT_CHUNK);
+  }
+  for (int i = c.num_levels; i < MRR_MAX_LEVELS; ++i) cp.zero_mask |= 1 << i;
+  cp.chunk_begin[cp.nlev] = nchunks;
+  if ((size_t)nchunks > ctx->chunk_cap)
+    return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size", W, H);
+  cp.chunk_counts = ctx->chunk_counts;
+  cp.counts = lv->counts;
+  MRR_CUDA(ctx, launch_compact(cp, s));
+  if (lv->label) {
+    int levels[MRR_MAX_LEVELS], Wi[MRR_MAX_LEVELS], n = 0;
+    const uint8_t* st[MRR_MAX_LEVELS];
+    for (int i = 0; i < c.num_levels; ++i) {
+      if (!c.enabled[i]) continue;
+      levels[n] = i;
+      Wi[n] = lv->width[i];
+      st[n] = lv->stencil[i];
+      ++n;
+    }
+    MRR_CUDA(ctx, launch_label(lv->label, W, H, n, levels, st, Wi, s));
+  }
+  return MRR_OK;
+}
+
+mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream_t s) {
+  EdgeParams p;
+  std::memset(&p, 0, sizeof p);
+  p.v = make_view(g->width, g->height, g->cam);
+  p.ssm = ctx->cfg.effect == MRR_SSM;
+  if (p.ssm) p.L = make_light(*g);
+  p.depth_rel = ctx->cfg.depth_rel;
+  p.normal_cos = ctx->cfg.normal_cos;
+  p.shadow_bias = ctx->cfg.shadow_bias;
+  const int h = ctx->cfg.precision == MRR_FP16;
+  MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
+  return MRR_OK;
+}
+
+mrr_levels pool_levels(mrr_ctx* ctx, int W, int H) {
+  mrr_levels lv;
+  std::memset(&lv, 0, sizeof lv);
+  lv.num_levels = ctx->cfg.num_levels;
+  for (int i = 0; i < ctx->cfg.num_levels; ++i) {
+    lv.width[i] = level_dim(W, i);
+    lv.height[i] = level_dim(H, i);
+    lv.alpha[i] = ctx->alpha[i];
+    lv.stencil[i] = ctx->stencil[i];
+    lv.worklist[i] = ctx->worklist[i];
+  }
+  lv.counts = ctx->counts;
+  lv.label = nullptr;
+  return lv;
+}
+
+mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s) {
+  const mrr_config& cf = ctx->cfg;
+  MergeParams mp;
+  std::memset(&mp, 0, sizeof mp);
+  mp.W = lv->width[0];
+  mp.H = lv->height[0];
+  mp.L = cf.num_levels;
+  mp.C = channels(cf);
+  mp.half_store = cf.precision == MRR_FP16;
+  for (int i = 0; i < cf.num_levels; ++i) {
+    mp.enabled[i] = cf.enabled[i];
+    mp.Wi[i] = lv->width[i];
+    mp.Hi[i] = lv->height[i];
+    mp.weight[i] = cf.weight[i];
+    mp.alpha[i] = lv->alpha[i];
+    mp.stencil[i] = lv->stencil[i];
+    mp.c[i] = c[i];
+  }
+  MRR_CUDA(ctx, launch_merge(mp, out, s));
+  return MRR_OK;
+}
+
+mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
+  const int W = g->width, H = g->height;
+  mrr_status st = edges_impl(ctx, g, ctx->edges, s);
+  if (st != MRR_OK) return st;
+  mrr_levels lv = pool_levels(ctx, W, H);
+  st = masks_impl(ctx, ctx->edges, &lv, s);
+  if (st != MRR_OK) return st;
+  ShadeParams p = make_shade_params(ctx, *g);
+  ShadeLevels sl;
+  std::memset(&sl, 0, sizeof sl);
+  for (int i = 0; i < ctx->cfg.num_levels; ++i) {
+    if (!ctx->cfg.enabled[i]) continue;
+    const int k = sl.nlev++;
+    sl.level[k] = i;
+    sl.list[k] = ctx->worklist[i];
+    sl.c[k] = ctx->cbuf[i];
+    sl.Wi[k] = lv.width[i];
+    sl.Hi[k] = lv.height[i];
+  }
+  sl.counts = ctx->counts;
+  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid, s));
+  return merge_impl(ctx, &lv, ctx->cbuf, out, s);
+}
+
+void free_pools(mrr_ctx* ctx) {
+  cudaFree(ctx->edges);
+  for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
+    cudaFree(ctx->alpha[i]);
+    cudaFree(ctx->stencil[i]);
+    cudaFree(ctx->worklist[i]);
+    cudaFree(ctx->cbuf[i]);
+  }
+  cudaFree(ctx->counts);
+  cudaFree(ctx->chunk_counts);
+  cudaFree(ctx->h_depth);
+  cudaFree(ctx->h_normal);
+  cudaFree(ctx->h_color);
+  cudaFree(ctx->h_smap);
+  cudaFree(ctx->h_out);
+}
+
+mrr_status alloc_pools(mrr_ctx* ctx) {
+  const mrr_config& c = ctx->cfg;
+  const int W = c.max_width, H = c.max_height;
+  ctx->pool_W = W;
+  ctx->pool_H = H;
+  const size_t npx = (size_t)W * H;
+  MRR_CUDA(ctx, cudaMalloc(&ctx->edges, npx));
+  size_t chunks = 0;
+  for (int i = 0; i < c.num_levels; ++i) {
+    const size_t n = (size_t)level_dim(W, i) * level_dim(H, i);
+    MRR_CUDA(ctx, cudaMalloc(&ctx->alpha[i], n * sizeof(float)));
+    MRR_CUDA(ctx, cudaMalloc(&ctx->stencil[i], n));
+    if (c.enabled[i]) {
+      MRR_CUDA(ctx, cudaMalloc(&ctx->worklist[i], n * sizeof(uint32_t)));
+      MRR_CUDA(ctx, cudaMalloc(&ctx->cbuf[i], n * cbytes(c)));
+    }
+    chunks += (n + COMPACT_CHUNK - 1) / COMPACT_CHUNK;
+  }
+  MRR_CUDA(ctx, cudaMalloc(&ctx->counts, MRR_MAX_LEVELS * sizeof(uint32_t)));
+  MRR_CUDA(ctx, cudaMemset(ctx->counts, 0, MRR_MAX_LEVELS * sizeof(uint32_t)));
+  ctx->chunk_cap = chunks;
+  MRR_CUDA(ctx, cudaMalloc(&ctx->chunk_counts, chunks * sizeof(uint32_t)));
+  return MRR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrr_status mrr_level_dims(int width, int height, int level, int* level_width, int* level_height) {
+  if (width < 1 || height < 1 || width > MAX_DIM || height > MAX_DIM || level < 0 || level >= MRR_MAX_LEVELS ||
+      !level_width || !level_height)
+    return MRR_EINVAL;
+  *level_width = level_dim(width, level);
+  *level_height = level_dim(height, level);
+  return MRR_OK;
+}
+
+mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
+  if (!out) return MRR_EINVAL;
+  *out = nullptr;
+  if (!cfg) return MRR_EINVAL;
+  const mrr_config& c = *cfg;
+  if (c.effect < MRR_SSAO || c.effect > MRR_SSGI) return MRR_EINVAL;
+  if (c.precision != MRR_FP32 && c.precision != MRR_FP16) return MRR_EINVAL;
+  if (c.num_levels < 1 || c.num_levels > MRR_MAX_LEVELS || !c.enabled[c.num_levels - 1]) return MRR_EINVAL;
+  for (int i = 0; i < c.num_levels; ++i) {
+    if (!c.enabled[i]) continue;
+    if (i < c.num_levels - 1 && !(i == 0 && c.force_level0)) {
+      if (!(c.sigma2[i] > 0.f) || std::ceil(3.0 * std::sqrt((double)c.sigma2[i])) > 6.0) return MRR_EINVAL;
+    }
+    if (!(c.weight[i] >= 0.f)) return MRR_EINVAL;
+  }
+  if (c.max_width < 1 || c.max_height < 1 || c.max_width > MAX_DIM || c.max_height > MAX_DIM) return MRR_EINVAL;
+  if (c.effect != MRR_SSM) {
+    if (c.samples < 1 || c.samples > MRR_MAX_SAMPLES || !c.kernel || !(c.radius > 0.f)) return MRR_EINVAL;
+  } else {
+    if (c.blocker_samples < 1 || c.blocker_samples > MRR_MAX_TAPS || c.pcf_samples < 1 ||
+        c.pcf_samples > MRR_MAX_TAPS || !c.blocker_taps || !c.pcf_taps || !(c.light_size > 0.f))
+      return MRR_EINVAL;
+  }
+  mrr_ctx* ctx = new (std::nothrow) mrr_ctx();
+  if (!ctx) return MRR_ENOMEM;
+  ctx->cfg = c;
+  ctx->cfg.kernel = ctx->cfg.blocker_taps = ctx->cfg.pcf_taps = nullptr;
+  std::memset(ctx->kernel, 0, sizeof ctx->kernel);
+  std::memset(ctx->btaps, 0, sizeof ctx->btaps);
+  std::memset(ctx->ptaps, 0, sizeof ctx->ptaps);
+  if (c.kernel)
+    for (int j = 0; j < c.samples; ++j)
+      ctx->kernel[j] = make_float4(c.kernel[4 * j], c.kernel[4 * j + 1], c.kernel[4 * j + 2], c.kernel[4 * j + 3]);
+  if (c.effect == MRR_SSM) {
+    for (int j = 0; j < c.blocker_samples; ++j) ctx->btaps[j] = make_float2(c.blocker_taps[2 * j], c.blocker_taps[2 * j + 1]);
+    for (int j = 0; j < c.pcf_samples; ++j) ctx->ptaps[j] = make_float2(c.pcf_taps[2 * j], c.pcf_taps[2 * j + 1]);
+  }
+  std::memset(ctx->gauss, 0, sizeof ctx->gauss);
+  for (int i = 0; i < c.num_levels; ++i) {
+    ctx->R[i] = 0;
+    if (c.enabled[i] && i < c.num_levels - 1 && c.sigma2[i] > 0.f) ctx->R[i] = gauss_weights((double)c.sigma2[i], ctx->gauss[i]);
+  }
+  mrr_status st = alloc_pools(ctx);
+  if (st != MRR_OK) {
+    free_pools(ctx);
+    delete ctx;
+    return st == MRR_ECUDA ? MRR_ENOMEM : st;
+  }
+  ctx->shade_grid = shade_grid_blocks();
+  *out = ctx;
+  return MRR_OK;
+}
+
+void mrr_destroy(mrr_ctx* ctx) {
+  if (!ctx) return;
+  free_pools(ctx);
+  delete ctx;
+}
+
+const char* mrr_last_error(mrr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+mrr_status mrr_edges(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* edges_dev, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  if (!edges_dev) return fail(ctx, MRR_EINVAL, "edges_dev is NULL");
+  return edges_impl(ctx, g, edges_dev, (cudaStream_t)stream);
+}
+
+mrr_status mrr_masks(mrr_ctx* ctx, const uint8_t* edges_dev, const mrr_levels* lv, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  if (!edges_dev) return fail(ctx, MRR_EINVAL, "edges_dev is NULL");
+  mrr_status st = check_levels(ctx, lv, true);
+  if (st != MRR_OK) return st;
+  if (lv->width[0] > ctx->pool_W || lv->height[0] > ctx->pool_H) {
+    // the chunk-count scratch is sized by texel count; allow any shape that fits it
+    size_t need = 0;
+    for (int i = 0; i < ctx->cfg.num_levels; ++i)
+      if (ctx->cfg.enabled[i]) need += ((size_t)lv->width[i] * lv->height[i] + COMPACT_CHUNK - 1) / COMPACT_CHUNK;
+    if (need > ctx->chunk_cap) return fail(ctx, MRR_EINVAL, "frame exceeds the context's max size");
+  }
+  return masks_impl(ctx, edges_dev, lv, (cudaStream_t)stream);
+}
+
+mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const mrr_levels* lv, void* c_level_dev,
+                           void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  st = check_levels(ctx, lv, true);
+  if (st != MRR_OK) return st;
+  if (level < 0 || level >= ctx->cfg.num_levels || !ctx->cfg.enabled[level])
+    return fail(ctx, MRR_EINVAL, "level %d is not an enabled level", level);
+  if (lv->width[0] != g->width || lv->height[0] != g->height)
+    return fail(ctx, MRR_EINVAL, "levels are for %dx%d, frame is %dx%d", lv->width[0], lv->height[0], g->width,
+                g->height);
+  if (!c_level_dev || !aligned(c_level_dev, cbytes(ctx->cfg)))
+    return fail(ctx, MRR_EINVAL, "c_level_dev is NULL or misaligned");
+  ShadeParams p = make_shade_params(ctx, *g);
+  ShadeLevels sl;
+  std::memset(&sl, 0, sizeof sl);
+  sl.nlev = 1;
+  sl.level[0] = level;
+  sl.list[0] = lv->worklist[level];
+  sl.c[0] = c_level_dev;
+  sl.Wi[0] = lv->width[level];
+  sl.Hi[0] = lv->height[level];
+  sl.counts = lv->counts;
+  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
+                                    (cudaStream_t)stream));
+  return MRR_OK;
+}
+
+mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv, void* const* c_levels_dev,
+                            void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  st = check_levels(ctx, lv, true);
+  if (st != MRR_OK) return st;
+  if (lv->width[0] != g->width || lv->height[0] != g->height)
+    return fail(ctx, MRR_EINVAL, "levels are for %dx%d, frame is %dx%d", lv->width[0], lv->height[0], g->width,
+                g->height);
+  if (!c_levels_dev) return fail(ctx, MRR_EINVAL, "c_levels_dev is NULL");
+  ShadeLevels sl;
+  std::memset(&sl, 0, sizeof sl);
+  for (int i = 0; i < ctx->cfg.num_levels; ++i) {
+    if (!ctx->cfg.enabled[i]) continue;
+    if (!c_levels_dev[i] || !aligned(c_levels_dev[i], cbytes(ctx->cfg)))
+      return fail(ctx, MRR_EINVAL, "sub-image %d is NULL or misaligned", i);
+    const int k = sl.nlev++;
+    sl.level[k] = i;
+    sl.list[k] = lv->worklist[i];
+    sl.c[k] = c_levels_dev[i];
+    sl.Wi[k] = lv->width[i];
+    sl.Hi[k] = lv->height[i];
+  }
+  sl.counts = lv->counts;
+  ShadeParams p = make_shade_params(ctx, *g);
+  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
+                                    (cudaStream_t)stream));
+  return MRR_OK;
+}
+
+uint64_t mrr_kernel_launches(void) { return mrr::launch_counter().load(); }
+
+mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,
+                              void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_levels(ctx, lv, false);
+  if (st != MRR_OK) return st;
+  if (!c_levels_dev || !out_dev) return fail(ctx, MRR_EINVAL, "c_levels_dev / out_dev is NULL");
+  for (int i = 0; i < ctx->cfg.num_levels; ++i)
+    if (ctx->cfg.enabled[i] && (!c_levels_dev[i] || !aligned(c_levels_dev[i], cbytes(ctx->cfg))))
+      return fail(ctx, MRR_EINVAL, "sub-image %d is NULL or misaligned", i);
+  if (!aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4)) return fail(ctx, MRR_EINVAL, "out_dev misaligned");
+  return merge_impl(ctx, lv, c_levels_dev, out_dev, (cudaStream_t)stream);
+}
+
+mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  if (g->width > ctx->pool_W || g->height > ctx->pool_H)
+    return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size %dx%d", g->width, g->height,
+                ctx->pool_W, ctx->pool_H);
+  if (!out_dev || !aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4))
+    return fail(ctx, MRR_EINVAL, "out_dev is NULL or misaligned");
+  return render_impl(ctx, g, out_dev, (cudaStream_t)stream);
+}
+
+mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  if (!out_dev || !aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4))
+    return fail(ctx, MRR_EINVAL, "out_dev is NULL or misaligned");
+  ShadeParams p = make_shade_params(ctx, *g);
+  MRR_CUDA(ctx, launch_shade_full(p, make_frame_in(*g), ctx->cfg.precision, out_dev, (cudaStream_t)stream));
+  return MRR_OK;
+}
+
+mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* gh, float* out_host, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, gh, false);
+  if (st != MRR_OK) return st;
+  if (!out_host) return fail(ctx, MRR_EINVAL, "out_host is NULL");
+  const mrr_config& c = ctx->cfg;
+  const int W = gh->width, H = gh->height;
+  if (W > ctx->pool_W || H > ctx->pool_H) return fail(ctx, MRR_EINVAL, "frame exceeds the context's max size");
+  const size_t npx_max = (size_t)ctx->pool_W * ctx->pool_H, npx = (size_t)W * H;
+  const size_t nbytes = c.precision == MRR_FP16 ? 8 : 16;
+  if (!ctx->h_depth) {
+    MRR_CUDA(ctx, cudaMalloc(&ctx->h_depth, npx_max * sizeof(float)));
+    MRR_CUDA(ctx, cudaMalloc(&ctx->h_normal, npx_max * nbytes));
+    MRR_CUDA(ctx, cudaMalloc(&ctx->h_out, npx_max * sizeof(float) * channels(c)));
+    if (c.effect == MRR_SSGI) MRR_CUDA(ctx, cudaMalloc(&ctx->h_color, npx_max * 8));
+  }
+  const size_t sm_bytes = c.effect == MRR_SSM
+                              ? (size_t)gh->shadow_size * gh->shadow_size * (c.precision == MRR_FP16 ? 2 : 4)
+                              : 0;
+  if (sm_bytes > ctx->h_smap_bytes) {
+    cudaFree(ctx->h_smap);
+    ctx->h_smap = nullptr;
+    ctx->h_smap_bytes = 0;
+    MRR_CUDA(ctx, cudaMalloc(&ctx->h_smap, sm_bytes));
+    ctx->h_smap_bytes = sm_bytes;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  mrr_gbuffer g = *gh;
+  MRR_CUDA(ctx, cudaMemcpyAsync(ctx->h_depth, gh->depth, npx * sizeof(float), cudaMemcpyHostToDevice, s));
+  MRR_CUDA(ctx, cudaMemcpyAsync(ctx->h_normal, gh->normal, npx * nbytes, cudaMemcpyHostToDevice, s));
+  g.depth = ctx->h_depth;
+  g.normal = ctx->h_normal;
+  if (c.effect == MRR_SSGI) {
+    MRR_CUDA(ctx, cudaMemcpyAsync(ctx->h_color, gh->color, npx * 8, cudaMemcpyHostToDevice, s));
+    g.color = ctx->h_color;
+  }
+  if (c.effect == MRR_SSM) {
+    MRR_CUDA(ctx, cudaMemcpyAsync(ctx->h_smap, gh->shadow_map, sm_bytes, cudaMemcpyHostToDevice, s));
+    g.shadow_map = ctx->h_smap;
+  }
+  st = render_impl(ctx, &g, ctx->h_out, s);
+  if (st != MRR_OK) return st;
+  MRR_CUDA(ctx, cudaMemcpyAsync(out_host, ctx->h_out, npx * sizeof(float) * channels(c), cudaMemcpyDeviceToHost, s));
+  MRR_CUDA(ctx, cudaStreamSynchronize(s));
+  return MRR_OK;
+}
+
+}  // extern "C"

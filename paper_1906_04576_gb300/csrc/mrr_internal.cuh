@@ -1,0 +1,139 @@
+// mrr_internal.cuh -- device-side parameter blocks and kernel launchers of libmrr.
+//
+// Every kernel is compiled with -fmad=false and IEEE division / square root, so each
+// floating-point operation is one correctly rounded IEEE operation in the order the
+// source writes it.  The order of every expression below is part of the method's
+// definition (it decides which samples are occluded), so it must not be "simplified".
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/mrr.h"
+
+namespace mrr {
+
+// half4: four binary16 values, 8-byte aligned (FP16 normals, SSGI colour, FP16 SSGI
+// sub-images).
+struct __align__(8) half4 {
+  __half x, y, z, w;
+};
+
+// Pinhole constants of the viewing camera, derived in double on the host from the
+// frame's float camera and rounded once to float (see make_view in api.cu):
+//   slope_x(x) = (x + 1/2) ax - bx,  slope_y(y) = by - (y + 1/2) ay,
+//   pixel X = (u + bx) kx,  Y = (by - v) ky  for a view direction (u, v, -1).
+struct ViewC {
+  int W, H;
+  float ax, bx, kx, ay, by, ky, nearp, farp;
+};
+
+// World-space basis of the viewing camera and the light camera (soft shadows).
+struct LightC {
+  float ce[3], cr[3], cu[3], cf[3];  // viewing camera eye / right / up / forward
+  float le[3], lr[3], lu[3], lf[3];  // light camera
+  float tl, kl, nearp, farp;         // light tan(half fov), S / (2 tl), near, far
+  int S;                             // shadow map side
+};
+
+// Everything an effect needs, passed by value as a kernel parameter so the sample
+// tables are read through the constant cache (every lane of a warp reads the same
+// sample at the same time).
+struct ShadeParams {
+  int effect;
+  ViewC v;
+  LightC L;
+  int samples;
+  float radius, ao_bias, gi_min_dist2;
+  float light_half, shadow_bias;
+  int nb, np;
+  float4 kernel[MRR_MAX_SAMPLES];
+  float2 btaps[MRR_MAX_TAPS];
+  float2 ptaps[MRR_MAX_TAPS];
+};
+
+// Frame inputs (device pointers).
+struct FrameIn {
+  const float* depth;
+  const void* normal;  // float4 or half4
+  const half4* color;  // SSGI
+  const void* smap;    // float or half
+};
+
+struct EdgeParams {
+  ViewC v;
+  LightC L;
+  float depth_rel, normal_cos, shadow_bias;
+  int ssm;
+};
+
+// Mask stage of one level.
+struct MaskLevel {
+  int level, Wi, Hi, R;
+  int mode;                 // 0 = blur, 1 = all ones (coarsest / forced), 2 = all zero (disabled)
+  float g[16];              // Gaussian taps k = -R..R
+  float* alpha;
+  uint8_t* stencil;
+  const uint8_t* prev;      // stencil of the previous enabled finer level, or null
+  int prev_W, prev_H, prev_shift;  // its size and log2 of the block ratio
+};
+
+// Work-list compaction of all levels in one launch: level l owns chunks
+// [chunk_begin[l], chunk_begin[l+1]) of COMPACT_CHUNK texels each.
+constexpr int COMPACT_CHUNK = 4096;
+constexpr int COMPACT_THREADS = 256;
+struct CompactParams {
+  int nlev;
+  int level_of[MRR_MAX_LEVELS];          // which level slot l refers to
+  int chunk_begin[MRR_MAX_LEVELS + 1];
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  const uint8_t* stencil[MRR_MAX_LEVELS];
+  uint32_t* list[MRR_MAX_LEVELS];
+  uint32_t* chunk_counts;                // [chunk_begin[nlev]]
+  uint32_t* counts;                      // [MRR_MAX_LEVELS]
+  int zero_mask;                         // bit i: counts[i] = 0 (levels not compacted)
+};
+
+// Shading of all listed texels of several levels in one launch.
+struct ShadeLevels {
+  int nlev;
+  int level[MRR_MAX_LEVELS];
+  const uint32_t* list[MRR_MAX_LEVELS];
+  void* c[MRR_MAX_LEVELS];
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  const uint32_t* counts;  // device, indexed by level; clamped to W_i * H_i when read
+};
+
+struct MergeParams {
+  int W, H, L, C, half_store;
+  int enabled[MRR_MAX_LEVELS];
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  float weight[MRR_MAX_LEVELS];
+  const float* alpha[MRR_MAX_LEVELS];
+  const uint8_t* stencil[MRR_MAX_LEVELS];
+  const void* c[MRR_MAX_LEVELS];
+};
+
+// ---- launchers (return cudaGetLastError() of the launch)
+cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
+                         const void* smap, int half_smap, uint8_t* E, cudaStream_t s);
+cudaError_t launch_mask_level(const MaskLevel& m, const uint8_t* E, int W, int H, cudaStream_t s);
+cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
+cudaError_t launch_label(uint8_t* label, int W, int H, int nlev, const int* levels, const uint8_t* const* stencil,
+                         const int* Wi, cudaStream_t s);
+cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
+                                int grid, cudaStream_t s);
+cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out,
+                              cudaStream_t s);
+cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
+
+int shade_grid_blocks();  // persistent grid size for the work-list shading kernel
+
+// Kernels launched by this library in this process (every launcher adds its launches).
+std::atomic<uint64_t>& launch_counter();
+inline void count_launches(int n) { launch_counter().fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+}  // namespace mrr

@@ -1,0 +1,265 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle on the same seeded
+inputs, through the C ABI.
+
+Bars: edge maps, stencils, blurred masks a_i, work lists, counts and labels
+bit-exact (the kernels make every decision in FP32 with the oracle's operation
+order); sub-images and composites within 1e-4 absolute in FP32 (bit-equality is
+expected); the FP16-storage path against the float oracle fed the same
+binary16-rounded inputs, within 1e-3 (one binary16 ulp at 1.0 is 9.8e-4).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL16 = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mrr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1906_04576_gb300 as m
+    return m
+
+
+def oracle_inputs(fr, precision):
+    """The oracle sees exactly what the kernels read: binary16-rounded colour always,
+    binary16-rounded normals and shadow map in FP16 storage."""
+    import copy
+    o = copy.copy(fr)
+    o.color = fr.color.astype(np.float16).astype(np.float32)
+    if precision == "fp16":
+        o.normal = fr.normal.astype(np.float16).astype(np.float32)
+        if fr.shadow_map is not None:
+            o.shadow_map = fr.shadow_map.astype(np.float16).astype(np.float32)
+    return o
+
+
+def make_cfg(effect, levels, W, H, precision="fp32", **kw):
+    extra = {}
+    if effect in ("ssao", "ssgi"):
+        n = kw.pop("samples", 16)
+        extra.update(samples=n, kernel=sg.hemisphere_kernel(n), radius=kw.pop("radius", 0.5 if effect == "ssao" else 1.0))
+    else:
+        extra.update(blocker_taps=sg.disk_taps(kw.pop("nb", 32), sg.BLOCKER_SEED),
+                     pcf_taps=sg.disk_taps(kw.pop("np_", 64), sg.PCF_SEED))
+    extra.update(kw)
+    cfg = orc.default_config(effect, levels, store_half=int(precision == "fp16"), **extra)
+    cfg.update(precision=precision, max_width=W, max_height=H)
+    return cfg
+
+
+def run_staged(mrr, ctx, dev, W, H, L):
+    import torch
+    edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    levels = mrr.alloc_levels(W, H, L)
+    subs = mrr.alloc_subimages(ctx, W, H)
+    out = mrr.alloc_output(ctx, W, H)
+    mrr.mrr_edges(ctx, dev, edges)
+    mrr.mrr_masks(ctx, edges, levels)
+    for i in range(L):
+        if ctx.config["enabled"][i]:
+            mrr.mrr_shade_level(ctx, i, dev, levels, subs[i])
+    mrr.mrr_upsample_merge(ctx, levels, subs, out)
+    torch.cuda.synchronize()
+    return edges, levels, subs, out
+
+
+def check_frame(mrr, fr, cfg, precision="fp32", check_full=True):
+    import torch
+    W, H, L = fr.width, fr.height, cfg["num_levels"]
+    ofr = oracle_inputs(fr, precision)
+    ref = orc.render(ofr, cfg, "f32")
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr, precision)
+    edges, levels, subs, out = run_staged(mrr, ctx, dev, W, H, L)
+    tol = TOL16 if precision == "fp16" else TOL32
+    C = 3 if cfg["effect"] == "ssgi" else 1
+
+    assert np.array_equal(edges.cpu().numpy(), ref["E"]), "edge map"
+    counts = levels.counts.cpu().numpy()
+    for i in range(L):
+        assert np.array_equal(levels.stencil[i].cpu().numpy(), ref["S"][i]), f"stencil {i}"
+        assert np.array_equal(levels.alpha[i].cpu().numpy().view(np.uint32),
+                              ref["a"][i].view(np.uint32)), f"alpha {i} (bit pattern)"
+        n = len(ref["lists"][i])
+        assert counts[i] == n, f"count {i}"
+        if n:
+            assert np.array_equal(levels.worklist[i][:n].cpu().numpy().view(np.uint32), ref["lists"][i]), f"list {i}"
+            wl = ref["lists"][i]
+            qy, qx = wl >> 16, wl & 0xFFFF
+            got = subs[i].float().cpu().numpy()
+            got = got[qy, qx] if C == 1 else got[qy, qx, :3]
+            exp = ref["c"][i][qy, qx, 0] if C == 1 else ref["c"][i][qy, qx, :]
+            assert np.abs(got - exp).max() <= tol, f"sub-image {i}: {np.abs(got - exp).max()}"
+    assert np.array_equal(levels.label.cpu().numpy(), ref["label"]), "label"
+    got = out.cpu().numpy()
+    got = got if C == 1 else got[..., :3]
+    exp = ref["out"][..., 0] if C == 1 else ref["out"]
+    assert np.abs(got - exp).max() <= tol, f"composite: {np.abs(got - exp).max()}"
+
+    # the one-call path equals the staged path bit for bit
+    out2 = mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    if check_full:
+        full = mrr.alloc_output(ctx, W, H)
+        mrr.mrr_render_full(ctx, dev, full)
+        torch.cuda.synchronize()
+        exp_full = orc.shade_full(ofr, cfg, "f32")
+        g = full.cpu().numpy()
+        g = g if C == 1 else g[..., :3]
+        e = exp_full[..., 0] if C == 1 else exp_full
+        assert np.abs(g - e).max() <= TOL32, f"full-res: {np.abs(g - e).max()}"
+    mrr.mrr_destroy(ctx)
+    return ref
+
+
+# ------------------------------------------------------------------ SSAO
+
+def test_ssao_256_three_levels(mrr):
+    fr = sg.gbuffer(0, 256, 256, 8, 0)
+    check_frame(mrr, fr, make_cfg("ssao", 3, 256, 256, samples=16))
+
+
+@pytest.mark.parametrize("W,H,seed", [(203, 141, 11), (257, 129, 3), (33, 17, 5), (1, 1, 0), (7, 3, 2), (300, 1, 4)])
+def test_ssao_ragged_sizes(mrr, W, H, seed):
+    fr = sg.gbuffer(seed, W, H, 16, 6)
+    check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=64))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ssao_fp16_storage(mrr, seed):
+    fr = sg.gbuffer(seed, 190, 110, 20, 6)
+    check_frame(mrr, fr, make_cfg("ssao", 4, 190, 110, "fp16", samples=32), "fp16")
+
+
+def test_all_sky_frame(mrr):
+    W, H = 64, 40
+    fr = sg.gbuffer(0, W, H, 0, 0, eye=(0.0, 2.0, 6.0), target=(0.0, 20.0, 0.0))   # looking up: sky only
+    assert np.all(fr.depth >= fr.cam.far)
+    ref = check_frame(mrr, fr, make_cfg("ssao", 4, W, H))
+    assert ref["E"].sum() == 0 and np.all(ref["out"] == 1.0)
+
+
+def test_dense_edges_everywhere(mrr):
+    """Noise depth: every pixel is an edge, so level 0 covers the whole frame."""
+    W, H = 96, 64
+    fr = sg.gbuffer(0, W, H, 0, 0)
+    rng = np.random.default_rng(0)
+    fr.depth = (2.0 + rng.random((H, W))).astype(np.float32)
+    fr.normal[:] = np.array([0, 0, 1, 0], np.float32)
+    ref = check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=16))
+    assert np.all(ref["label"] == 0)
+
+
+def test_force_level0_equals_full_resolution_on_gpu(mrr):
+    import torch
+    W, H = 160, 90
+    fr = sg.gbuffer(6, W, H, 12, 4)
+    cfg = make_cfg("ssao", 4, W, H, samples=32, force_level0=1)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    out, full = mrr.alloc_output(ctx, W, H), mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, out)
+    mrr.mrr_render_full(ctx, dev, full)
+    torch.cuda.synchronize()
+    assert torch.equal(out, full)
+    assert np.array_equal(full.cpu().numpy(), orc.shade_full(fr, cfg, "f32")[..., 0])
+
+
+# ------------------------------------------------------------------ SSGI / SSM
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_ssgi_skips_half_level(mrr, precision):
+    W, H = 170, 100
+    fr = sg.gbuffer(8, W, H, 20, 6)
+    cfg = make_cfg("ssgi", 4, W, H, precision, samples=32, radius=1.0)
+    assert cfg["enabled"] == [1, 0, 1, 1]
+    ref = check_frame(mrr, fr, cfg, precision)
+    assert len(ref["lists"][1]) == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_ssm_soft_shadows(mrr, precision):
+    W, H = 180, 120
+    fr = sg.gbuffer(4, W, H, 16, 4, shadow_size=512)
+    check_frame(mrr, fr, make_cfg("ssm", 4, W, H, precision), precision)
+
+
+# ------------------------------------------------------------------ full-size workload samples
+
+def test_ssao64_1080p_full_size(mrr):
+    """The 1920x1080 SSAO-64 workload in the launch configuration the benchmark times:
+    masks and lists bit-exact over the whole frame; the composite against the oracle
+    over the whole frame."""
+    import torch
+    wl = sg.WORKLOADS["ssao64_1080p"]
+    W, H = wl["width"], wl["height"]
+    fr = sg.gbuffer(0, W, H, wl["n_boxes"], wl["n_spheres"])
+    cfg = make_cfg("ssao", 4, W, H, samples=64)
+    ref = orc.render(fr, cfg, "f32")
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    out = mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref["out"][..., 0]).max() <= TOL32
+    edges, levels, subs, out2 = run_staged(mrr, ctx, dev, W, H, 4)
+    assert np.array_equal(edges.cpu().numpy(), ref["E"])
+    for i in range(4):
+        assert np.array_equal(levels.stencil[i].cpu().numpy(), ref["S"][i])
+        n = len(ref["lists"][i])
+        assert levels.counts[i].item() == n
+        assert np.array_equal(levels.worklist[i][:n].cpu().numpy().view(np.uint32), ref["lists"][i])
+    # sampled full-resolution pixels of the plain kernel against the oracle one by one
+    full = mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render_full(ctx, dev, full)
+    torch.cuda.synchronize()
+    g = full.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for _ in range(400):
+        x, y = int(rng.integers(W)), int(rng.integers(H))
+        assert abs(g[y, x] - orc.shade_pixel(fr, cfg, x, y, "f32")[0]) <= TOL32
+    # the quality gate of the method: RMSE against full-resolution shading
+    assert float(np.sqrt(np.mean((out.cpu().numpy() - g) ** 2))) <= 1e-2
+    mrr.mrr_destroy(ctx)
+
+
+def test_render_host_matches_device_path(mrr):
+    import torch
+    W, H = 200, 120
+    fr = sg.gbuffer(2, W, H, 16, 4)
+    cfg = make_cfg("ssao", 4, W, H, samples=32)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    out = mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, out)
+    host = mrr.pin_frame(fr)
+    out_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    mrr.mrr_render_host(ctx, host, out_h)
+    torch.cuda.synchronize()
+    assert torch.equal(out.cpu(), out_h)
+    mrr.mrr_destroy(ctx)
+
+
+def test_frame_larger_than_context_is_rejected(mrr):
+    W, H = 64, 64
+    fr = sg.gbuffer(0, W, H, 4, 0)
+    cfg = make_cfg("ssao", 4, 32, 32)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    out = mrr.alloc_output(ctx, W, H)
+    with pytest.raises(mrr.MrrError) as ei:
+        mrr.mrr_render(ctx, dev, out)
+    assert ei.value.status == mrr.MRR_EINVAL
+    mrr.mrr_destroy(ctx)
