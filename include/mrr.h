@@ -86,6 +86,12 @@ typedef struct mrr_config {
   float light_size;               /* side of the square area light (world units) */
   float shadow_bias;              /* light-depth bias */
   int max_width, max_height;      /* largest frame mrr_render / mrr_masks will see (sizes pools) */
+  /* tuning knobs (0 = library default); they change speed, never results */
+  int lanes_per_texel;            /* SSAO work-list kernel: lanes sharing one texel's samples: 1, 2 or 4 */
+  int lanes_per_pixel;            /* SSAO full-resolution kernel: lanes sharing one pixel: 1, 2 or 4 */
+  int no_graph;                   /* 1: mrr_render launches its kernels one by one instead of replaying a
+                                     CUDA graph of them (the graph is re-captured whenever the frame
+                                     descriptor or output pointer changes) */
 } mrr_config;
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the

@@ -17,9 +17,10 @@
 //             formulas, so the readings below are fixed in the design notes;
 //   Sec. 4.2  bilinear upsampling of every sub-image to full size and the sequential
 //             blend of Eq. (1), from the coarsest level to the finest.
-// T = float is the parity oracle (discrete decisions in the kernels' precision, FP32,
-// built with -ffp-contract=off so no multiply-add is fused); T = double is the FP64
-// reference for error statements.
+// T = float is the parity oracle (discrete decisions in the kernels' precision, FP32);
+// T = double is the FP64 reference for error statements.  The build uses
+// -ffp-contract=off: a multiply-add is fused only where the source writes std::fma
+// (one rounding), every other operation is rounded on its own, in source order.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -137,11 +138,38 @@ struct Inputs {
   const float* smap;    // [S][S] or null
 };
 
+// View-space position of pixel (x, y) at linear depth d: the pixel centre's ray slopes
+// sx = (x + 1/2) ax - bx and sy = by - (y + 1/2) ay (each one fused multiply-add), times d.
 template <typename T> V3<T> view_pos(const View<T>& v, int x, int y, T d) {
-  T sx = ((T)x + T(0.5)) * v.ax - v.bx;
-  T sy = v.by - ((T)y + T(0.5)) * v.ay;
+  T sx = std::fma((T)x + T(0.5), v.ax, -v.bx);
+  T sy = std::fma(-((T)y + T(0.5)), v.ay, v.by);
   V3<T> p = {sx * d, sy * d, -d};
   return p;
+}
+
+// Sample point S = P + k.x (r T) + k.y (r B) + k.z (r N), accumulated with fused
+// multiply-adds in the order k.x, k.y, k.z.
+template <typename T>
+V3<T> sample_point(const V3<T>& P, const V3<T>& tr, const V3<T>& br, const V3<T>& nr, T kx, T ky, T kz) {
+  V3<T> S;
+  S.x = std::fma(kz, nr.x, std::fma(ky, br.x, std::fma(kx, tr.x, P.x)));
+  S.y = std::fma(kz, nr.y, std::fma(ky, br.y, std::fma(kx, tr.y, P.y)));
+  S.z = std::fma(kz, nr.z, std::fma(ky, br.z, std::fma(kx, tr.z, P.z)));
+  return S;
+}
+
+// Projection of a view-space point with depth dS = -S.z >= near to pixel coordinates:
+// inv = 1 / dS (correctly rounded), X = (S.x inv + bx) kx, Y = (by - S.y inv) ky, the
+// bracketed terms as fused multiply-adds.  The pixel index is the integer part.
+template <typename T> void project(const View<T>& v, const V3<T>& S, T dS, T& X, T& Y) {
+  T inv = T(1) / dS;
+  X = std::fma(S.x, inv, v.bx) * v.kx;
+  Y = std::fma(-S.y, inv, v.by) * v.ky;
+}
+
+template <typename T> V3<T> scale3(const V3<T>& a, T s) {
+  V3<T> r = {s * a.x, s * a.y, s * a.z};
+  return r;
 }
 
 template <typename T> V3<T> load_normal(const Inputs& in, int W, int x, int y) {
@@ -150,8 +178,8 @@ template <typename T> V3<T> load_normal(const Inputs& in, int W, int x, int y) {
   return r;
 }
 
-// SSAO (Mittring 2007; Bavoil et al. 2008), our reading: N samples S = P + r (k_x T +
-// k_y B + k_z N) in the normal's hemisphere; each is projected to its pixel, and it is
+// SSAO (Mittring 2007; Bavoil et al. 2008), our reading: N samples S = P + k_x (rT) +
+// k_y (rB) + k_z (rN) in the normal's hemisphere; each is projected to its pixel, and it is
 // occluded when the depth buffer there lies in front of it by more than the bias and
 // within the radius of the shaded point.  AO = 1 - occluded / N; sky is 1.
 template <typename T> T ssao_at(const orc_params& p, const View<T>& v, const Inputs& in, int x, int y) {
@@ -163,18 +191,15 @@ template <typename T> T ssao_at(const orc_params& p, const View<T>& v, const Inp
   V3<T> t, b;
   make_basis(n, t, b);
   const T r = (T)p.radius, bias = (T)p.ao_bias;
+  const V3<T> tr = scale3(t, r), br = scale3(b, r), nr = scale3(n, r);
   int occ = 0;
   for (int j = 0; j < p.samples; ++j) {
     T kx = (T)p.kernel[4 * j], ky = (T)p.kernel[4 * j + 1], kz = (T)p.kernel[4 * j + 2];
-    V3<T> S;
-    S.x = P.x + r * (kx * t.x + ky * b.x + kz * n.x);
-    S.y = P.y + r * (kx * t.y + ky * b.y + kz * n.y);
-    S.z = P.z + r * (kx * t.z + ky * b.z + kz * n.z);
+    V3<T> S = sample_point(P, tr, br, nr, kx, ky, kz);
     T dS = -S.z;
     if (dS < v.nearp) continue;
-    T inv = T(1) / dS;
-    T X = (S.x * inv + v.bx) * v.kx;
-    T Y = (v.by - S.y * inv) * v.ky;
+    T X, Y;
+    project(v, S, dS, X, Y);
     if (!(X >= T(0) && X < (T)W)) continue;
     if (!(Y >= T(0) && Y < (T)H)) continue;
     int ix = (int)X, iy = (int)Y;
@@ -202,18 +227,15 @@ void ssgi_at(const orc_params& p, const View<T>& v, const Inputs& in, int x, int
   const T r = (T)p.radius;
   const T r2 = r * r;
   const T dmin2 = (T)p.gi_min_dist2;
+  const V3<T> tr = scale3(t, r), br = scale3(b, r), nr = scale3(n, r);
   T acc[3] = {T(0), T(0), T(0)};
   for (int j = 0; j < p.samples; ++j) {
     T kx = (T)p.kernel[4 * j], ky = (T)p.kernel[4 * j + 1], kz = (T)p.kernel[4 * j + 2];
-    V3<T> S;
-    S.x = P.x + r * (kx * t.x + ky * b.x + kz * n.x);
-    S.y = P.y + r * (kx * t.y + ky * b.y + kz * n.y);
-    S.z = P.z + r * (kx * t.z + ky * b.z + kz * n.z);
+    V3<T> S = sample_point(P, tr, br, nr, kx, ky, kz);
     T dS = -S.z;
     if (dS < v.nearp) continue;
-    T inv = T(1) / dS;
-    T X = (S.x * inv + v.bx) * v.kx;
-    T Y = (v.by - S.y * inv) * v.ky;
+    T X, Y;
+    project(v, S, dS, X, Y);
     if (!(X >= T(0) && X < (T)W)) continue;
     if (!(Y >= T(0) && Y < (T)H)) continue;
     int ix = (int)X, iy = (int)Y;
@@ -221,18 +243,18 @@ void ssgi_at(const orc_params& p, const View<T>& v, const Inputs& in, int x, int
     if (ds >= v.farp) continue;
     V3<T> Ps = view_pos(v, ix, iy, ds);
     V3<T> D = {Ps.x - P.x, Ps.y - P.y, Ps.z - P.z};
-    T dd = D.x * D.x + D.y * D.y + D.z * D.z;
+    T dd = std::fma(D.z, D.z, std::fma(D.y, D.y, D.x * D.x));
     if (dd > r2 || dd == T(0)) continue;
     T il = T(1) / std::sqrt(dd);
     V3<T> w = {D.x * il, D.y * il, D.z * il};
     V3<T> ns = load_normal<T>(in, W, ix, iy);
-    T c1 = n.x * w.x + n.y * w.y + n.z * w.z;
-    T c2 = -(ns.x * w.x + ns.y * w.y + ns.z * w.z);
+    T c1 = std::fma(n.z, w.z, std::fma(n.y, w.y, n.x * w.x));
+    T c2 = -std::fma(ns.z, w.z, std::fma(ns.y, w.y, ns.x * w.x));
     T g = std::max(T(0), c1) * std::max(T(0), c2) / std::max(dd, dmin2);
     const float* C = in.color + 4 * ((size_t)iy * W + ix);
-    acc[0] = acc[0] + (T)C[0] * g;
-    acc[1] = acc[1] + (T)C[1] * g;
-    acc[2] = acc[2] + (T)C[2] * g;
+    acc[0] = std::fma((T)C[0], g, acc[0]);
+    acc[1] = std::fma((T)C[1], g, acc[1]);
+    acc[2] = std::fma((T)C[2], g, acc[2]);
   }
   T scale = r2 / (T)p.samples;
   out[0] = acc[0] * scale;
@@ -316,8 +338,8 @@ T ssm_at(const orc_params& p, const View<T>& v, const LightView<T>& L, const Inp
   T sum = T(0);
   int cnt = 0;
   for (int j = 0; j < p.blocker_samples; ++j) {
-    T tx = Xt + (T)p.blocker_taps[2 * j] * rs;
-    T ty = Yt + (T)p.blocker_taps[2 * j + 1] * rs;
+    T tx = std::fma((T)p.blocker_taps[2 * j], rs, Xt);
+    T ty = std::fma((T)p.blocker_taps[2 * j + 1], rs, Yt);
     if (!(tx >= T(0) && tx < S && ty >= T(0) && ty < S)) continue;
     T zb = (T)in.smap[(size_t)(int)ty * L.S + (int)tx];
     if (zb < zr - bias) {
@@ -330,8 +352,8 @@ T ssm_at(const orc_params& p, const View<T>& v, const LightView<T>& L, const Inp
   T rf = hl * (zr - zavg) / (zavg * zr) * L.kl;
   int lit = 0;
   for (int j = 0; j < p.pcf_samples; ++j) {
-    T tx = Xt + (T)p.pcf_taps[2 * j] * rf;
-    T ty = Yt + (T)p.pcf_taps[2 * j + 1] * rf;
+    T tx = std::fma((T)p.pcf_taps[2 * j], rf, Xt);
+    T ty = std::fma((T)p.pcf_taps[2 * j + 1], rf, Yt);
     if (!(tx >= T(0) && tx < S && ty >= T(0) && ty < S)) {
       lit += 1;
       continue;
@@ -444,7 +466,7 @@ template <typename T> int gauss_weights(double sigma2, T* g) {
 // Masks of all levels (Sec. 3.1, Table 1, Sec. 4.1):
 //   D_i(q) = max of E over the block of q (the downsampled edge image);
 //   a_i = horizontal then vertical truncated Gaussian of D_i with variance sigma_i^2,
-//         taps in ascending order, zero outside the level;
+//         taps in ascending order (one fused multiply-add per tap), zero outside the level;
 //   S_i = [a_i > 0] (the stencil of Sec. 4.1);
 //   nesting (Fig. 2/3): S_j(Q) |= S_k(q) for every q of the previous enabled finer
 //         level k inside Q's block, so finer areas are included in coarser ones;
@@ -489,7 +511,7 @@ void masks(const orc_params& p, const uint8_t* E, T* const* a, uint8_t* const* S
           for (int k = -R; k <= R; ++k) {
             int xx = x + k;
             if (xx < 0 || xx >= Wi) continue;
-            s = s + g[k + R] * (T)D[(size_t)y * Wi + xx];
+            s = std::fma(g[k + R], (T)D[(size_t)y * Wi + xx], s);
           }
           h[(size_t)y * Wi + x] = s;
         }
@@ -499,7 +521,7 @@ void masks(const orc_params& p, const uint8_t* E, T* const* a, uint8_t* const* S
           for (int k = -R; k <= R; ++k) {
             int yy = y + k;
             if (yy < 0 || yy >= Hi) continue;
-            s = s + g[k + R] * h[(size_t)yy * Wi + x];
+            s = std::fma(g[k + R], h[(size_t)yy * Wi + x], s);
           }
           a[i][(size_t)y * Wi + x] = s;
           S[i][(size_t)y * Wi + x] = s > T(0) ? 1 : 0;

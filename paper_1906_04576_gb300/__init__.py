@@ -14,7 +14,7 @@ device memory and streams.  The functions carry the C names of include/mrr.h:
     mrr_kernel_launches()
 
 Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
-``python -m paper_1906_04576_gb300._build``): there is no CPU fallback.
+``python paper_1906_04576_gb300/_build.py``): there is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -55,6 +55,7 @@ class mrr_config(ctypes.Structure):
         ("blocker_taps", ctypes.POINTER(ctypes.c_float)), ("pcf_taps", ctypes.POINTER(ctypes.c_float)),
         ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float),
         ("max_width", ctypes.c_int), ("max_height", ctypes.c_int),
+        ("lanes_per_texel", ctypes.c_int), ("lanes_per_pixel", ctypes.c_int), ("no_graph", ctypes.c_int),
     ]
 
 
@@ -195,6 +196,9 @@ def make_config(cfg: dict) -> tuple[mrr_config, list]:
     c.shadow_bias = cfg.get("shadow_bias", 0.03)
     c.max_width = cfg["max_width"]
     c.max_height = cfg["max_height"]
+    c.lanes_per_texel = int(cfg.get("lanes_per_texel", 0))
+    c.lanes_per_pixel = int(cfg.get("lanes_per_pixel", 0))
+    c.no_graph = int(cfg.get("no_graph", 0))
     return c, keep
 
 

@@ -19,6 +19,7 @@ struct mrr_ctx {
   float gauss[MRR_MAX_LEVELS][16];
   int R[MRR_MAX_LEVELS];
   int shade_grid = 0;
+  int split_texel = 2, split_pixel = 1;  // SSAO lanes per texel / pixel
   std::string err;
   // pools of mrr_render / mrr_masks, sized for max_width x max_height
   int pool_W = 0, pool_H = 0;
@@ -37,6 +38,13 @@ struct mrr_ctx {
   void* h_smap = nullptr;
   size_t h_smap_bytes = 0;
   float* h_out = nullptr;
+  // mrr_render replays a CUDA graph of its launches while the frame's arguments repeat
+  bool use_graph = true;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  mrr_gbuffer graph_key;
+  float* graph_out = nullptr;
+  uint64_t graph_replays = 0;
 };
 
 namespace {
@@ -195,34 +203,24 @@ mrr_status check_levels(mrr_ctx* ctx, const mrr_levels* lv, bool need_lists) {
 mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cudaStream_t s) {
   const mrr_config& c = ctx->cfg;
   const int W = lv->width[0], H = lv->height[0];
-  int prev = -1;
+  MaskParams m;
+  std::memset(&m, 0, sizeof m);
+  m.W = W;
+  m.H = H;
+  m.L = c.num_levels;
   for (int i = 0; i < c.num_levels; ++i) {
-    MaskLevel m;
-    std::memset(&m, 0, sizeof m);
-    m.level = i;
-    m.Wi = lv->width[i];
-    m.Hi = lv->height[i];
-    if (!c.enabled[i]) {
-      if (!lv->alpha[i] || !lv->stencil[i]) continue;  // nothing to clear
-      m.mode = 2;
-    } else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) {
-      m.mode = 1;
-    } else {
-      m.mode = 0;
-      m.R = ctx->R[i];
-      std::memcpy(m.g, ctx->gauss[i], sizeof m.g);
-      if (prev >= 0) {
-        m.prev = lv->stencil[prev];
-        m.prev_W = lv->width[prev];
-        m.prev_H = lv->height[prev];
-        m.prev_shift = i - prev;
-      }
-    }
-    m.alpha = lv->alpha[i];
-    m.stencil = lv->stencil[i];
-    MRR_CUDA(ctx, launch_mask_level(m, E, W, H, s));
-    if (c.enabled[i]) prev = i;
+    if (!c.enabled[i]) m.mode[i] = 2;
+    else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) m.mode[i] = 1;
+    else m.mode[i] = 0;
+    m.R[i] = ctx->R[i];
+    std::memcpy(m.g[i], ctx->gauss[i], sizeof m.g[i]);
+    m.Wi[i] = lv->width[i];
+    m.Hi[i] = lv->height[i];
+    m.alpha[i] = lv->alpha[i];
+    m.stencil[i] = lv->stencil[i];
   }
+  m.label = lv->label;
+  MRR_CUDA(ctx, launch_masks(m, E, s));
   // work lists of every enabled level in one two-pass compaction
   CompactParams cp;
   std::memset(&cp, 0, sizeof cp);
@@ -248,18 +246,6 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
   cp.chunk_counts = ctx->chunk_counts;
   cp.counts = lv->counts;
   MRR_CUDA(ctx, launch_compact(cp, s));
-  if (lv->label) {
-    int levels[MRR_MAX_LEVELS], Wi[MRR_MAX_LEVELS], n = 0;
-    const uint8_t* st[MRR_MAX_LEVELS];
-    for (int i = 0; i < c.num_levels; ++i) {
-      if (!c.enabled[i]) continue;
-      levels[n] = i;
-      Wi[n] = lv->width[i];
-      st[n] = lv->stencil[i];
-      ++n;
-    }
-    MRR_CUDA(ctx, launch_label(lv->label, W, H, n, levels, st, Wi, s));
-  }
   return MRR_OK;
 }
 
@@ -315,7 +301,61 @@ mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
   return MRR_OK;
 }
 
+mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s);
+
+// mrr_render's launches depend only on the frame descriptor (pointers, sizes, cameras)
+// and the output pointer: the first call with a new descriptor captures them into a
+// graph on an internal stream, later calls with the same descriptor replay it on the
+// caller's stream (one launch instead of six).
+mrr_gbuffer canonical_key(const mrr_gbuffer* g) {  // field copy: padding bytes are zero
+  mrr_gbuffer k;
+  std::memset(&k, 0, sizeof k);
+  k.width = g->width;
+  k.height = g->height;
+  k.depth = g->depth;
+  k.normal = g->normal;
+  k.color = g->color;
+  k.shadow_map = g->shadow_map;
+  k.shadow_size = g->shadow_size;
+  k.cam = g->cam;
+  k.light = g->light;
+  return k;
+}
+
 mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
+  if (!ctx->use_graph) return render_launches(ctx, g, out, s);
+  const mrr_gbuffer key = canonical_key(g);
+  const bool same = ctx->graph_exec && out == ctx->graph_out && std::memcmp(&ctx->graph_key, &key, sizeof key) == 0;
+  if (!same) {
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    if (!ctx->capture_stream) MRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    MRR_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    mrr_status st = render_launches(ctx, g, out, ctx->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (st != MRR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(ctx, MRR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      return fail(ctx, MRR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    ctx->graph_key = key;
+    ctx->graph_out = out;
+  }
+  MRR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, s));
+  ++ctx->graph_replays;
+  return MRR_OK;
+}
+
+mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const int W = g->width, H = g->height;
   mrr_status st = edges_impl(ctx, g, ctx->edges, s);
   if (st != MRR_OK) return st;
@@ -335,11 +375,16 @@ mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStrea
     sl.Hi[k] = lv.height[i];
   }
   sl.counts = ctx->counts;
-  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid, s));
+  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
+                                    ctx->split_texel, s));
   return merge_impl(ctx, &lv, ctx->cbuf, out, s);
 }
 
 void free_pools(mrr_ctx* ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  ctx->graph_exec = nullptr;
+  ctx->capture_stream = nullptr;
   cudaFree(ctx->edges);
   for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
     cudaFree(ctx->alpha[i]);
@@ -410,6 +455,8 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
     if (!(c.weight[i] >= 0.f)) return MRR_EINVAL;
   }
   if (c.max_width < 1 || c.max_height < 1 || c.max_width > MAX_DIM || c.max_height > MAX_DIM) return MRR_EINVAL;
+  for (int v : {c.lanes_per_texel, c.lanes_per_pixel})
+    if (v != 0 && v != 1 && v != 2 && v != 4) return MRR_EINVAL;
   if (c.effect != MRR_SSM) {
     if (c.samples < 1 || c.samples > MRR_MAX_SAMPLES || !c.kernel || !(c.radius > 0.f)) return MRR_EINVAL;
   } else {
@@ -443,6 +490,9 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
     return st == MRR_ECUDA ? MRR_ENOMEM : st;
   }
   ctx->shade_grid = shade_grid_blocks();
+  if (c.lanes_per_texel) ctx->split_texel = c.lanes_per_texel;
+  if (c.lanes_per_pixel) ctx->split_pixel = c.lanes_per_pixel;
+  ctx->use_graph = c.no_graph == 0;
   *out = ctx;
   return MRR_OK;
 }
@@ -503,7 +553,7 @@ mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const 
   sl.Hi[0] = lv->height[level];
   sl.counts = lv->counts;
   MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
-                                    (cudaStream_t)stream));
+                                    ctx->split_texel, (cudaStream_t)stream));
   return MRR_OK;
 }
 
@@ -534,7 +584,7 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
   sl.counts = lv->counts;
   ShadeParams p = make_shade_params(ctx, *g);
   MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
-                                    (cudaStream_t)stream));
+                                    ctx->split_texel, (cudaStream_t)stream));
   return MRR_OK;
 }
 
@@ -572,7 +622,8 @@ mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, v
   if (!out_dev || !aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4))
     return fail(ctx, MRR_EINVAL, "out_dev is NULL or misaligned");
   ShadeParams p = make_shade_params(ctx, *g);
-  MRR_CUDA(ctx, launch_shade_full(p, make_frame_in(*g), ctx->cfg.precision, out_dev, (cudaStream_t)stream));
+  MRR_CUDA(ctx, launch_shade_full(p, make_frame_in(*g), ctx->cfg.precision, out_dev, ctx->split_pixel,
+                                  (cudaStream_t)stream));
   return MRR_OK;
 }
 

@@ -1,10 +1,13 @@
 // k_edges.cu -- the edge image of Sec. 3.1.
 //
-// One thread per pixel, one CTA per 32x8 tile.  The tile and a one-pixel halo of depth,
-// normals and (soft shadows) the one-sample hard shadow are staged in shared memory
-// once, so each G-buffer texel is read from global memory by one thread and the
-// 4-neighbour tests read shared memory.  The hard shadow of Sec. 3.1 ("one sample per
-// pixel") is computed once per staged texel, not once per neighbour test.
+// One thread per pixel, one CTA per 32x8 tile.
+// edges_direct_kernel (SSAO, SSGI): each lane reads its pixel and its 4 neighbours
+//   straight from global memory; the neighbours' lines are the block's own rows, so
+//   they are L1 hits and DRAM sees each G-buffer texel about once.
+// edges_kernel (soft shadows): the tile and a one-pixel halo of depth, normals and the
+//   one-sample hard shadow of Sec. 3.1 are staged in shared memory, so each staged
+//   texel's hard shadow (a reconstruction, a light-space projection and a shadow-map
+//   read) is computed once, not once per neighbour test.
 #include "mrr_internal.cuh"
 #include "shade_common.cuh"
 
@@ -78,12 +81,54 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   E[(size_t)y * W + x] = e;
 }
 
+template <typename NT>
+__global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, const float* __restrict__ depth,
+                                                               const NT* __restrict__ normal,
+                                                               uint8_t* __restrict__ E) {
+  const int W = p.v.W, H = p.v.H;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const int i = y * W + x;
+  const float farp = p.v.farp;
+  const float d = __ldg(depth + i);
+  uint8_t e = 0;
+  if (d < farp) {
+    const float3 n = load_normal(normal, i);
+    const bool has[4] = {x > 0, x < W - 1, y > 0, y < H - 1};
+    const int off[4] = {-1, 1, -W, W};
+    float dn[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dn[k] = has[k] ? __ldg(depth + i + off[k]) : 0.0f;
+      if (!has[k]) continue;
+      if (dn[k] >= farp) {  // sky neighbour
+        e = 1;
+        continue;
+      }
+      const float3 m = load_normal(normal, i + off[k]);
+      if (n.x * m.x + n.y * m.y + n.z * m.z < p.normal_cos) e = 1;
+    }
+    if (has[0] && has[1]) {
+      const float lap = (dn[0] + dn[1]) - 2.0f * d;
+      if (fabsf(lap) > p.depth_rel * d) e = 1;
+    }
+    if (has[2] && has[3]) {
+      const float lap = (dn[2] + dn[3]) - 2.0f * d;
+      if (fabsf(lap) > p.depth_rel * d) e = 1;
+    }
+  }
+  E[i] = e;
+}
+
 }  // namespace
 
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
-  if (half_normal) {
+  if (!p.ssm) {
+    if (half_normal) edges_direct_kernel<half4><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, E);
+    else edges_direct_kernel<float4><<<grid, block, 0, s>>>(p, depth, (const float4*)normal, E);
+  } else if (half_normal) {
     if (half_smap)
       edges_kernel<half4, __half><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const __half*)smap, E);
     else

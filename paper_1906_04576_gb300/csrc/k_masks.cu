@@ -1,89 +1,191 @@
 // k_masks.cu -- the per-level masks of Sec. 3.1 / Table 1, the stencil of Sec. 4.1 and
 // the dense work lists that replace the stencil test on the GPU.
 //
-// mask_level_kernel: one CTA per 32x16 tile of level texels.  It stages the downsampled
-//   edge image D_i (block maximum of the edge image) for the tile plus an R_i halo in
-//   shared memory, blurs it horizontally into a second shared buffer and vertically
-//   into a_i, sets S_i = [a_i > 0] and ORs in the set texels of the previous enabled
-//   finer level inside the texel's block (inclusive nesting, Fig. 2/3).
+// masks_kernel: ONE launch computes every level.  A CTA owns a 64x64 full-resolution
+//   tile (32x32 at level 1, 16x16 at level 2, ...) and stages the edge image of the tile
+//   plus a 24-pixel halo in shared memory once.  For each blurred level i it forms the
+//   downsampled edge image D_i (block maximum) over the tile and an R_i halo, blurs it
+//   horizontally then vertically (taps in ascending order, one fused multiply-add each,
+//   the Gaussian held in registers), sets S_i = [a_i > 0] OR-ed with the set texels of
+//   the previous enabled finer level inside the block (inclusive nesting, Fig. 2/3 --
+//   the children of a texel always lie in the same tile), and writes a_i, S_i.  The
+//   coarsest level is written as a = 1, S = 1; disabled levels as 0.  Finally every
+//   pixel's owning level (the finest enabled level whose stencil covers it).
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
 //   every level's stencil into a row-major list of (y << 16) | x.  Pass 1 counts the set
 //   texels of each 4096-texel chunk; pass 2 gives each chunk its exclusive prefix (a
-//   block reduction over the preceding chunk counts of its level) and scatters with a
-//   warp ballot + popc per 256-texel round, so list order = index order and no warp of
-//   the shading kernel idles on an unmasked texel.
-// label_kernel: the owning level of each full-resolution pixel.
+//   block reduction over the preceding chunk counts of its level), then each warp
+//   scatters its 512 texels with ballot + popc, so list order = index order and no warp
+//   of the shading kernel idles on an unmasked texel.
 #include "mrr_internal.cuh"
 
 namespace mrr {
 
 namespace {
 
-constexpr int MTX = 32, MTY = 16, MAXR = 6;
+constexpr int TS = MASK_TILE;            // 64
+constexpr int MG = MASK_MARGIN;          // 24
+constexpr int ES = TS + 2 * MG;          // 112: staged edge image side
+constexpr int MAXR = 6;
+constexpr int DMAX = TS + 2 * MAXR;      // 76: largest D region side (level 0)
+constexpr int MTHREADS = 256;            // as 32 x 8
 
-__global__ void __launch_bounds__(256) mask_level_kernel(MaskLevel m, const uint8_t* __restrict__ E, int W, int H) {
-  __shared__ float sD[MTY + 2 * MAXR][MTX + 2 * MAXR];
-  __shared__ float sh[MTY + 2 * MAXR][MTX];
-  const int tid = threadIdx.x;
-  const int tx0 = blockIdx.x * MTX, ty0 = blockIdx.y * MTY;
-  const int Wi = m.Wi, Hi = m.Hi;
-  if (m.mode != 0) {
-    const float av = m.mode == 1 ? 1.0f : 0.0f;
-    const uint8_t sv = m.mode == 1 ? 1 : 0;
-    for (int k = tid; k < MTX * MTY; k += blockDim.x) {
-      const int qx = tx0 + (k % MTX), qy = ty0 + (k / MTX);
-      if (qx < Wi && qy < Hi) {
-        m.alpha[(size_t)qy * Wi + qx] = av;
-        m.stencil[(size_t)qy * Wi + qx] = sv;
+__device__ __forceinline__ int s_offset(int i) {  // offset of level i's tile stencil in smem
+  // 64^2, 32^2, 16^2, 8^2 texels for levels 0..3
+  return i == 0 ? 0 : (i == 1 ? 4096 : (i == 2 ? 5120 : 5376));
+}
+
+struct MaskSmem {
+  uint8_t E[ES][ES];
+  uint8_t D[DMAX][DMAX];
+  float h[DMAX][TS];
+  uint8_t S[5440];
+};
+
+template <int R>
+__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int i, int prev, int x0, int y0) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int Ti = TS >> i, DN = Ti + 2 * R, bs = 1 << i;
+  const int q0x = x0 >> i, q0y = y0 >> i;
+  const int Wi = m.Wi[i], Hi = m.Hi[i];
+  float g[2 * R + 1];
+#pragma unroll
+  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[i][t];
+  // D_i over the tile and its R halo; E outside the image is staged as 0
+  for (int r = ty; r < DN; r += 8) {
+    const int qy = q0y - R + r;
+    for (int c = tx; c < DN; c += 32) {
+      const int qx = q0x - R + c;
+      uint8_t v = 0;
+      if (qx >= 0 && qx < Wi && qy >= 0 && qy < Hi) {
+        const int ey = qy * bs - (y0 - MG), ex = qx * bs - (x0 - MG);
+        for (int by = 0; by < bs; ++by)
+          for (int bx = 0; bx < bs; ++bx) v |= sm.E[ey + by][ex + bx];
+      }
+      sm.D[r][c] = v;
+    }
+  }
+  __syncthreads();
+  // horizontal pass: with D in {0,1}, fma(g, D, s) is s + g where D is set and s elsewhere
+  for (int r = ty; r < DN; r += 8) {
+    for (int c = tx; c < Ti; c += 32) {
+      float s = 0.0f;
+#pragma unroll
+      for (int t = 0; t <= 2 * R; ++t)
+        if (sm.D[r][c + t]) s = s + g[t];
+      sm.h[r][c] = s;
+    }
+  }
+  __syncthreads();
+  // vertical pass, stencil, nesting, stores
+  uint8_t* Si = sm.S + s_offset(i);
+  const uint8_t* Sp = prev >= 0 ? sm.S + s_offset(prev) : nullptr;
+  const int f = prev >= 0 ? i - prev : 0;
+  const int Tp = prev >= 0 ? (TS >> prev) : 0;
+  for (int r = ty; r < Ti; r += 8) {
+    const int qy = q0y + r;
+    for (int c = tx; c < Ti; c += 32) {
+      const int qx = q0x + c;
+      float s = 0.0f;
+#pragma unroll
+      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[r + t][c], s);
+      uint8_t st = s > 0.0f ? 1 : 0;
+      if (!st && Sp) {
+        const int n = 1 << f;
+        for (int dy = 0; dy < n && !st; ++dy)
+          for (int dx = 0; dx < n; ++dx) st |= Sp[((r << f) + dy) * Tp + (c << f) + dx];
+      }
+      const bool inside = qx < Wi && qy < Hi;
+      Si[r * Ti + c] = inside ? st : 0;
+      if (inside) {
+        m.alpha[i][(size_t)qy * Wi + qx] = s;
+        m.stencil[i][(size_t)qy * Wi + qx] = st;
       }
     }
-    return;
-  }
-  const int R = m.R;
-  const int DX = MTX + 2 * R, DY = MTY + 2 * R;
-  const int bs = 1 << m.level;
-  for (int k = tid; k < DX * DY; k += blockDim.x) {
-    const int ly = k / DX, lx = k - ly * DX;
-    const int qx = tx0 - R + lx, qy = ty0 - R + ly;
-    float v = 0.0f;
-    if (qx >= 0 && qx < Wi && qy >= 0 && qy < Hi) {
-      const int xa = qx * bs, ya = qy * bs;
-      const int xb = min(xa + bs, W), yb = min(ya + bs, H);
-      uint8_t mx = 0;
-      for (int y = ya; y < yb; ++y)
-        for (int x = xa; x < xb; ++x) mx |= __ldg(E + (size_t)y * W + x);
-      v = mx ? 1.0f : 0.0f;
-    }
-    sD[ly][lx] = v;
-  }
-  __syncthreads();
-  for (int k = tid; k < DY * MTX; k += blockDim.x) {
-    const int ly = k / MTX, lx = k - ly * MTX;
-    float s = 0.0f;
-    for (int t = 0; t <= 2 * R; ++t) s = s + m.g[t] * sD[ly][lx + t];
-    sh[ly][lx] = s;
-  }
-  __syncthreads();
-  for (int k = tid; k < MTX * MTY; k += blockDim.x) {
-    const int ly = k / MTX, lx = k - ly * MTX;
-    const int qx = tx0 + lx, qy = ty0 + ly;
-    if (qx >= Wi || qy >= Hi) continue;
-    float s = 0.0f;
-    for (int t = 0; t <= 2 * R; ++t) s = s + m.g[t] * sh[ly + t][lx];
-    uint8_t st = s > 0.0f ? 1 : 0;
-    if (!st && m.prev) {
-      const int f = 1 << m.prev_shift;
-      const int xa = qx * f, ya = qy * f;
-      const int xb = min(xa + f, m.prev_W), yb = min(ya + f, m.prev_H);
-      for (int y = ya; y < yb && !st; ++y)
-        for (int x = xa; x < xb; ++x) st |= __ldg(m.prev + (size_t)y * m.prev_W + x);
-    }
-    m.alpha[(size_t)qy * Wi + qx] = s;
-    m.stencil[(size_t)qy * Wi + qx] = st;
   }
 }
 
-// Which (slot, chunk-in-level) does this block own?
+__global__ void __launch_bounds__(MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
+  __shared__ MaskSmem sm;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
+  const int W = m.W, H = m.H;
+  // stage the edge image of the tile + margin (zero outside the image)
+  if ((W & 3) == 0) {
+    for (int r = ty; r < ES; r += 8) {
+      const int y = y0 - MG + r;
+      for (int c = tx * 4; c < ES; c += 128) {
+        const int x = x0 - MG + c;  // a multiple of 4, and W is one: the group is all in or all out
+        uchar4 v = make_uchar4(0, 0, 0, 0);
+        if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uchar4*>(E + (size_t)y * W + x));
+        *reinterpret_cast<uchar4*>(&sm.E[r][c]) = v;
+      }
+    }
+  } else {
+    for (int r = ty; r < ES; r += 8) {
+      const int y = y0 - MG + r;
+      for (int c = tx; c < ES; c += 32) {
+        const int x = x0 - MG + c;
+        sm.E[r][c] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(E + (size_t)y * W + x) : 0;
+      }
+    }
+  }
+  __syncthreads();
+  int prev = -1;
+  for (int i = 0; i < m.L; ++i) {
+    const int mode = m.mode[i];
+    if (mode == 0) {
+      switch (m.R[i]) {
+        case 1: blur_level<1>(m, sm, i, prev, x0, y0); break;
+        case 2: blur_level<2>(m, sm, i, prev, x0, y0); break;
+        case 3: blur_level<3>(m, sm, i, prev, x0, y0); break;
+        case 4: blur_level<4>(m, sm, i, prev, x0, y0); break;
+        case 5: blur_level<5>(m, sm, i, prev, x0, y0); break;
+        default: blur_level<6>(m, sm, i, prev, x0, y0); break;
+      }
+    } else {
+      const int Ti = TS >> i, q0x = x0 >> i, q0y = y0 >> i;
+      const float av = mode == 1 ? 1.0f : 0.0f;
+      const uint8_t sv = mode == 1 ? 1 : 0;
+      uint8_t* Si = sm.S + s_offset(i);
+      for (int r = ty; r < Ti; r += 8) {
+        for (int c = tx; c < Ti; c += 32) {
+          const int qx = q0x + c, qy = q0y + r;
+          const bool inside = qx < m.Wi[i] && qy < m.Hi[i];
+          Si[r * Ti + c] = inside ? sv : 0;
+          if (inside && m.alpha[i]) {
+            m.alpha[i][(size_t)qy * m.Wi[i] + qx] = av;
+            m.stencil[i][(size_t)qy * m.Wi[i] + qx] = sv;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (mode != 2) prev = i;
+  }
+  if (m.label) {
+    for (int r = ty; r < TS; r += 8) {
+      const int y = y0 + r;
+      if (y >= H) break;
+      for (int c = tx; c < TS; c += 32) {
+        const int x = x0 + c;
+        if (x >= W) break;
+        uint8_t lab = 0xFF;
+        for (int i = 0; i < m.L; ++i) {
+          if (m.mode[i] == 2) continue;
+          const int Ti = TS >> i;
+          if (sm.S[s_offset(i) + (r >> i) * Ti + (c >> i)]) {
+            lab = (uint8_t)i;
+            break;
+          }
+        }
+        m.label[(size_t)y * W + x] = lab;
+      }
+    }
+  }
+}
+
+// Which level slot does this block serve?
 __device__ __forceinline__ int slot_of(const CompactParams& p, int b) {
   int l = 0;
   while (l + 1 < p.nlev && b >= p.chunk_begin[l + 1]) ++l;
@@ -97,29 +199,25 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   uint32_t t = 0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < COMPACT_THREADS / 32; ++w) t += red[w];
-    red[COMPACT_THREADS / 32] = t;
-  }
-  __syncthreads();
-  t = red[COMPACT_THREADS / 32];
+#pragma unroll
+  for (int w = 0; w < COMPACT_THREADS / 32; ++w) t += red[w];
   __syncthreads();
   return t;
 }
 
 __global__ void __launch_bounds__(COMPACT_THREADS) compact_count_kernel(CompactParams p) {
-  __shared__ uint32_t red[COMPACT_THREADS / 32 + 1];
+  __shared__ uint32_t red[COMPACT_THREADS / 32];
   const int l = slot_of(p, blockIdx.x);
   const int c = blockIdx.x - p.chunk_begin[l];
-  const size_t n = (size_t)p.Wi[l] * p.Hi[l];
+  const uint32_t n = (uint32_t)p.Wi[l] * (uint32_t)p.Hi[l];
   const uint8_t* S = p.stencil[l];
-  const size_t base = (size_t)c * COMPACT_CHUNK + (size_t)threadIdx.x * (COMPACT_CHUNK / COMPACT_THREADS);
+  const uint32_t base = (uint32_t)c * COMPACT_CHUNK + threadIdx.x * (COMPACT_CHUNK / COMPACT_THREADS);
   uint32_t cnt = 0;
   if (base + 16 <= n && ((reinterpret_cast<uintptr_t>(S + base) & 15) == 0)) {
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(S + base));
     cnt = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);  // bytes are 0 or 1
   } else {
-    for (size_t k = base; k < base + 16 && k < n; ++k) cnt += S[k] ? 1u : 0u;
+    for (uint32_t k = base; k < base + 16 && k < n; ++k) cnt += S[k] ? 1u : 0u;
   }
   const uint32_t tot = block_sum(cnt, red);
   if (threadIdx.x == 0) p.chunk_counts[blockIdx.x] = tot;
@@ -128,7 +226,7 @@ __global__ void __launch_bounds__(COMPACT_THREADS) compact_count_kernel(CompactP
 }
 
 __global__ void __launch_bounds__(COMPACT_THREADS) compact_scatter_kernel(CompactParams p) {
-  __shared__ uint32_t red[COMPACT_THREADS / 32 + 1];
+  __shared__ uint32_t red[COMPACT_THREADS / 32];
   __shared__ uint32_t wsum[COMPACT_THREADS / 32];
   const int l = slot_of(p, blockIdx.x);
   const int c0 = p.chunk_begin[l];
@@ -136,63 +234,44 @@ __global__ void __launch_bounds__(COMPACT_THREADS) compact_scatter_kernel(Compac
   // exclusive prefix of this chunk within its level
   uint32_t part = 0;
   for (int k = c0 + threadIdx.x; k < (int)blockIdx.x; k += COMPACT_THREADS) part += p.chunk_counts[k];
-  uint32_t offset = block_sum(part, red);
-  const int Wi = p.Wi[l];
-  const size_t n = (size_t)Wi * p.Hi[l];
+  const uint32_t offset = block_sum(part, red);
+  const uint32_t Wi = (uint32_t)p.Wi[l];
+  const uint32_t n = Wi * (uint32_t)p.Hi[l];
   const uint8_t* S = p.stencil[l];
   uint32_t* list = p.list[l];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const size_t base = (size_t)c * COMPACT_CHUNK;
-  for (int round = 0; round < COMPACT_CHUNK / COMPACT_THREADS; ++round) {
-    const size_t idx = base + (size_t)round * COMPACT_THREADS + threadIdx.x;
+  constexpr int PER_WARP = COMPACT_CHUNK / (COMPACT_THREADS / 32);  // 512
+  const uint32_t wbase = (uint32_t)c * COMPACT_CHUNK + warp * PER_WARP;
+  // each warp counts its 512 texels, then writes them after the block-level offsets
+  uint32_t mine = 0;
+#pragma unroll 4
+  for (int r = 0; r < PER_WARP / 32; ++r) {
+    const uint32_t idx = wbase + r * 32 + lane;
+    mine += __popc(__ballot_sync(0xffffffffu, idx < n && S[idx] != 0));
+  }
+  if (lane == 0) wsum[warp] = mine;
+  __syncthreads();
+  uint32_t pos = offset;
+  for (int w = 0; w < warp; ++w) pos += wsum[w];
+  for (int r = 0; r < PER_WARP / 32; ++r) {
+    const uint32_t idx = wbase + r * 32 + lane;
     const bool set = idx < n && S[idx] != 0;
     const uint32_t bal = __ballot_sync(0xffffffffu, set);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    uint32_t before = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < COMPACT_THREADS / 32; ++w) {
-      const uint32_t s = wsum[w];
-      before += (w < warp) ? s : 0u;
-      total += s;
-    }
     if (set) {
-      const uint32_t pos = offset + before + __popc(bal & ((1u << lane) - 1u));
-      const uint32_t y = (uint32_t)(idx / Wi), x = (uint32_t)(idx - (size_t)y * Wi);
-      list[pos] = (y << 16) | x;
+      const uint32_t y = idx / Wi, x = idx - y * Wi;
+      list[pos + __popc(bal & ((1u << lane) - 1u))] = (y << 16) | x;
     }
-    offset += total;
-    __syncthreads();
+    pos += __popc(bal);
   }
-  if (threadIdx.x == 0 && (int)blockIdx.x == p.chunk_begin[l + 1] - 1) p.counts[p.level_of[l]] = offset;
-}
-
-struct LabelParams {
-  int nlev;
-  int level[MRR_MAX_LEVELS];
-  const uint8_t* stencil[MRR_MAX_LEVELS];
-  int Wi[MRR_MAX_LEVELS];
-};
-
-__global__ void label_kernel(LabelParams lp, uint8_t* __restrict__ label, int W, int H) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
-  uint8_t lab = 0xFF;
-  for (int k = 0; k < lp.nlev; ++k) {
-    const int i = lp.level[k];
-    if (__ldg(lp.stencil[k] + (size_t)(y >> i) * lp.Wi[k] + (x >> i))) {
-      lab = (uint8_t)i;
-      break;
-    }
-  }
-  label[(size_t)y * W + x] = lab;
+  if (warp == COMPACT_THREADS / 32 - 1 && lane == 0 && (int)blockIdx.x == p.chunk_begin[l + 1] - 1)
+    p.counts[p.level_of[l]] = pos;
 }
 
 }  // namespace
 
-cudaError_t launch_mask_level(const MaskLevel& m, const uint8_t* E, int W, int H, cudaStream_t s) {
-  dim3 grid((m.Wi + MTX - 1) / MTX, (m.Hi + MTY - 1) / MTY);
-  mask_level_kernel<<<grid, 256, 0, s>>>(m, E, W, H);
+cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s) {
+  dim3 grid((m.W + TS - 1) / TS, (m.H + TS - 1) / TS);
+  masks_kernel<<<grid, MTHREADS, 0, s>>>(m, E);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -206,21 +285,6 @@ cudaError_t launch_compact(const CompactParams& p, cudaStream_t s) {
     compact_scatter_kernel<<<nchunks, COMPACT_THREADS, 0, s>>>(p);
     count_launches(2);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_label(uint8_t* label, int W, int H, int nlev, const int* levels, const uint8_t* const* stencil,
-                         const int* Wi, cudaStream_t s) {
-  LabelParams lp;
-  lp.nlev = nlev;
-  for (int k = 0; k < nlev; ++k) {
-    lp.level[k] = levels[k];
-    lp.stencil[k] = stencil[k];
-    lp.Wi[k] = Wi[k];
-  }
-  dim3 block(64, 4), grid((W + 63) / 64, (H + 3) / 4);
-  label_kernel<<<grid, block, 0, s>>>(lp, label, W, H);
-  count_launches(1);
   return cudaGetLastError();
 }
 

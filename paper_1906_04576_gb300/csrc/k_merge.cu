@@ -30,63 +30,77 @@ template <> __device__ __forceinline__ float3 load_c<__half>(const void* c, size
   return make_float3(__low2float(xy), __high2float(xy), __low2float(zw));
 }
 
+// Blend of one level into the composite c (Eq. (1)); `first` = the coarsest level,
+// which initialises c.  Level coordinate of pixel x: u = (x - o_i) / 2^i, whose floor and
+// fraction are (x - o_i) >> i and ((x - o_i) & (2^i - 1)) * 2^-i exactly.
+template <typename CT, int C>
+__device__ __forceinline__ void blend_level(const MergeParams& p, int i, int x, int y, bool first, float& c0,
+                                            float& c1, float& c2) {
+  const int Wi = p.Wi[i], Hi = p.Hi[i];
+  int tx = x, ty = y, x0 = x, y0 = y;
+  float fx = 0.0f, fy = 0.0f;
+  if (i > 0) {
+    const int o = 1 << (i - 1), mask = (1 << i) - 1;
+    const float inv = __int_as_float((127 - i) << 23);  // 2^-i
+    tx = x - o;
+    ty = y - o;
+    x0 = tx >> i;
+    y0 = ty >> i;
+    fx = (float)(tx & mask) * inv;
+    fy = (float)(ty & mask) * inv;
+  }
+  const int xa = min(max(x0, 0), Wi - 1), xb = min(max(x0 + 1, 0), Wi - 1);
+  const int ya = min(max(y0, 0), Hi - 1), yb = min(max(y0 + 1, 0), Hi - 1);
+  const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
+  const int idx[4] = {ya * Wi + xa, ya * Wi + xb, yb * Wi + xa, yb * Wi + xb};
+  float ahat = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (w[k] != 0.0f) ahat = ahat + w[k] * __ldg(p.alpha[i] + idx[k]);
+  const float wa = p.weight[i] * ahat;
+  const float alpha = (1.0f < wa) ? 1.0f : wa;
+  if (!first && !(alpha > 0.0f)) return;
+  float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (w[k] == 0.0f || !__ldg(p.stencil[i] + idx[k])) continue;
+    const float3 v = load_c<CT>(p.c[i], idx[k], C);
+    n0 = n0 + w[k] * v.x;
+    if (C == 4) {
+      n1 = n1 + w[k] * v.y;
+      n2 = n2 + w[k] * v.z;
+    }
+    den = den + w[k];
+  }
+  if (den != 1.0f) {  // x / 1 is x: the division only matters when a tap was dropped
+    n0 = n0 / den;
+    if (C == 4) {
+      n1 = n1 / den;
+      n2 = n2 / den;
+    }
+  }
+  if (first) {
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    return;
+  }
+  const float om = 1.0f - alpha;
+  c0 = n0 * alpha + c0 * om;
+  if (C == 4) {
+    c1 = n1 * alpha + c1 * om;
+    c2 = n2 * alpha + c2 * om;
+  }
+}
+
 template <typename CT, int C>
 __global__ void __launch_bounds__(256) merge_kernel(MergeParams p, float* __restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= p.W || y >= p.H) return;
   float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  bool first = true;
-  for (int i = p.L - 1; i >= 0; --i) {
-    if (!p.enabled[i]) continue;
-    const int Wi = p.Wi[i], Hi = p.Hi[i];
-    const float scale = (float)(1 << i);
-    const int o = i == 0 ? 0 : (1 << (i - 1));
-    const float ux = (float)(x - o) / scale, uy = (float)(y - o) / scale;
-    const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
-    const float fx = ux - (float)x0, fy = uy - (float)y0;
-    const int xs[2] = {min(max(x0, 0), Wi - 1), min(max(x0 + 1, 0), Wi - 1)};
-    const int ys[2] = {min(max(y0, 0), Hi - 1), min(max(y0 + 1, 0), Hi - 1)};
-    const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
-    size_t idx[4];
-    idx[0] = (size_t)ys[0] * Wi + xs[0];
-    idx[1] = (size_t)ys[0] * Wi + xs[1];
-    idx[2] = (size_t)ys[1] * Wi + xs[0];
-    idx[3] = (size_t)ys[1] * Wi + xs[1];
-    float ahat = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (w[k] != 0.0f) ahat = ahat + w[k] * __ldg(p.alpha[i] + idx[k]);
-    const float wa = p.weight[i] * ahat;
-    const float alpha = (1.0f < wa) ? 1.0f : wa;
-    if (!first && !(alpha > 0.0f)) continue;
-    float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (w[k] == 0.0f || !__ldg(p.stencil[i] + idx[k])) continue;
-      const float3 v = load_c<CT>(p.c[i], idx[k], C);
-      n0 = n0 + w[k] * v.x;
-      if (C == 4) {
-        n1 = n1 + w[k] * v.y;
-        n2 = n2 + w[k] * v.z;
-      }
-      den = den + w[k];
-    }
-    if (first) {
-      c0 = n0 / den;
-      if (C == 4) {
-        c1 = n1 / den;
-        c2 = n2 / den;
-      }
-      first = false;
-      continue;
-    }
-    const float om = 1.0f - alpha;
-    c0 = (n0 / den) * alpha + c0 * om;
-    if (C == 4) {
-      c1 = (n1 / den) * alpha + c1 * om;
-      c2 = (n2 / den) * alpha + c2 * om;
-    }
-  }
+  blend_level<CT, C>(p, p.L - 1, x, y, true, c0, c1, c2);
+  for (int i = p.L - 2; i >= 0; --i)
+    if (p.enabled[i]) blend_level<CT, C>(p, i, x, y, false, c0, c1, c2);
   const size_t o = (size_t)y * p.W + x;
   if (C == 4)
     reinterpret_cast<float4*>(out)[o] = make_float4(c0, c1, c2, 0.0f);

@@ -3,12 +3,15 @@
 //
 // shade_levels_kernel: a persistent grid strides over the concatenation of the work
 //   lists of one or more levels (their lengths are read on the device, so the launch
-//   needs no host synchronisation).  Consecutive lanes take consecutive list entries,
-//   i.e. neighbouring texels of one row, so the gathers of one sample index land close
-//   together and every lane has real work -- the GPU counterpart of the stencil test.
-// shade_full_kernel: one thread per pixel over 32x8 tiles.
-// Both evaluate the same effect function at the same full-resolution pixel, so a
-// level texel's value equals full-resolution shading at its sample pixel bit for bit.
+//   needs no host synchronisation).  Consecutive lane groups take consecutive list
+//   entries, i.e. neighbouring texels of one row, so the gathers of one sample index land
+//   close together and every lane has real work -- the GPU counterpart of the stencil
+//   test.  For SSAO, SPLIT lanes share a texel and split its samples (the occlusion count
+//   is an integer, so the split is exact); SSM and SSGI accumulate floats in sample order
+//   and use one lane per texel.
+// shade_full_kernel: one lane group per pixel over 2-D tiles of 8 rows.
+// Both evaluate the same effect function at the same full-resolution pixel, so a level
+// texel's value equals full-resolution shading at its sample pixel bit for bit.
 #include "mrr_internal.cuh"
 #include "shade_common.cuh"
 
@@ -18,14 +21,15 @@ namespace {
 
 constexpr int SHADE_THREADS = 256;
 
-template <int EFFECT, typename NT, typename SMT>
-__device__ __forceinline__ float3 effect_at(const ShadeParams& p, const FrameIn& in, int x, int y) {
+template <int EFFECT, typename NT, typename SMT, int SPLIT>
+__device__ __forceinline__ float3 effect_at(const ShadeParams& p, const FrameIn& in, int x, int y, bool valid) {
   if (EFFECT == MRR_SSAO) {
-    return make_float3(ssao_at<NT>(p, in.depth, (const NT*)in.normal, x, y), 0.f, 0.f);
+    return make_float3(ssao_at<NT, SPLIT>(p, in.depth, (const NT*)in.normal, x, y, valid), 0.f, 0.f);
   } else if (EFFECT == MRR_SSM) {
-    return make_float3(ssm_at<SMT>(p, in.depth, (const SMT*)in.smap, x, y), 0.f, 0.f);
+    return valid ? make_float3(ssm_at<SMT>(p, in.depth, (const SMT*)in.smap, x, y), 0.f, 0.f)
+                 : make_float3(0.f, 0.f, 0.f);
   } else {
-    return ssgi_at<NT>(p, in.depth, (const NT*)in.normal, in.color, x, y);
+    return valid ? ssgi_at<NT>(p, in.depth, (const NT*)in.normal, in.color, x, y) : make_float3(0.f, 0.f, 0.f);
   }
 }
 
@@ -51,47 +55,110 @@ __device__ __forceinline__ void store_value(void* c, size_t i, float3 v, bool ha
   }
 }
 
-template <int EFFECT, typename NT, typename SMT>
-__global__ void __launch_bounds__(SHADE_THREADS) shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv,
+template <int EFFECT, typename NT, typename SMT, int SPLIT>
+__global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv,
                                                                      int half_store) {
-  uint32_t pre[MRR_MAX_LEVELS + 1];
-  pre[0] = 0;
-  for (int k = 0; k < lv.nlev; ++k)
-    pre[k + 1] = pre[k] + min(__ldg(lv.counts + lv.level[k]), (uint32_t)lv.Wi[k] * (uint32_t)lv.Hi[k]);
-  const uint32_t total = pre[lv.nlev];
+  // per-level descriptors in shared memory (indexed by a runtime level slot)
+  __shared__ uint32_t s_pre[MRR_MAX_LEVELS + 1];
+  __shared__ const uint32_t* s_list[MRR_MAX_LEVELS];
+  __shared__ void* s_c[MRR_MAX_LEVELS];
+  __shared__ int s_lvl[MRR_MAX_LEVELS], s_W[MRR_MAX_LEVELS], s_H[MRR_MAX_LEVELS];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    s_pre[0] = 0;
+#pragma unroll
+    for (int k = 0; k < MRR_MAX_LEVELS; ++k) {
+      if (k >= lv.nlev) break;
+      acc += min(__ldg(lv.counts + lv.level[k]), (uint32_t)lv.Wi[k] * (uint32_t)lv.Hi[k]);
+      s_pre[k + 1] = acc;
+      s_list[k] = lv.list[k];
+      s_c[k] = lv.c[k];
+      s_lvl[k] = lv.level[k];
+      s_W[k] = lv.Wi[k];
+      s_H[k] = lv.Hi[k];
+    }
+  }
+  __syncthreads();
+  const int nlev = lv.nlev;
+  const uint32_t total = s_pre[nlev];
+  const uint32_t lanes = total * SPLIT;
   const int W = p.v.W, H = p.v.H;
-  for (uint32_t g = blockIdx.x * SHADE_THREADS + threadIdx.x; g < total; g += gridDim.x * SHADE_THREADS) {
-    int k = 0;
-    while (g >= pre[k + 1]) ++k;
-    const int i = lv.level[k];
-    const uint32_t e = __ldg(lv.list[k] + (g - pre[k]));
-    const int qx = (int)(e & 0xFFFFu), qy = (int)(e >> 16);
-    if (qx >= lv.Wi[k] || qy >= lv.Hi[k]) continue;  // not a texel of this level
-    const int o = i == 0 ? 0 : (1 << (i - 1));
-    const int x = min((qx << i) + o, W - 1), y = min((qy << i) + o, H - 1);
-    const float3 v = effect_at<EFFECT, NT, SMT>(p, in, x, y);
-    store_value<EFFECT>(lv.c[k], (size_t)qy * lv.Wi[k] + qx, v, half_store != 0);
+  const int sub = threadIdx.x & (SPLIT - 1);
+  for (uint32_t base = blockIdx.x * SHADE_THREADS; base < lanes; base += gridDim.x * SHADE_THREADS) {
+    const uint32_t g = (base + threadIdx.x) / SPLIT;
+    bool valid = g < total;
+    int k = 0, x = 0, y = 0, qx = 0, qy = 0;
+    if (valid) {
+      while (k + 1 < nlev && g >= s_pre[k + 1]) ++k;
+      const int i = s_lvl[k];
+      const uint32_t e = __ldg(s_list[k] + (g - s_pre[k]));
+      qx = (int)(e & 0xFFFFu);
+      qy = (int)(e >> 16);
+      valid = qx < s_W[k] && qy < s_H[k];  // skip anything that is not a texel of the level
+      const int o = i == 0 ? 0 : (1 << (i - 1));
+      x = min((qx << i) + o, W - 1);
+      y = min((qy << i) + o, H - 1);
+    }
+    const float3 v = effect_at<EFFECT, NT, SMT, SPLIT>(p, in, x, y, valid);
+    if (valid && sub == 0) store_value<EFFECT>(s_c[k], (size_t)qy * s_W[k] + qx, v, half_store != 0);
   }
 }
 
-template <int EFFECT, typename NT, typename SMT>
-__global__ void __launch_bounds__(256) shade_full_kernel(ShadeParams p, FrameIn in, float* __restrict__ out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= p.v.W || y >= p.v.H) return;
-  const float3 v = effect_at<EFFECT, NT, SMT>(p, in, x, y);
-  store_value<EFFECT>(out, (size_t)y * p.v.W + x, v, false);
+template <int EFFECT, typename NT, typename SMT, int SPLIT>
+__global__ void __launch_bounds__(256, 2) shade_full_kernel(ShadeParams p, FrameIn in, float* __restrict__ out) {
+  // block = 32 x 8 lanes; a warp row covers 32 / SPLIT consecutive pixels
+  const int x = blockIdx.x * (32 / SPLIT) + (int)threadIdx.x / SPLIT;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool valid = x < p.v.W && y < p.v.H;
+  const float3 v = effect_at<EFFECT, NT, SMT, SPLIT>(p, in, valid ? x : 0, valid ? y : 0, valid);
+  if (valid && (threadIdx.x & (SPLIT - 1)) == 0) store_value<EFFECT>(out, (size_t)y * p.v.W + x, v, false);
 }
 
-template <int EFFECT, typename NT, typename SMT>
+template <int EFFECT, typename NT, typename SMT, int SPLIT>
 void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid,
                      cudaStream_t s) {
-  shade_levels_kernel<EFFECT, NT, SMT><<<grid, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
+  shade_levels_kernel<EFFECT, NT, SMT, SPLIT><<<grid, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
 }
 
-template <int EFFECT, typename NT, typename SMT>
+template <int EFFECT, typename NT, typename SMT, int SPLIT>
 void launch_full_t(const ShadeParams& p, const FrameIn& in, float* out, cudaStream_t s) {
-  dim3 block(32, 8), grid((p.v.W + 31) / 32, (p.v.H + 7) / 8);
-  shade_full_kernel<EFFECT, NT, SMT><<<grid, block, 0, s>>>(p, in, out);
+  dim3 block(32, 8), grid((p.v.W + 32 / SPLIT - 1) / (32 / SPLIT), (p.v.H + 7) / 8);
+  shade_full_kernel<EFFECT, NT, SMT, SPLIT><<<grid, block, 0, s>>>(p, in, out);
+}
+
+template <typename NT, typename SMT>
+void levels_dispatch(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid,
+                     int split, cudaStream_t s) {
+  switch (p.effect) {
+    case MRR_SSAO:
+      if (split >= 4) launch_levels_t<MRR_SSAO, NT, SMT, 4>(p, in, lv, half_store, grid, s);
+      else if (split == 2) launch_levels_t<MRR_SSAO, NT, SMT, 2>(p, in, lv, half_store, grid, s);
+      else launch_levels_t<MRR_SSAO, NT, SMT, 1>(p, in, lv, half_store, grid, s);
+      break;
+    case MRR_SSM:
+      launch_levels_t<MRR_SSM, NT, SMT, 1>(p, in, lv, half_store, grid, s);
+      break;
+    default:
+      launch_levels_t<MRR_SSGI, NT, SMT, 1>(p, in, lv, half_store, grid, s);
+      break;
+  }
+}
+
+template <typename NT, typename SMT>
+void full_dispatch(const ShadeParams& p, const FrameIn& in, float* out, int split, cudaStream_t s) {
+  switch (p.effect) {
+    case MRR_SSAO:
+      if (split >= 4) launch_full_t<MRR_SSAO, NT, SMT, 4>(p, in, out, s);
+      else if (split == 2) launch_full_t<MRR_SSAO, NT, SMT, 2>(p, in, out, s);
+      else launch_full_t<MRR_SSAO, NT, SMT, 1>(p, in, out, s);
+      break;
+    case MRR_SSM:
+      launch_full_t<MRR_SSM, NT, SMT, 1>(p, in, out, s);
+      break;
+    default:
+      launch_full_t<MRR_SSGI, NT, SMT, 1>(p, in, out, s);
+      break;
+  }
 }
 
 }  // namespace
@@ -107,7 +174,7 @@ int shade_grid_blocks() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shade_levels_kernel<MRR_SSAO, float4, float>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shade_levels_kernel<MRR_SSAO, float4, float, 1>,
                                                   SHADE_THREADS, 0);
     if (sms <= 0) sms = 1;
     if (per_sm <= 0) per_sm = 1;
@@ -117,42 +184,17 @@ int shade_grid_blocks() {
 }
 
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
-                                int grid, cudaStream_t s) {
-  const bool h = precision == MRR_FP16;
-  switch (p.effect) {
-    case MRR_SSAO:
-      if (h) launch_levels_t<MRR_SSAO, half4, __half>(p, in, lv, 1, grid, s);
-      else launch_levels_t<MRR_SSAO, float4, float>(p, in, lv, 0, grid, s);
-      break;
-    case MRR_SSM:
-      if (h) launch_levels_t<MRR_SSM, half4, __half>(p, in, lv, 1, grid, s);
-      else launch_levels_t<MRR_SSM, float4, float>(p, in, lv, 0, grid, s);
-      break;
-    default:
-      if (h) launch_levels_t<MRR_SSGI, half4, __half>(p, in, lv, 1, grid, s);
-      else launch_levels_t<MRR_SSGI, float4, float>(p, in, lv, 0, grid, s);
-      break;
-  }
+                                int grid, int split, cudaStream_t s) {
+  if (precision == MRR_FP16) levels_dispatch<half4, __half>(p, in, lv, 1, grid, split, s);
+  else levels_dispatch<float4, float>(p, in, lv, 0, grid, split, s);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, cudaStream_t s) {
-  const bool h = precision == MRR_FP16;
-  switch (p.effect) {
-    case MRR_SSAO:
-      if (h) launch_full_t<MRR_SSAO, half4, __half>(p, in, out, s);
-      else launch_full_t<MRR_SSAO, float4, float>(p, in, out, s);
-      break;
-    case MRR_SSM:
-      if (h) launch_full_t<MRR_SSM, half4, __half>(p, in, out, s);
-      else launch_full_t<MRR_SSM, float4, float>(p, in, out, s);
-      break;
-    default:
-      if (h) launch_full_t<MRR_SSGI, half4, __half>(p, in, out, s);
-      else launch_full_t<MRR_SSGI, float4, float>(p, in, out, s);
-      break;
-  }
+cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
+                              cudaStream_t s) {
+  if (precision == MRR_FP16) full_dispatch<half4, __half>(p, in, out, split, s);
+  else full_dispatch<float4, float>(p, in, out, split, s);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -70,15 +70,19 @@ struct EdgeParams {
   int ssm;
 };
 
-// Mask stage of one level.
-struct MaskLevel {
-  int level, Wi, Hi, R;
-  int mode;                 // 0 = blur, 1 = all ones (coarsest / forced), 2 = all zero (disabled)
-  float g[16];              // Gaussian taps k = -R..R
-  float* alpha;
-  uint8_t* stencil;
-  const uint8_t* prev;      // stencil of the previous enabled finer level, or null
-  int prev_W, prev_H, prev_shift;  // its size and log2 of the block ratio
+// Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
+// 1 = all ones (coarsest level or forced level 0), 2 = all zero (disabled).
+constexpr int MASK_TILE = 64;    // full-resolution pixels per CTA tile side
+constexpr int MASK_MARGIN = 24;  // halo of the staged edge image: max R_i 2^i over blurred levels
+struct MaskParams {
+  int W, H, L;
+  int mode[MRR_MAX_LEVELS];
+  int R[MRR_MAX_LEVELS];
+  float g[MRR_MAX_LEVELS][16];   // Gaussian taps k = -R..R
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  float* alpha[MRR_MAX_LEVELS];
+  uint8_t* stencil[MRR_MAX_LEVELS];
+  uint8_t* label;                // [H][W] or null
 };
 
 // Work-list compaction of all levels in one launch: level l owns chunks
@@ -120,13 +124,11 @@ struct MergeParams {
 // ---- launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s);
-cudaError_t launch_mask_level(const MaskLevel& m, const uint8_t* E, int W, int H, cudaStream_t s);
+cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s);
 cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
-cudaError_t launch_label(uint8_t* label, int W, int H, int nlev, const int* levels, const uint8_t* const* stencil,
-                         const int* Wi, cudaStream_t s);
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
-                                int grid, cudaStream_t s);
-cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out,
+                                int grid, int split, cudaStream_t s);
+cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
                               cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 

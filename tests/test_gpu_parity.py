@@ -252,6 +252,48 @@ def test_render_host_matches_device_path(mrr):
     mrr.mrr_destroy(ctx)
 
 
+def test_graph_replay_matches_direct_launches(mrr):
+    import torch
+    W, H = 220, 130
+    frames = [sg.gbuffer(s, W, H, 16, 4) for s in (1, 2)]
+    outs = {}
+    for no_graph in (0, 1):
+        cfg = make_cfg("ssao", 4, W, H, samples=32, no_graph=no_graph)
+        ctx = mrr.mrr_create(cfg)
+        res = []
+        for fr in frames + frames:      # new descriptor, new descriptor, then repeats
+            dev = mrr.upload_frame(fr)
+            out = mrr.alloc_output(ctx, W, H)
+            for _ in range(2):
+                mrr.mrr_render(ctx, dev, out)
+            torch.cuda.synchronize()
+            res.append(out.clone())
+        outs[no_graph] = res
+        mrr.mrr_destroy(ctx)
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    assert torch.equal(outs[0][0], outs[0][2]) and not torch.equal(outs[0][0], outs[0][1])
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_lane_split_does_not_change_results(mrr, lanes):
+    import torch
+    W, H = 150, 90
+    fr = sg.gbuffer(3, W, H, 12, 4)
+    cfg = make_cfg("ssao", 4, W, H, samples=64, lanes_per_texel=lanes, lanes_per_pixel=lanes)
+    ref = orc.render(fr, cfg, "f32")
+    full_ref = orc.shade_full(fr, cfg, "f32")[..., 0]
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    out, full = mrr.alloc_output(ctx, W, H), mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, out)
+    mrr.mrr_render_full(ctx, dev, full)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref["out"][..., 0]).max() <= TOL32
+    assert np.array_equal(full.cpu().numpy(), full_ref)
+    mrr.mrr_destroy(ctx)
+
+
 def test_frame_larger_than_context_is_rejected(mrr):
     W, H = 64, 64
     fr = sg.gbuffer(0, W, H, 4, 0)
