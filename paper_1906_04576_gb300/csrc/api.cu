@@ -45,6 +45,7 @@ struct mrr_ctx {
   mrr_gbuffer graph_key;
   float* graph_out = nullptr;
   uint64_t graph_replays = 0;
+  uint64_t graph_kernels = 0;
 };
 
 namespace {
@@ -333,7 +334,11 @@ mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStrea
     }
     if (!ctx->capture_stream) MRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     MRR_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    const uint64_t before = launch_counter().load();
     mrr_status st = render_launches(ctx, g, out, ctx->capture_stream);
+    // captured launches do not run: count them per replay instead
+    ctx->graph_kernels = launch_counter().load() - before;
+    launch_counter().fetch_sub(ctx->graph_kernels);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (st != MRR_OK) {
@@ -351,6 +356,7 @@ mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStrea
     ctx->graph_out = out;
   }
   MRR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, s));
+  count_launches((int)ctx->graph_kernels);
   ++ctx->graph_replays;
   return MRR_OK;
 }

@@ -1,8 +1,8 @@
 // k_masks.cu -- the per-level masks of Sec. 3.1 / Table 1, the stencil of Sec. 4.1 and
 // the dense work lists that replace the stencil test on the GPU.
 //
-// masks_kernel: ONE launch computes every level.  A CTA owns a 64x64 full-resolution
-//   tile (32x32 at level 1, 16x16 at level 2, ...) and stages the edge image of the tile
+// masks_kernel: ONE launch computes every level.  A CTA owns a 32x32 full-resolution
+//   tile (16x16 at level 1, 8x8 at level 2, ...) and stages the edge image of the tile
 //   plus a 24-pixel halo in shared memory once.  For each blurred level i it forms the
 //   downsampled edge image D_i (block maximum) over the tile and an R_i halo, blurs it
 //   horizontally then vertically (taps in ascending order, one fused multiply-add each,
@@ -23,23 +23,25 @@ namespace mrr {
 
 namespace {
 
-constexpr int TS = MASK_TILE;            // 64
+constexpr int TS = MASK_TILE;            // 32
 constexpr int MG = MASK_MARGIN;          // 24
-constexpr int ES = TS + 2 * MG;          // 112: staged edge image side
+constexpr int ES = TS + 2 * MG;          // 80: staged edge image side
 constexpr int MAXR = 6;
-constexpr int DMAX = TS + 2 * MAXR;      // 76: largest D region side (level 0)
+constexpr int DMAX = TS + 2 * MAXR;      // 44: largest D region side (level 0)
 constexpr int MTHREADS = 256;            // as 32 x 8
+constexpr int S_TOTAL = TS * TS + (TS / 2) * (TS / 2) + (TS / 4) * (TS / 4) + (TS / 8) * (TS / 8);
 
 __device__ __forceinline__ int s_offset(int i) {  // offset of level i's tile stencil in smem
-  // 64^2, 32^2, 16^2, 8^2 texels for levels 0..3
-  return i == 0 ? 0 : (i == 1 ? 4096 : (i == 2 ? 5120 : 5376));
+  int o = 0;
+  for (int k = 0; k < i; ++k) o += (TS >> k) * (TS >> k);
+  return o;
 }
 
 struct MaskSmem {
   uint8_t E[ES][ES];
   uint8_t D[DMAX][DMAX];
   float h[DMAX][TS];
-  uint8_t S[5440];
+  uint8_t S[S_TOTAL];
 };
 
 template <int R>

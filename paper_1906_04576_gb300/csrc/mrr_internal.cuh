@@ -72,7 +72,7 @@ struct EdgeParams {
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
 // 1 = all ones (coarsest level or forced level 0), 2 = all zero (disabled).
-constexpr int MASK_TILE = 64;    // full-resolution pixels per CTA tile side
+constexpr int MASK_TILE = 32;    // full-resolution pixels per CTA tile side
 constexpr int MASK_MARGIN = 24;  // halo of the staged edge image: max R_i 2^i over blurred levels
 struct MaskParams {
   int W, H, L;
