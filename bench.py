@@ -232,6 +232,7 @@ def main():
     ap.add_argument("--workload", default="ssao64_1080p")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip mrr_autotune (library defaults)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -286,6 +287,7 @@ def main():
         barrier()
         return [s.elapsed_time(e) for s, e in ev]
 
+    tuning = None if args.no_tune else mrr.mrr_autotune(ctx, dev, stream)
     render = lambda: mrr.mrr_render(ctx, dev, out, stream)
     render_full = lambda: mrr.mrr_render_full(ctx, dev, full, stream)
     for _ in range(args.warmup):
@@ -396,6 +398,7 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "api": "mrr_render_host (pinned host buffers, copies and sync inside)"},
             "gpu_launches": int(launches),
+            "tuning": tuning,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -202,6 +202,25 @@ mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, v
  * the result to out_host and synchronises the stream before returning. */
 mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* g_host, float* out_host, void* stream);
 
+/* Result of mrr_autotune: the settings chosen and the measured kernel times (ms). */
+typedef struct mrr_tuning {
+  int lanes_per_texel;      /* chosen split of a work-list texel's samples over lanes */
+  int grid_multiplier;      /* work-list kernel grid = multiplier x (SMs x resident CTAs per SM) */
+  int lanes_per_pixel;      /* chosen split for the full-resolution kernel */
+  float shade_levels_ms;    /* work-list shading kernel time with the chosen settings */
+  float shade_full_ms;      /* full-resolution kernel time with the chosen setting */
+  int candidates;           /* configurations timed */
+} mrr_tuning;
+
+/* Autotuner: times every supported (lanes_per_texel, grid_multiplier) pair of the
+ * work-list shading kernel and every lanes_per_pixel of the full-resolution kernel on
+ * this frame (median of 5 timed launches after 2 warm-up launches each, CUDA events on
+ * `stream`), keeps the fastest in the context (they change speed, never results) and
+ * reports them in *out (may be NULL).  Runs mrr_edges / mrr_masks into the context's
+ * pools first; synchronises `stream`.  Settings fixed in the config (non-zero
+ * lanes_per_texel / lanes_per_pixel) are kept. */
+mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tuning* out);
+
 /* Number of kernels this library has launched in this process (all contexts), for
  * accounting of GPU work in benchmarks. */
 uint64_t mrr_kernel_launches(void);

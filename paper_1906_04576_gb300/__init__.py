@@ -11,7 +11,7 @@ device memory and streams.  The functions carry the C names of include/mrr.h:
     mrr_render(ctx, frame, out)         mrr_render_full(ctx, frame, out)
     mrr_render_host(ctx, host_frame, out_host)
     mrr_level_dims(W, H, level)         mrr_last_error(ctx)
-    mrr_kernel_launches()
+    mrr_autotune(ctx, frame)            mrr_kernel_launches()
 
 Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
 ``python paper_1906_04576_gb300/_build.py``): there is no CPU fallback.
@@ -77,7 +77,15 @@ class mrr_levels(ctypes.Structure):
                 ("worklist", ctypes.c_void_p * 4), ("counts", ctypes.c_void_p), ("label", ctypes.c_void_p)]
 
 
+class mrr_tuning(ctypes.Structure):
+    _fields_ = [("lanes_per_texel", ctypes.c_int), ("grid_multiplier", ctypes.c_int),
+                ("lanes_per_pixel", ctypes.c_int), ("shade_levels_ms", ctypes.c_float),
+                ("shade_full_ms", ctypes.c_float), ("candidates", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
+_lib.mrr_autotune.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, ctypes.POINTER(mrr_tuning)]
+_lib.mrr_autotune.restype = ctypes.c_int
 _lib.mrr_level_dims.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)]
 _lib.mrr_create.argtypes = [ctypes.POINTER(mrr_config), ctypes.POINTER(_vp)]
@@ -338,6 +346,13 @@ def mrr_shade_levels(ctx: Context, frame: DeviceFrame, levels: Levels, c_list: l
     g, lv = frame.struct(), levels.struct()
     arr = (_vp * MAX_LEVELS)(*[(_ptr(c) if c is not None else None) for c in c_list])
     _check(ctx, _lib.mrr_shade_levels(ctx.handle, ctypes.byref(g), ctypes.byref(lv), arr, _stream(stream)))
+
+
+def mrr_autotune(ctx: Context, frame: DeviceFrame, stream=None) -> dict:
+    g = frame.struct()
+    t = mrr_tuning()
+    _check(ctx, _lib.mrr_autotune(ctx.handle, ctypes.byref(g), _stream(stream), ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in mrr_tuning._fields_}
 
 
 def mrr_kernel_launches() -> int:

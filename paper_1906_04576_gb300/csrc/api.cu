@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libmrr (include/mrr.h): argument validation, the host-side
 // constants of each stage and the launches.  No exception crosses the ABI; every
 // failure is a status code plus a message kept on the context.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -595,6 +596,107 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
 }
 
 uint64_t mrr_kernel_launches(void) { return mrr::launch_counter().load(); }
+
+mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tuning* out) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  if (g->width > ctx->pool_W || g->height > ctx->pool_H)
+    return fail(ctx, MRR_EINVAL, "frame exceeds the context's max size");
+  cudaStream_t s = (cudaStream_t)stream;
+  const mrr_config& c = ctx->cfg;
+  st = edges_impl(ctx, g, ctx->edges, s);
+  if (st != MRR_OK) return st;
+  mrr_levels lv = pool_levels(ctx, g->width, g->height);
+  st = masks_impl(ctx, ctx->edges, &lv, s);
+  if (st != MRR_OK) return st;
+  ShadeParams p = make_shade_params(ctx, *g);
+  ShadeLevels sl;
+  std::memset(&sl, 0, sizeof sl);
+  for (int i = 0; i < c.num_levels; ++i) {
+    if (!c.enabled[i]) continue;
+    const int k = sl.nlev++;
+    sl.level[k] = i;
+    sl.list[k] = ctx->worklist[i];
+    sl.c[k] = ctx->cbuf[i];
+    sl.Wi[k] = lv.width[i];
+    sl.Hi[k] = lv.height[i];
+  }
+  sl.counts = ctx->counts;
+  cudaEvent_t e0, e1;
+  MRR_CUDA(ctx, cudaEventCreate(&e0));
+  MRR_CUDA(ctx, cudaEventCreate(&e1));
+  auto median_ms = [&](auto&& launch) -> float {
+    float t[5];
+    for (int w = 0; w < 2; ++w) launch();
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e0, s);
+      launch();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    std::sort(t, t + 5);
+    return t[2];
+  };
+  const FrameIn in = make_frame_in(*g);
+  const bool ssao = c.effect == MRR_SSAO;
+  const int lanes_opts[3] = {1, 2, 4};
+  int best_lanes = ctx->split_texel, best_mult = 1, cand = 0;
+  float best = 1e30f;
+  for (int li = 0; li < 3; ++li) {
+    const int lanes = lanes_opts[li];
+    if (!ssao && lanes != 1) continue;
+    if (c.lanes_per_texel && lanes != c.lanes_per_texel) continue;
+    for (int mult = 1; mult <= 4; mult *= 2) {
+      const float ms = median_ms([&] {
+        launch_shade_levels(p, in, c.precision, sl, shade_grid_blocks() * mult, lanes, s);
+      });
+      ++cand;
+      if (ms < best) {
+        best = ms;
+        best_lanes = lanes;
+        best_mult = mult;
+      }
+    }
+  }
+  int best_pix = ctx->split_pixel;
+  float best_full = 1e30f;
+  float* tmp = nullptr;  // the full-resolution kernel's output while it is timed
+  MRR_CUDA(ctx, cudaMalloc(&tmp, (size_t)g->width * g->height * sizeof(float) * channels(c)));
+  for (int li = 0; li < 3; ++li) {
+    const int lanes = lanes_opts[li];
+    if (!ssao && lanes != 1) continue;
+    if (c.lanes_per_pixel && lanes != c.lanes_per_pixel) continue;
+    const float ms = median_ms([&] { launch_shade_full(p, in, c.precision, tmp, lanes, s); });
+    ++cand;
+    if (ms < best_full) {
+      best_full = ms;
+      best_pix = lanes;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  MRR_CUDA(ctx, cudaGetLastError());
+  ctx->split_texel = best_lanes;
+  ctx->split_pixel = best_pix;
+  ctx->shade_grid = shade_grid_blocks() * best_mult;
+  if (ctx->graph_exec) {  // the captured launches used the old settings
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  if (out) {
+    out->lanes_per_texel = best_lanes;
+    out->grid_multiplier = best_mult;
+    out->lanes_per_pixel = best_pix;
+    out->shade_levels_ms = best;
+    out->shade_full_ms = best_full;
+    out->candidates = cand;
+  }
+  return MRR_OK;
+}
 
 mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,
                               void* stream) {

@@ -81,43 +81,69 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   E[(size_t)y * W + x] = e;
 }
 
+// edges_direct_kernel: a lane owns a column of ER vertically adjacent pixels, so the
+// column's own depth/normal values (rows y0-1 .. y0+ER) are loaded once and shared as
+// up/down neighbours; only the left/right neighbours are extra loads.
+constexpr int ER = 4;
+
 template <typename NT>
 __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, const float* __restrict__ depth,
                                                                const NT* __restrict__ normal,
                                                                uint8_t* __restrict__ E) {
   const int W = p.v.W, H = p.v.H;
-  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const int i = y * W + x;
+  const int x = blockIdx.x * TX + threadIdx.x;
+  const int y0 = (blockIdx.y * TY + threadIdx.y) * ER;
+  if (x >= W || y0 >= H) return;
   const float farp = p.v.farp;
-  const float d = __ldg(depth + i);
-  uint8_t e = 0;
-  if (d < farp) {
-    const float3 n = load_normal(normal, i);
-    const bool has[4] = {x > 0, x < W - 1, y > 0, y < H - 1};
-    const int off[4] = {-1, 1, -W, W};
-    float dn[4];
+  // column values for rows y0-1 .. y0+ER (index r+1 for row y0+r)
+  float dc[ER + 2];
+  float3 nc[ER + 2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      dn[k] = has[k] ? __ldg(depth + i + off[k]) : 0.0f;
-      if (!has[k]) continue;
-      if (dn[k] >= farp) {  // sky neighbour
-        e = 1;
-        continue;
-      }
-      const float3 m = load_normal(normal, i + off[k]);
-      if (n.x * m.x + n.y * m.y + n.z * m.z < p.normal_cos) e = 1;
-    }
-    if (has[0] && has[1]) {
-      const float lap = (dn[0] + dn[1]) - 2.0f * d;
-      if (fabsf(lap) > p.depth_rel * d) e = 1;
-    }
-    if (has[2] && has[3]) {
-      const float lap = (dn[2] + dn[3]) - 2.0f * d;
-      if (fabsf(lap) > p.depth_rel * d) e = 1;
-    }
+  for (int r = -1; r <= ER; ++r) {
+    const int y = y0 + r;
+    const bool ok = y >= 0 && y < H;
+    dc[r + 1] = ok ? __ldg(depth + y * W + x) : 0.0f;
+    nc[r + 1] = ok ? load_normal(normal, y * W + x) : make_float3(0.f, 0.f, 0.f);
   }
-  E[i] = e;
+#pragma unroll
+  for (int r = 0; r < ER; ++r) {
+    const int y = y0 + r;
+    if (y >= H) break;
+    const int i = y * W + x;
+    const float d = dc[r + 1];
+    uint8_t e = 0;
+    if (d < farp) {
+      const float3 n = nc[r + 1];
+      const bool has[4] = {x > 0, x < W - 1, y > 0, y < H - 1};
+      float dn[4];
+      float3 nn[4];
+      dn[0] = has[0] ? __ldg(depth + i - 1) : 0.0f;
+      dn[1] = has[1] ? __ldg(depth + i + 1) : 0.0f;
+      dn[2] = dc[r];
+      dn[3] = dc[r + 2];
+      nn[2] = nc[r];
+      nn[3] = nc[r + 2];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!has[k]) continue;
+        if (dn[k] >= farp) {  // sky neighbour
+          e = 1;
+          continue;
+        }
+        const float3 m = k == 0 ? load_normal(normal, i - 1) : (k == 1 ? load_normal(normal, i + 1) : nn[k]);
+        if (n.x * m.x + n.y * m.y + n.z * m.z < p.normal_cos) e = 1;
+      }
+      if (has[0] && has[1]) {
+        const float lap = (dn[0] + dn[1]) - 2.0f * d;
+        if (fabsf(lap) > p.depth_rel * d) e = 1;
+      }
+      if (has[2] && has[3]) {
+        const float lap = (dn[2] + dn[3]) - 2.0f * d;
+        if (fabsf(lap) > p.depth_rel * d) e = 1;
+      }
+    }
+    E[i] = e;
+  }
 }
 
 }  // namespace
@@ -126,8 +152,9 @@ cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* no
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
   if (!p.ssm) {
-    if (half_normal) edges_direct_kernel<half4><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, E);
-    else edges_direct_kernel<float4><<<grid, block, 0, s>>>(p, depth, (const float4*)normal, E);
+    dim3 dgrid((p.v.W + TX - 1) / TX, (p.v.H + TY * ER - 1) / (TY * ER));
+    if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);
+    else edges_direct_kernel<float4><<<dgrid, block, 0, s>>>(p, depth, (const float4*)normal, E);
   } else if (half_normal) {
     if (half_smap)
       edges_kernel<half4, __half><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const __half*)smap, E);

@@ -31,80 +31,142 @@ constexpr int DMAX = TS + 2 * MAXR;      // 44: largest D region side (level 0)
 constexpr int MTHREADS = 256;            // as 32 x 8
 constexpr int S_TOTAL = TS * TS + (TS / 2) * (TS / 2) + (TS / 4) * (TS / 4) + (TS / 8) * (TS / 8);
 
-__device__ __forceinline__ int s_offset(int i) {  // offset of level i's tile stencil in smem
-  int o = 0;
-  for (int k = 0; k < i; ++k) o += (TS >> k) * (TS >> k);
-  return o;
-}
+template <int I> struct LevelShape {  // level I of a tile: side, smem stencil offset
+  static constexpr int T = TS >> I;
+  static constexpr int OFF = I == 0 ? 0 : LevelShape<I - 1>::OFF + (TS >> (I - 1)) * (TS >> (I - 1));
+};
+template <> struct LevelShape<-1> {
+  static constexpr int T = 0;
+  static constexpr int OFF = 0;
+};
 
 struct MaskSmem {
   uint8_t E[ES][ES];
-  uint8_t D[DMAX][DMAX];
-  float h[DMAX][TS];
+  uint8_t D[DMAX * DMAX];
+  float h[DMAX * TS];
   uint8_t S[S_TOTAL];
 };
 
-template <int R>
-__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int i, int prev, int x0, int y0) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int Ti = TS >> i, DN = Ti + 2 * R, bs = 1 << i;
-  const int q0x = x0 >> i, q0y = y0 >> i;
-  const int Wi = m.Wi[i], Hi = m.Hi[i];
+// Level I with blur radius R (both compile-time): D over the tile + R halo, the two
+// blur passes, the stencil with nesting from level P (P < 0: none), and the stores.
+template <int I, int R, int P>
+__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  constexpr int Ti = LevelShape<I>::T, DN = Ti + 2 * R, BS = 1 << I;
+  const int tid = threadIdx.x;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  const int Wi = m.Wi[I], Hi = m.Hi[I];
   float g[2 * R + 1];
 #pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[i][t];
-  // D_i over the tile and its R halo; E outside the image is staged as 0
-  for (int r = ty; r < DN; r += 8) {
-    const int qy = q0y - R + r;
-    for (int c = tx; c < DN; c += 32) {
-      const int qx = q0x - R + c;
-      uint8_t v = 0;
-      if (qx >= 0 && qx < Wi && qy >= 0 && qy < Hi) {
-        const int ey = qy * bs - (y0 - MG), ex = qx * bs - (x0 - MG);
-        for (int by = 0; by < bs; ++by)
-          for (int bx = 0; bx < bs; ++bx) v |= sm.E[ey + by][ex + bx];
-      }
-      sm.D[r][c] = v;
+  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[I][t];
+  // D_I over the tile and its R halo; E outside the image is staged as 0
+  for (int k = tid; k < DN * DN; k += MTHREADS) {
+    const int r = k / DN, c = k - r * DN;
+    const int qx = q0x - R + c, qy = q0y - R + r;
+    uint8_t v = 0;
+    if (qx >= 0 && qx < Wi && qy >= 0 && qy < Hi) {
+      const uint8_t* e = &sm.E[qy * BS - (y0 - MG)][qx * BS - (x0 - MG)];
+#pragma unroll
+      for (int by = 0; by < BS; ++by)
+#pragma unroll
+        for (int bx = 0; bx < BS; ++bx) v |= e[by * ES + bx];
     }
+    sm.D[k] = v;
   }
   __syncthreads();
   // horizontal pass: with D in {0,1}, fma(g, D, s) is s + g where D is set and s elsewhere
-  for (int r = ty; r < DN; r += 8) {
-    for (int c = tx; c < Ti; c += 32) {
-      float s = 0.0f;
+  for (int k = tid; k < DN * Ti; k += MTHREADS) {
+    const int r = k / Ti, c = k - r * Ti;
+    const uint8_t* d = &sm.D[r * DN + c];
+    float s = 0.0f;
 #pragma unroll
-      for (int t = 0; t <= 2 * R; ++t)
-        if (sm.D[r][c + t]) s = s + g[t];
-      sm.h[r][c] = s;
-    }
+    for (int t = 0; t <= 2 * R; ++t)
+      if (d[t]) s = s + g[t];
+    sm.h[k] = s;
   }
   __syncthreads();
   // vertical pass, stencil, nesting, stores
-  uint8_t* Si = sm.S + s_offset(i);
-  const uint8_t* Sp = prev >= 0 ? sm.S + s_offset(prev) : nullptr;
-  const int f = prev >= 0 ? i - prev : 0;
-  const int Tp = prev >= 0 ? (TS >> prev) : 0;
-  for (int r = ty; r < Ti; r += 8) {
-    const int qy = q0y + r;
-    for (int c = tx; c < Ti; c += 32) {
-      const int qx = q0x + c;
-      float s = 0.0f;
+  uint8_t* Si = sm.S + LevelShape<I>::OFF;
+  for (int k = tid; k < Ti * Ti; k += MTHREADS) {
+    const int r = k / Ti, c = k - r * Ti;
+    const int qx = q0x + c, qy = q0y + r;
+    float s = 0.0f;
 #pragma unroll
-      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[r + t][c], s);
-      uint8_t st = s > 0.0f ? 1 : 0;
-      if (!st && Sp) {
-        const int n = 1 << f;
-        for (int dy = 0; dy < n && !st; ++dy)
-          for (int dx = 0; dx < n; ++dx) st |= Sp[((r << f) + dy) * Tp + (c << f) + dx];
-      }
-      const bool inside = qx < Wi && qy < Hi;
-      Si[r * Ti + c] = inside ? st : 0;
-      if (inside) {
-        m.alpha[i][(size_t)qy * Wi + qx] = s;
-        m.stencil[i][(size_t)qy * Wi + qx] = st;
-      }
+    for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[(r + t) * Ti + c], s);
+    uint8_t st = s > 0.0f ? 1 : 0;
+    if (P >= 0) {
+      constexpr int F = P >= 0 ? I - P : 0, TP = P >= 0 ? LevelShape<(P >= 0 ? P : 0)>::T : 1;
+      const uint8_t* Sp = sm.S + LevelShape<(P >= 0 ? P : 0)>::OFF + (r << F) * TP + (c << F);
+#pragma unroll
+      for (int dy = 0; dy < (1 << F); ++dy)
+#pragma unroll
+        for (int dx = 0; dx < (1 << F); ++dx) st |= Sp[dy * TP + dx];
+    }
+    const bool inside = qx < Wi && qy < Hi;
+    Si[k] = inside ? st : 0;
+    if (inside) {
+      m.alpha[I][(size_t)qy * Wi + qx] = s;
+      m.stencil[I][(size_t)qy * Wi + qx] = st;
     }
   }
+  __syncthreads();
+}
+
+template <int I, int P>
+__device__ __forceinline__ void blur_dispatch(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  switch (m.R[I]) {
+    case 1: blur_level<I, 1, P>(m, sm, x0, y0); break;
+    case 2: blur_level<I, 2, P>(m, sm, x0, y0); break;
+    case 3: blur_level<I, 3, P>(m, sm, x0, y0); break;
+    case 4: blur_level<I, 4, P>(m, sm, x0, y0); break;
+    case 5: blur_level<I, 5, P>(m, sm, x0, y0); break;
+    default: blur_level<I, 6, P>(m, sm, x0, y0); break;
+  }
+}
+
+// Level I written as a constant (mode 1: a = 1, S = 1; mode 2: a = 0, S = 0).
+template <int I>
+__device__ __forceinline__ void fill_level(const MaskParams& m, MaskSmem& sm, int x0, int y0, int mode) {
+  constexpr int Ti = LevelShape<I>::T;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  const float av = mode == 1 ? 1.0f : 0.0f;
+  const uint8_t sv = mode == 1 ? 1 : 0;
+  uint8_t* Si = sm.S + LevelShape<I>::OFF;
+  for (int k = threadIdx.x; k < Ti * Ti; k += MTHREADS) {
+    const int r = k / Ti, c = k - r * Ti;
+    const int qx = q0x + c, qy = q0y + r;
+    const bool inside = qx < m.Wi[I] && qy < m.Hi[I];
+    Si[k] = inside ? sv : 0;
+    if (inside && m.alpha[I]) {
+      m.alpha[I][(size_t)qy * m.Wi[I] + qx] = av;
+      m.stencil[I][(size_t)qy * m.Wi[I] + qx] = sv;
+    }
+  }
+  __syncthreads();
+}
+
+// Level I, whose previous enabled finer level is P (-1: none).
+template <int I, int P>
+__device__ __forceinline__ void do_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  const int mode = m.mode[I];
+  if (mode == 0) blur_dispatch<I, P>(m, sm, x0, y0);
+  else fill_level<I>(m, sm, x0, y0, mode);
+}
+
+// The levels in order; blurred levels are 0..2 (the coarsest, at most 3, is a fill).
+// `prev` tracks the previous enabled level for nesting (disabled levels are skipped).
+__device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  do_level<0, -1>(m, sm, x0, y0);
+  if (m.L < 2) return;
+  const bool en0 = m.mode[0] != 2;
+  if (en0) do_level<1, 0>(m, sm, x0, y0);
+  else do_level<1, -1>(m, sm, x0, y0);
+  if (m.L < 3) return;
+  const bool en1 = m.mode[1] != 2;
+  if (en1) do_level<2, 1>(m, sm, x0, y0);
+  else if (en0) do_level<2, 0>(m, sm, x0, y0);
+  else do_level<2, -1>(m, sm, x0, y0);
+  if (m.L < 4) return;
+  fill_level<3>(m, sm, x0, y0, m.mode[3]);  // level 3 can only be the coarsest
 }
 
 __global__ void __launch_bounds__(MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
@@ -114,75 +176,36 @@ __global__ void __launch_bounds__(MTHREADS) masks_kernel(MaskParams m, const uin
   const int W = m.W, H = m.H;
   // stage the edge image of the tile + margin (zero outside the image)
   if ((W & 3) == 0) {
-    for (int r = ty; r < ES; r += 8) {
-      const int y = y0 - MG + r;
-      for (int c = tx * 4; c < ES; c += 128) {
-        const int x = x0 - MG + c;  // a multiple of 4, and W is one: the group is all in or all out
-        uchar4 v = make_uchar4(0, 0, 0, 0);
-        if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uchar4*>(E + (size_t)y * W + x));
-        *reinterpret_cast<uchar4*>(&sm.E[r][c]) = v;
-      }
+    constexpr int Q = ES / 4;
+    for (int k = threadIdx.x; k < ES * Q; k += MTHREADS) {
+      const int r = k / Q, c = (k - r * Q) * 4;
+      const int y = y0 - MG + r, x = x0 - MG + c;  // x and W multiples of 4: all 4 in or all out
+      uchar4 v = make_uchar4(0, 0, 0, 0);
+      if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uchar4*>(E + (size_t)y * W + x));
+      *reinterpret_cast<uchar4*>(&sm.E[r][c]) = v;
     }
   } else {
-    for (int r = ty; r < ES; r += 8) {
-      const int y = y0 - MG + r;
-      for (int c = tx; c < ES; c += 32) {
-        const int x = x0 - MG + c;
-        sm.E[r][c] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(E + (size_t)y * W + x) : 0;
-      }
+    for (int k = threadIdx.x; k < ES * ES; k += MTHREADS) {
+      const int r = k / ES, c = k - r * ES;
+      const int y = y0 - MG + r, x = x0 - MG + c;
+      sm.E[r][c] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(E + (size_t)y * W + x) : 0;
     }
   }
   __syncthreads();
-  int prev = -1;
-  for (int i = 0; i < m.L; ++i) {
-    const int mode = m.mode[i];
-    if (mode == 0) {
-      switch (m.R[i]) {
-        case 1: blur_level<1>(m, sm, i, prev, x0, y0); break;
-        case 2: blur_level<2>(m, sm, i, prev, x0, y0); break;
-        case 3: blur_level<3>(m, sm, i, prev, x0, y0); break;
-        case 4: blur_level<4>(m, sm, i, prev, x0, y0); break;
-        case 5: blur_level<5>(m, sm, i, prev, x0, y0); break;
-        default: blur_level<6>(m, sm, i, prev, x0, y0); break;
-      }
-    } else {
-      const int Ti = TS >> i, q0x = x0 >> i, q0y = y0 >> i;
-      const float av = mode == 1 ? 1.0f : 0.0f;
-      const uint8_t sv = mode == 1 ? 1 : 0;
-      uint8_t* Si = sm.S + s_offset(i);
-      for (int r = ty; r < Ti; r += 8) {
-        for (int c = tx; c < Ti; c += 32) {
-          const int qx = q0x + c, qy = q0y + r;
-          const bool inside = qx < m.Wi[i] && qy < m.Hi[i];
-          Si[r * Ti + c] = inside ? sv : 0;
-          if (inside && m.alpha[i]) {
-            m.alpha[i][(size_t)qy * m.Wi[i] + qx] = av;
-            m.stencil[i][(size_t)qy * m.Wi[i] + qx] = sv;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (mode != 2) prev = i;
-  }
+  all_levels(m, sm, x0, y0);
   if (m.label) {
     for (int r = ty; r < TS; r += 8) {
-      const int y = y0 + r;
-      if (y >= H) break;
-      for (int c = tx; c < TS; c += 32) {
-        const int x = x0 + c;
-        if (x >= W) break;
-        uint8_t lab = 0xFF;
-        for (int i = 0; i < m.L; ++i) {
-          if (m.mode[i] == 2) continue;
-          const int Ti = TS >> i;
-          if (sm.S[s_offset(i) + (r >> i) * Ti + (c >> i)]) {
-            lab = (uint8_t)i;
-            break;
-          }
-        }
-        m.label[(size_t)y * W + x] = lab;
+      const int y = y0 + r, x = x0 + tx;
+      if (y >= H || x >= W) continue;
+      uint8_t lab = 0xFF;
+#pragma unroll
+      for (int i = MRR_MAX_LEVELS - 1; i >= 0; --i) {
+        if (i >= m.L || m.mode[i] == 2) continue;
+        const int Ti = TS >> i;
+        const int off = i == 0 ? 0 : (i == 1 ? LevelShape<1>::OFF : (i == 2 ? LevelShape<2>::OFF : LevelShape<3>::OFF));
+        if (sm.S[off + (r >> i) * Ti + (tx >> i)]) lab = (uint8_t)i;
       }
+      m.label[(size_t)y * W + x] = lab;
     }
   }
 }

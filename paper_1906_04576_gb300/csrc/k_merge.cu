@@ -50,160 +50,201 @@ struct MergeSmem {
   int any[MRR_MAX_LEVELS];
 };
 
-// Eq. (1) step for one level from staged taps.
-template <int C>
-__device__ __forceinline__ void blend_staged(const MergeParams& p, const LevelTile& t, int i, int ox, int oy,
-                                             int side, int x, int y, bool first, float& c0, float& c1,
-                                             float& c2) {
-  const int o = 1 << (i - 1), mask = (1 << i) - 1;
-  const float inv = __int_as_float((127 - i) << 23);  // 2^-i
-  const int tx = x - o, ty = y - o;
-  const float fx = (float)(tx & mask) * inv, fy = (float)(ty & mask) * inv;
-  const int lx = (tx >> i) - ox, ly = (ty >> i) - oy;
-  const int base = ly * side + lx;
-  const int idx[4] = {base, base + 1, base + side, base + side + 1};
-  const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
-  float ahat = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (w[k] != 0.0f) ahat = ahat + w[k] * t.a[idx[k]];
-  const float wa = p.weight[i] * ahat;
-  const float alpha = (1.0f < wa) ? 1.0f : wa;
-  if (!first && !(alpha > 0.0f)) return;
-  float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (w[k] == 0.0f || !t.s[idx[k]]) continue;
-    n0 = n0 + w[k] * t.c[idx[k]][0];
-    if (C == 4) {
-      n1 = n1 + w[k] * t.c[idx[k]][1];
-      n2 = n2 + w[k] * t.c[idx[k]][2];
+constexpr int ROWS = MT / 8;  // pixel rows per lane
+
+// Stage the (clamped) taps of level I that the tile can touch; returns via sm.any[I]
+// whether any of them is rendered.
+template <typename CT, int C, int I>
+__device__ __forceinline__ void stage_level(const MergeParams& p, MergeSmem& sm, int X0, int Y0) {
+  constexpr int o = 1 << (I - 1);
+  const int fx0 = (X0 - o) >> I, fy0 = (Y0 - o) >> I;
+  const int side = ((X0 + MT - 1 - o) >> I) - fx0 + 2;
+  const int rows = ((Y0 + MT - 1 - o) >> I) - fy0 + 2;
+  LevelTile& t = sm.lt[I - 1];
+  const int Wi = p.Wi[I], Hi = p.Hi[I];
+  int any = 0;
+  for (int k = threadIdx.x; k < side * rows; k += 256) {
+    const int ly = k / side, lx = k - ly * side;
+    const int qx = min(max(fx0 + lx, 0), Wi - 1), qy = min(max(fy0 + ly, 0), Hi - 1);
+    const size_t q = (size_t)qy * Wi + qx;
+    const uint8_t st = __ldg(p.stencil[I] + q);
+    t.s[k] = st;
+    t.a[k] = __ldg(p.alpha[I] + q);
+    if (st) {
+      const float3 v = load_c<CT>(p.c[I], q, C);
+      t.c[k][0] = v.x;
+      t.c[k][1] = v.y;
+      t.c[k][2] = v.z;
     }
-    den = den + w[k];
+    any |= st;
   }
-  if (den != 1.0f) {
-    n0 = n0 / den;
-    if (C == 4) {
-      n1 = n1 / den;
-      n2 = n2 / den;
+  if (threadIdx.x == 0) {
+    sm.org_x[I] = fx0;
+    sm.org_y[I] = fy0;
+    sm.side[I] = side;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) sm.any[I] = any;
+}
+
+// Eq. (1) for level I (compile-time) on the lane's ROWS pixels of column x.
+template <int C, int I>
+__device__ __forceinline__ void blend_rows(const MergeParams& p, const MergeSmem& sm, int x, int Y0, int ty,
+                                           bool first, float (&c)[ROWS][3]) {
+  constexpr int o = 1 << (I - 1), mask = (1 << I) - 1;
+  const float inv = __int_as_float((127 - I) << 23);  // 2^-I
+  const LevelTile& t = sm.lt[I - 1];
+  const int side = sm.side[I];
+  const int tx = x - o;
+  const float fx = (float)(tx & mask) * inv;
+  const float gx = 1.0f - fx;
+  const int lx = (tx >> I) - sm.org_x[I];
+  const float weight = p.weight[I];
+#pragma unroll
+  for (int rr = 0; rr < ROWS; ++rr) {
+    const int y = Y0 + ty + 8 * rr;
+    const int tyy = y - o;
+    const float fy = (float)(tyy & mask) * inv;
+    const float gy = 1.0f - fy;
+    const int base = ((tyy >> I) - sm.org_y[I]) * side + lx;
+    const int idx[4] = {base, base + 1, base + side, base + side + 1};
+    const float w[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
+    float ahat = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (w[k] != 0.0f) ahat = ahat + w[k] * t.a[idx[k]];
+    const float wa = weight * ahat;
+    const float alpha = (1.0f < wa) ? 1.0f : wa;
+    if (!first && !(alpha > 0.0f)) continue;
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (w[k] == 0.0f || !t.s[idx[k]]) continue;
+      n0 = n0 + w[k] * t.c[idx[k]][0];
+      if (C == 4) {
+        n1 = n1 + w[k] * t.c[idx[k]][1];
+        n2 = n2 + w[k] * t.c[idx[k]][2];
+      }
+      den = den + w[k];
     }
-  }
-  if (first) {
-    c0 = n0;
-    c1 = n1;
-    c2 = n2;
-    return;
-  }
-  const float om = 1.0f - alpha;
-  c0 = n0 * alpha + c0 * om;
-  if (C == 4) {
-    c1 = n1 * alpha + c1 * om;
-    c2 = n2 * alpha + c2 * om;
+    if (den != 1.0f) {
+      n0 = n0 / den;
+      if (C == 4) {
+        n1 = n1 / den;
+        n2 = n2 / den;
+      }
+    }
+    if (first) {
+      c[rr][0] = n0;
+      c[rr][1] = n1;
+      c[rr][2] = n2;
+    } else {
+      const float om = 1.0f - alpha;
+      c[rr][0] = n0 * alpha + c[rr][0] * om;
+      if (C == 4) {
+        c[rr][1] = n1 * alpha + c[rr][1] * om;
+        c[rr][2] = n2 * alpha + c[rr][2] * om;
+      }
+    }
   }
 }
 
-template <typename CT, int C>
+template <typename CT, int C, int L>
 __global__ void __launch_bounds__(256) merge_kernel(MergeParams p, float* __restrict__ out) {
   __shared__ MergeSmem sm;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int X0 = blockIdx.x * MT, Y0 = blockIdx.y * MT;
-  // stage the footprints of levels 1..L-1
-  for (int i = 1; i < p.L; ++i) {
-    if (!p.enabled[i]) continue;
-    const int o = 1 << (i - 1);
-    const int fx0 = (X0 - o) >> i, fy0 = (Y0 - o) >> i;
-    const int side = ((X0 + MT - 1 - o) >> i) - fx0 + 2;
-    const int rows = ((Y0 + MT - 1 - o) >> i) - fy0 + 2;
-    if (threadIdx.x == 0) {
-      sm.org_x[i] = fx0;
-      sm.org_y[i] = fy0;
-      sm.side[i] = side;
-    }
-    LevelTile& t = sm.lt[i - 1];
-    int any = 0;
-    const int Wi = p.Wi[i], Hi = p.Hi[i];
-    for (int k = threadIdx.x; k < side * rows; k += 256) {
-      const int ly = k / side, lx = k - ly * side;
-      const int qx = min(max(fx0 + lx, 0), Wi - 1), qy = min(max(fy0 + ly, 0), Hi - 1);
-      const size_t q = (size_t)qy * Wi + qx;
-      const uint8_t s = __ldg(p.stencil[i] + q);
-      t.s[k] = s;
-      t.a[k] = __ldg(p.alpha[i] + q);
-      if (s) {
-        const float3 v = load_c<CT>(p.c[i], q, C);
-        t.c[k][0] = v.x;
-        t.c[k][1] = v.y;
-        t.c[k][2] = v.z;
-      }
-      any |= s;
-    }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) sm.any[i] = any;
-  }
+  if (L > 1 && p.enabled[1]) stage_level<CT, C, 1>(p, sm, X0, Y0);
+  if (L > 2 && p.enabled[2]) stage_level<CT, C, (L > 2 ? 2 : 1)>(p, sm, X0, Y0);
+  if (L > 3) stage_level<CT, C, (L > 3 ? 3 : 1)>(p, sm, X0, Y0);
   __syncthreads();
   const int W = p.W, H = p.H;
   const int x = X0 + tx;
-  for (int r = ty; r < MT; r += 8) {
-    const int y = Y0 + r;
-    if (x >= W || y >= H) continue;
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    bool first = true;
-    for (int i = p.L - 1; i >= 1; --i) {
-      if (!p.enabled[i] || (!first && !sm.any[i])) continue;
-      blend_staged<C>(p, sm.lt[i - 1], i, sm.org_x[i], sm.org_y[i], sm.side[i], x, y, first, c0, c1, c2);
-      first = false;
-    }
-    if (p.enabled[0]) {
+  if (x >= W) return;
+  float c[ROWS][3] = {};
+  // coarsest level first, then the finer enabled levels that the tile touches
+  bool first = true;
+  if (L == 4) {
+    blend_rows<C, (L == 4 ? 3 : 1)>(p, sm, x, Y0, ty, true, c);
+    first = false;
+  }
+  if (L >= 3 && p.enabled[2] && (first || sm.any[2])) {
+    blend_rows<C, (L >= 3 ? 2 : 1)>(p, sm, x, Y0, ty, first, c);
+    first = false;
+  }
+  if (L >= 2 && p.enabled[1] && (first || sm.any[1])) {
+    blend_rows<C, 1>(p, sm, x, Y0, ty, first, c);
+    first = false;
+  }
+  if (p.enabled[0]) {
+#pragma unroll
+    for (int rr = 0; rr < ROWS; ++rr) {
+      const int y = Y0 + ty + 8 * rr;
+      if (y >= H) break;
       const size_t q = (size_t)y * W + x;
       const float a0 = __ldg(p.alpha[0] + q);
       const float ahat = 0.0f + 1.0f * a0;
       const float wa = p.weight[0] * ahat;
       const float alpha = (1.0f < wa) ? 1.0f : wa;
-      if (first || alpha > 0.0f) {
-        float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
-        if (__ldg(p.stencil[0] + q)) {
-          const float3 v = load_c<CT>(p.c[0], q, C);
-          n0 = v.x;
-          n1 = v.y;
-          n2 = v.z;
-          den = 1.0f;
-        } else {
-          n0 = n0 / den;  // no rendered tap: 0/0, as the definition gives
-          n1 = n1 / den;
-          n2 = n2 / den;
-        }
-        if (first) {
-          c0 = n0;
-          c1 = n1;
-          c2 = n2;
-        } else {
-          const float om = 1.0f - alpha;
-          c0 = n0 * alpha + c0 * om;
-          if (C == 4) {
-            c1 = n1 * alpha + c1 * om;
-            c2 = n2 * alpha + c2 * om;
-          }
+      if (!first && !(alpha > 0.0f)) continue;
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
+      if (__ldg(p.stencil[0] + q)) {
+        const float3 v = load_c<CT>(p.c[0], q, C);
+        n0 = v.x;
+        n1 = v.y;
+        n2 = v.z;
+        den = 1.0f;
+      } else {
+        n0 = n0 / den;  // no rendered tap: 0/0, as the definition gives
+        n1 = n1 / den;
+        n2 = n2 / den;
+      }
+      if (first) {
+        c[rr][0] = n0;
+        c[rr][1] = n1;
+        c[rr][2] = n2;
+      } else {
+        const float om = 1.0f - alpha;
+        c[rr][0] = n0 * alpha + c[rr][0] * om;
+        if (C == 4) {
+          c[rr][1] = n1 * alpha + c[rr][1] * om;
+          c[rr][2] = n2 * alpha + c[rr][2] * om;
         }
       }
     }
+  }
+#pragma unroll
+  for (int rr = 0; rr < ROWS; ++rr) {
+    const int y = Y0 + ty + 8 * rr;
+    if (y >= H) break;
     const size_t o = (size_t)y * W + x;
     if (C == 4)
-      reinterpret_cast<float4*>(out)[o] = make_float4(c0, c1, c2, 0.0f);
+      reinterpret_cast<float4*>(out)[o] = make_float4(c[rr][0], c[rr][1], c[rr][2], 0.0f);
     else
-      out[o] = c0;
+      out[o] = c[rr][0];
+  }
+}
+
+template <typename CT, int C>
+void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
+  dim3 grid((p.W + MT - 1) / MT, (p.H + MT - 1) / MT);
+  switch (p.L) {
+    case 1: merge_kernel<CT, C, 1><<<grid, 256, 0, s>>>(p, out); break;
+    case 2: merge_kernel<CT, C, 2><<<grid, 256, 0, s>>>(p, out); break;
+    case 3: merge_kernel<CT, C, 3><<<grid, 256, 0, s>>>(p, out); break;
+    default: merge_kernel<CT, C, 4><<<grid, 256, 0, s>>>(p, out); break;
   }
 }
 
 }  // namespace
 
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s) {
-  dim3 grid((p.W + MT - 1) / MT, (p.H + MT - 1) / MT);
   if (p.C == 4) {
-    if (p.half_store) merge_kernel<__half, 4><<<grid, 256, 0, s>>>(p, out);
-    else merge_kernel<float, 4><<<grid, 256, 0, s>>>(p, out);
+    if (p.half_store) launch_merge_t<__half, 4>(p, out, s);
+    else launch_merge_t<float, 4>(p, out, s);
   } else {
-    if (p.half_store) merge_kernel<__half, 1><<<grid, 256, 0, s>>>(p, out);
-    else merge_kernel<float, 1><<<grid, 256, 0, s>>>(p, out);
+    if (p.half_store) launch_merge_t<__half, 1>(p, out, s);
+    else launch_merge_t<float, 1>(p, out, s);
   }
   count_launches(1);
   return cudaGetLastError();

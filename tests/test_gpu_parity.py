@@ -294,6 +294,25 @@ def test_lane_split_does_not_change_results(mrr, lanes):
     mrr.mrr_destroy(ctx)
 
 
+@pytest.mark.parametrize("effect", ["ssao", "ssgi"])
+def test_autotune_keeps_results(mrr, effect):
+    import torch
+    W, H = 240, 136
+    fr = sg.gbuffer(5, W, H, 16, 4)
+    cfg = make_cfg(effect, 4, W, H, samples=32)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    before, after = mrr.alloc_output(ctx, W, H), mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, before)
+    t = mrr.mrr_autotune(ctx, dev)
+    assert t["lanes_per_texel"] in (1, 2, 4) and t["grid_multiplier"] in (1, 2, 4)
+    assert t["shade_levels_ms"] > 0 and t["shade_full_ms"] > 0 and t["candidates"] >= 4
+    mrr.mrr_render(ctx, dev, after)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    mrr.mrr_destroy(ctx)
+
+
 def test_frame_larger_than_context_is_rejected(mrr):
     W, H = 64, 64
     fr = sg.gbuffer(0, W, H, 4, 0)
