@@ -81,10 +81,11 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   E[(size_t)y * W + x] = e;
 }
 
-// edges_direct_kernel: a lane owns a column of ER vertically adjacent pixels, so the
-// column's own depth/normal values (rows y0-1 .. y0+ER) are loaded once and shared as
-// up/down neighbours; only the left/right neighbours are extra loads.
-constexpr int ER = 4;
+// edges_direct_kernel: a lane owns a column of ER vertically adjacent pixels.  Every
+// load it needs -- the column rows y0-1 .. y0+ER and the left/right neighbours of its
+// pixels, at clamped addresses -- is issued before any of them is used, so a warp waits
+// for memory once, and the column values double as up/down neighbours.
+constexpr int ER = 2;
 
 template <typename NT>
 __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, const float* __restrict__ depth,
@@ -95,34 +96,34 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
   const int y0 = (blockIdx.y * TY + threadIdx.y) * ER;
   if (x >= W || y0 >= H) return;
   const float farp = p.v.farp;
-  // column values for rows y0-1 .. y0+ER (index r+1 for row y0+r)
-  float dc[ER + 2];
-  float3 nc[ER + 2];
+  const int xl = max(x - 1, 0), xr = min(x + 1, W - 1);
+  float dc[ER + 2], dl[ER], dr[ER];
+  float3 nc[ER + 2], nl[ER], nr[ER];
 #pragma unroll
   for (int r = -1; r <= ER; ++r) {
-    const int y = y0 + r;
-    const bool ok = y >= 0 && y < H;
-    dc[r + 1] = ok ? __ldg(depth + y * W + x) : 0.0f;
-    nc[r + 1] = ok ? load_normal(normal, y * W + x) : make_float3(0.f, 0.f, 0.f);
+    const int y = min(max(y0 + r, 0), H - 1);
+    dc[r + 1] = __ldg(depth + y * W + x);
+    nc[r + 1] = load_normal(normal, y * W + x);
+  }
+#pragma unroll
+  for (int r = 0; r < ER; ++r) {
+    const int y = min(y0 + r, H - 1);
+    dl[r] = __ldg(depth + y * W + xl);
+    dr[r] = __ldg(depth + y * W + xr);
+    nl[r] = load_normal(normal, y * W + xl);
+    nr[r] = load_normal(normal, y * W + xr);
   }
 #pragma unroll
   for (int r = 0; r < ER; ++r) {
     const int y = y0 + r;
     if (y >= H) break;
-    const int i = y * W + x;
     const float d = dc[r + 1];
     uint8_t e = 0;
     if (d < farp) {
       const float3 n = nc[r + 1];
       const bool has[4] = {x > 0, x < W - 1, y > 0, y < H - 1};
-      float dn[4];
-      float3 nn[4];
-      dn[0] = has[0] ? __ldg(depth + i - 1) : 0.0f;
-      dn[1] = has[1] ? __ldg(depth + i + 1) : 0.0f;
-      dn[2] = dc[r];
-      dn[3] = dc[r + 2];
-      nn[2] = nc[r];
-      nn[3] = nc[r + 2];
+      const float dn[4] = {dl[r], dr[r], dc[r], dc[r + 2]};
+      const float3 nn[4] = {nl[r], nr[r], nc[r], nc[r + 2]};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (!has[k]) continue;
@@ -130,8 +131,7 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
           e = 1;
           continue;
         }
-        const float3 m = k == 0 ? load_normal(normal, i - 1) : (k == 1 ? load_normal(normal, i + 1) : nn[k]);
-        if (n.x * m.x + n.y * m.y + n.z * m.z < p.normal_cos) e = 1;
+        if (n.x * nn[k].x + n.y * nn[k].y + n.z * nn[k].z < p.normal_cos) e = 1;
       }
       if (has[0] && has[1]) {
         const float lap = (dn[0] + dn[1]) - 2.0f * d;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
         if (fabsf(lap) > p.depth_rel * d) e = 1;
       }
     }
-    E[i] = e;
+    E[y * W + x] = e;
   }
 }
 

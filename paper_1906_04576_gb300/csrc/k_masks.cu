@@ -14,9 +14,10 @@
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
 //   every level's stencil into a row-major list of (y << 16) | x.  Pass 1 counts the set
 //   texels of each 4096-texel chunk; pass 2 gives each chunk its exclusive prefix (a
-//   block reduction over the preceding chunk counts of its level), then each warp
-//   scatters its 512 texels with ballot + popc, so list order = index order and no warp
-//   of the shading kernel idles on an unmasked texel.
+//   block reduction over the preceding chunk counts of its level); every lane loads its 16
+//   texels at once, and a warp shuffle scan plus the per-warp totals give each lane its
+//   output position, so list order = index order and no warp of the shading kernel idles
+//   on an unmasked texel.
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -59,6 +60,7 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
 #pragma unroll
   for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[I][t];
   // D_I over the tile and its R halo; E outside the image is staged as 0
+  int anyd = 0;
   for (int k = tid; k < DN * DN; k += MTHREADS) {
     const int r = k / DN, c = k - r * DN;
     const int qx = q0x - R + c, qy = q0y - R + r;
@@ -71,8 +73,11 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
         for (int bx = 0; bx < BS; ++bx) v |= e[by * ES + bx];
     }
     sm.D[k] = v;
+    anyd |= v;
   }
-  __syncthreads();
+  // no edge within reach of the tile: a_I = 0 here and the blur passes add only zeros
+  const bool blur = __syncthreads_or(anyd) != 0;
+  if (blur) {
   // horizontal pass: with D in {0,1}, fma(g, D, s) is s + g where D is set and s elsewhere
   for (int k = tid; k < DN * Ti; k += MTHREADS) {
     const int r = k / Ti, c = k - r * Ti;
@@ -84,14 +89,17 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
     sm.h[k] = s;
   }
   __syncthreads();
+  }
   // vertical pass, stencil, nesting, stores
   uint8_t* Si = sm.S + LevelShape<I>::OFF;
   for (int k = tid; k < Ti * Ti; k += MTHREADS) {
     const int r = k / Ti, c = k - r * Ti;
     const int qx = q0x + c, qy = q0y + r;
     float s = 0.0f;
+    if (blur) {
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[(r + t) * Ti + c], s);
+      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[(r + t) * Ti + c], s);
+    }
     uint8_t st = s > 0.0f ? 1 : 0;
     if (P >= 0) {
       constexpr int F = P >= 0 ? I - P : 0, TP = P >= 0 ? LevelShape<(P >= 0 ? P : 0)>::T : 1;
@@ -256,39 +264,48 @@ __global__ void __launch_bounds__(COMPACT_THREADS) compact_scatter_kernel(Compac
   const int l = slot_of(p, blockIdx.x);
   const int c0 = p.chunk_begin[l];
   const int c = blockIdx.x - c0;
-  // exclusive prefix of this chunk within its level
-  uint32_t part = 0;
-  for (int k = c0 + threadIdx.x; k < (int)blockIdx.x; k += COMPACT_THREADS) part += p.chunk_counts[k];
-  const uint32_t offset = block_sum(part, red);
   const uint32_t Wi = (uint32_t)p.Wi[l];
   const uint32_t n = Wi * (uint32_t)p.Hi[l];
   const uint8_t* S = p.stencil[l];
-  uint32_t* list = p.list[l];
+  // each lane owns 16 consecutive texels, loaded at once (one 16-byte load when aligned)
+  constexpr int PER_LANE = COMPACT_CHUNK / COMPACT_THREADS;  // 16
+  const uint32_t base = (uint32_t)c * COMPACT_CHUNK + threadIdx.x * PER_LANE;
+  uint32_t bits = 0;  // bit b: texel base + b is set
+  if (base + PER_LANE <= n && ((reinterpret_cast<uintptr_t>(S + base) & 15) == 0)) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(S + base));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int b = 0; b < PER_LANE; ++b) bits |= ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu) ? (1u << b) : 0u;
+  } else {
+    for (int b = 0; b < PER_LANE; ++b)
+      if (base + b < n && S[base + b]) bits |= 1u << b;
+  }
+  // exclusive prefix of this chunk within its level (sum of the preceding chunk counts)
+  uint32_t part = 0;
+  for (int k = c0 + threadIdx.x; k < (int)blockIdx.x; k += COMPACT_THREADS) part += p.chunk_counts[k];
+  const uint32_t offset = block_sum(part, red);
+  // lane prefix within the warp, then warp prefix within the block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int PER_WARP = COMPACT_CHUNK / (COMPACT_THREADS / 32);  // 512
-  const uint32_t wbase = (uint32_t)c * COMPACT_CHUNK + warp * PER_WARP;
-  // each warp counts its 512 texels, then writes them after the block-level offsets
-  uint32_t mine = 0;
-#pragma unroll 4
-  for (int r = 0; r < PER_WARP / 32; ++r) {
-    const uint32_t idx = wbase + r * 32 + lane;
-    mine += __popc(__ballot_sync(0xffffffffu, idx < n && S[idx] != 0));
+  const uint32_t mine = __popc(bits);
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  if (lane == 0) wsum[warp] = mine;
+  if (lane == 31) wsum[warp] = incl;
   __syncthreads();
-  uint32_t pos = offset;
+  uint32_t pos = offset + incl - mine;
   for (int w = 0; w < warp; ++w) pos += wsum[w];
-  for (int r = 0; r < PER_WARP / 32; ++r) {
-    const uint32_t idx = wbase + r * 32 + lane;
-    const bool set = idx < n && S[idx] != 0;
-    const uint32_t bal = __ballot_sync(0xffffffffu, set);
-    if (set) {
-      const uint32_t y = idx / Wi, x = idx - y * Wi;
-      list[pos + __popc(bal & ((1u << lane) - 1u))] = (y << 16) | x;
-    }
-    pos += __popc(bal);
+  uint32_t* list = p.list[l];
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint32_t idx = base + b;
+    const uint32_t y = idx / Wi, x = idx - y * Wi;
+    list[pos++] = (y << 16) | x;
   }
-  if (warp == COMPACT_THREADS / 32 - 1 && lane == 0 && (int)blockIdx.x == p.chunk_begin[l + 1] - 1)
+  if (threadIdx.x == COMPACT_THREADS - 1 && (int)blockIdx.x == p.chunk_begin[l + 1] - 1)
     p.counts[p.level_of[l]] = pos;
 }
 

@@ -11,8 +11,8 @@
 // Level 0 (one tap, weight 1) is read straight from global memory, c only where
 // alpha > 0.  Per pixel, from the coarsest level down: a_i is interpolated plainly,
 // c_i over rendered taps with renormalised weights, alpha = min(w_i a_i, 1) and
-// c' = c_i alpha + c' (1 - alpha).  Taps of weight exactly 0 are not read (they would
-// add +0), and the renormalising division is skipped when the weight sum is exactly 1.
+// c' = c_i alpha + c' (1 - alpha).  A tap of weight 0 adds +0 either way, and the
+// renormalising division is skipped when the weight sum is exactly 1 (x / 1 = x).
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -57,9 +57,9 @@ constexpr int ROWS = MT / 8;  // pixel rows per lane
 template <typename CT, int C, int I>
 __device__ __forceinline__ void stage_level(const MergeParams& p, MergeSmem& sm, int X0, int Y0) {
   constexpr int o = 1 << (I - 1);
+  // X0 is a multiple of MT, so the footprint is (MT >> I) + 2 texels on each side
+  constexpr int side = (MT >> I) + 2, rows = side;
   const int fx0 = (X0 - o) >> I, fy0 = (Y0 - o) >> I;
-  const int side = ((X0 + MT - 1 - o) >> I) - fx0 + 2;
-  const int rows = ((Y0 + MT - 1 - o) >> I) - fy0 + 2;
   LevelTile& t = sm.lt[I - 1];
   const int Wi = p.Wi[I], Hi = p.Hi[I];
   int any = 0;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void blend_rows(const MergeParams& p, const MergeSmem
   constexpr int o = 1 << (I - 1), mask = (1 << I) - 1;
   const float inv = __int_as_float((127 - I) << 23);  // 2^-I
   const LevelTile& t = sm.lt[I - 1];
-  const int side = sm.side[I];
+  constexpr int side = (MT >> I) + 2;
   const int tx = x - o;
   const float fx = (float)(tx & mask) * inv;
   const float gx = 1.0f - fx;
@@ -109,23 +109,23 @@ __device__ __forceinline__ void blend_rows(const MergeParams& p, const MergeSmem
     const int base = ((tyy >> I) - sm.org_y[I]) * side + lx;
     const int idx[4] = {base, base + 1, base + side, base + side + 1};
     const float w[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
+    // every tap is added (a weight of 0 adds +0); unrendered taps add +0 through a select
     float ahat = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (w[k] != 0.0f) ahat = ahat + w[k] * t.a[idx[k]];
+    for (int k = 0; k < 4; ++k) ahat = ahat + w[k] * t.a[idx[k]];
     const float wa = weight * ahat;
     const float alpha = (1.0f < wa) ? 1.0f : wa;
     if (!first && !(alpha > 0.0f)) continue;
     float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      if (w[k] == 0.0f || !t.s[idx[k]]) continue;
-      n0 = n0 + w[k] * t.c[idx[k]][0];
+      const bool on = t.s[idx[k]] != 0;
+      n0 = n0 + (on ? w[k] * t.c[idx[k]][0] : 0.0f);
       if (C == 4) {
-        n1 = n1 + w[k] * t.c[idx[k]][1];
-        n2 = n2 + w[k] * t.c[idx[k]][2];
+        n1 = n1 + (on ? w[k] * t.c[idx[k]][1] : 0.0f);
+        n2 = n2 + (on ? w[k] * t.c[idx[k]][2] : 0.0f);
       }
-      den = den + w[k];
+      den = den + (on ? w[k] : 0.0f);
     }
     if (den != 1.0f) {
       n0 = n0 / den;
