@@ -202,6 +202,24 @@ mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, v
  * the result to out_host and synchronises the stream before returning. */
 mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* g_host, float* out_host, void* stream);
 
+/* mrr_masks for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the mask stage.  Host programs that may
+ * not call cudaMalloc (a plug-in inside an engine that owns every device allocation, a
+ * process working inside a pre-reserved memory budget) cannot create a context, since
+ * mrr_create allocates pools.  This call needs no context: it reads only the mask fields
+ * of *cfg (num_levels, sigma2, enabled, force_level0; host memory), computes exactly
+ * what mrr_masks computes into the caller's buffers, and keeps its one piece of scratch
+ * -- the work-list compaction's per-chunk counts -- in a fixed 32 KiB array that the
+ * library holds on every device that loads it until the process exits.
+ *  - Frames up to 4096 x 4096 pixels; larger frames (or inconsistent level sizes or
+ *    missing buffers) return MRR_EINVAL before anything is launched.
+ *  - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *  - The first call on each device looks the array's device address up (with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other streams, other
+ *    host threads) race on it; order them.  Returns MRR_ECUDA on a launch failure. */
+mrr_status mrr_masks_static(const mrr_config* cfg, const uint8_t* edges_dev, const mrr_levels* lv, void* stream);
+
 /* Result of mrr_autotune: the settings chosen and the measured kernel times (ms). */
 typedef struct mrr_tuning {
   int lanes_per_texel;      /* chosen split of a work-list texel's samples over lanes */

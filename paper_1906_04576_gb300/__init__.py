@@ -98,6 +98,8 @@ _lib.mrr_masks.argtypes = [_vp, _vp, ctypes.POINTER(mrr_levels), _vp]
 _lib.mrr_shade_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp]
 _lib.mrr_upsample_merge.argtypes = [_vp, ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp, _vp]
 _lib.mrr_shade_levels.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp]
+_lib.mrr_masks_static.argtypes = [ctypes.POINTER(mrr_config), _vp, ctypes.POINTER(mrr_levels), _vp]
+_lib.mrr_masks_static.restype = ctypes.c_int
 _lib.mrr_kernel_launches.argtypes = []
 _lib.mrr_kernel_launches.restype = ctypes.c_uint64
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
@@ -353,6 +355,15 @@ def mrr_autotune(ctx: Context, frame: DeviceFrame, stream=None) -> dict:
     t = mrr_tuning()
     _check(ctx, _lib.mrr_autotune(ctx.handle, ctypes.byref(g), _stream(stream), ctypes.byref(t)))
     return {k: getattr(t, k) for k, _ in mrr_tuning._fields_}
+
+
+def mrr_masks_static(cfg: dict, edges: torch.Tensor, levels: Levels, stream=None) -> None:
+    """The mask stage without a context and without any allocation (see include/mrr.h)."""
+    c, keep = make_config(cfg)
+    lv = levels.struct()
+    st = _lib.mrr_masks_static(ctypes.byref(c), _ptr(edges), ctypes.byref(lv), _stream(stream))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_masks_static")
 
 
 def mrr_kernel_launches() -> int:
