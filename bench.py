@@ -124,20 +124,21 @@ def algorithmic_bytes(cfg, n_nonsky, n_sky):
     return n_nonsky * (per + store) + n_sky * (4 + store)
 
 
-def workload_config(mrr, sg, name):
-    wl = dict(sg.WORKLOADS[name])
-    W, H = wl["width"], wl["height"]
-    eff = wl["effect"]
+def effect_config(mrr, sg, spec, W, H, precision):
+    eff = spec["effect"]
     kw = {}
     if eff in ("ssao", "ssgi"):
-        kw.update(kernel=sg.hemisphere_kernel(wl["samples"]), radius=wl["radius"], samples=wl["samples"])
+        kw.update(kernel=sg.hemisphere_kernel(spec["samples"]), radius=spec["radius"], samples=spec["samples"])
     else:
-        kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
-                  pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED),
-                  blocker_samples=wl["blocker_samples"], pcf_samples=wl["pcf_samples"])
-    if eff == "ssgi":
-        kw["precision"] = "fp16"
-    cfg = mrr.default_config(eff, wl["levels"], W, H, **kw)
+        kw.update(blocker_taps=sg.disk_taps(spec["blocker_samples"], sg.BLOCKER_SEED),
+                  pcf_taps=sg.disk_taps(spec["pcf_samples"], sg.PCF_SEED),
+                  blocker_samples=spec["blocker_samples"], pcf_samples=spec["pcf_samples"])
+    return mrr.default_config(eff, spec["levels"], W, H, precision=precision, **kw)
+
+
+def workload_config(mrr, sg, name):
+    wl = dict(sg.WORKLOADS[name])
+    cfg = effect_config(mrr, sg, wl, wl["width"], wl["height"], wl.get("precision", "fp32"))
     return wl, cfg
 
 
@@ -224,6 +225,96 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
+    """One step = both effects of the workload on one frame through mrr_render_batch
+    (one batched shading launch), against the two plain full-resolution kernels."""
+    import torch
+    W, H = wl["width"], wl["height"]
+    prec = cfg["precision"]
+    cfg2 = effect_config(mrr, sg, wl["batch_with"], W, H, prec)
+    fr = make_frame(sg, wl, rank)
+    ctxs = [mrr.mrr_create(cfg), mrr.mrr_create(cfg2)]
+    dev = mrr.upload_frame(fr, prec)
+    outs = [mrr.alloc_output(c, W, H) for c in ctxs]
+    fulls = [mrr.alloc_output(c, W, H) for c in ctxs]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    b = mrr.mrr_batch_create()
+    tune = None if args.no_tune else mrr.mrr_batch_autotune(b, ctxs, [dev, dev], stream)
+    step = lambda: mrr.mrr_render_batch(b, ctxs, [dev, dev], outs, stream)
+
+    def step_full():
+        for c, o in zip(ctxs, fulls):
+            mrr.mrr_render_full(c, dev, o, stream)
+
+    for _ in range(args.warmup):
+        step()
+        step_full()
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        for s_, e_ in ev:
+            flush.zero_()
+            s_.record(stream)
+            fn()
+            e_.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        return [s_.elapsed_time(e_) for s_, e_ in ev]
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[int(os.environ.get("LOCAL_RANK", "0"))].strip() if vis
+                           else torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    l0 = mrr.mrr_kernel_launches()
+    t_b = timed(step, args.steps)
+    launches = mrr.mrr_kernel_launches() - l0
+    t_f = timed(step_full, args.steps)
+    clocks = sampler.stop()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    rmse = []
+    for o, f_ in zip(outs, fulls):
+        d = (o - f_)[..., :3] if o.dim() == 3 else (o - f_)
+        rmse.append(float(torch.sqrt(torch.mean(d.double() ** 2)).item()))
+    px = world * args.steps * 2 * W * H
+    sb, sf = max_over_ranks(sum(t_b)), max_over_ranks(sum(t_f))
+    value, fvalue = px / (sb * 1e-3) / 1e6, px / (sf * 1e-3) / 1e6
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sb / args.steps, 5), "p50_ms": round(pct(t_b, 0.5), 5),
+            "p99_ms": round(pct(t_b, 0.99), 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-storage/f32" if prec == "fp16" else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "width": W, "height": H,
+                       "effects": [cfg["effect"], cfg2["effect"]], "samples": [cfg.get("samples"), cfg2.get("samples")],
+                       "precision": prec, "batch": "both effects of one frame in one persistent shading launch",
+                       "l2": "flushed (256 MiB write) before every timed step, outside the events",
+                       "parallelism": f"replicas x{world}"},
+            "full_res": {"value": round(fvalue, 3), "unit": "Mpix/s", "p50_ms": round(pct(t_f, 0.5), 5),
+                         "p99_ms": round(pct(t_f, 0.99), 5)},
+            "speedup_vs_full_res": round(value / fvalue, 4), "rmse_vs_full_res": rmse,
+            "gpu_launches": int(launches), "tuning": tune, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    mrr.mrr_batch_destroy(b)
+    for c in ctxs:
+        mrr.mrr_destroy(c)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,6 +347,8 @@ def main():
     wl, cfg = workload_config(mrr, sg, args.workload)
     W, H = wl["width"], wl["height"]
     prec = cfg["precision"]
+    if "batch_with" in wl:
+        return run_batch(args, mrr, sg, wl, cfg, rank, world, dist)
     fr = make_frame(sg, wl, rank)
     ctx = mrr.mrr_create(cfg)
     dev = mrr.upload_frame(fr, prec)

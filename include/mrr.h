@@ -239,6 +239,43 @@ typedef struct mrr_tuning {
  * lanes_per_texel / lanes_per_pixel) are kept. */
 mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tuning* out);
 
+/* Batched rendering: several frames -- of different sizes, through different contexts
+ * and so possibly different effects and precisions -- in one pass, with ONE persistent
+ * shading launch for all of them.  That launch pulls fixed-size chunks of the
+ * concatenated work lists of every frame and level from a global queue (an atomic
+ * counter), so cheap and expensive frames balance across the GPU.  Edges, masks and
+ * the blend run per frame as in mrr_render; every frame's image equals mrr_render of the
+ * same context and frame, bit for bit.  The paper renders one frame at a time; this is
+ * a serving extension of its Sec. 3 pipeline. */
+typedef struct mrr_batch mrr_batch;
+
+/* Tuning of a batch (0 = default): entries per queue chunk (multiple of 32, at most
+ * 65536) and the launch grid as a multiple of the resident CTAs. */
+typedef struct mrr_batch_tuning {
+  int chunk;
+  int grid_multiplier;
+  float shade_ms;       /* batched shading launch time with these settings (autotune output) */
+  int candidates;       /* configurations timed (autotune output) */
+} mrr_batch_tuning;
+
+/* Create a batch object: device item table for up to 8 frames, queue head, pinned
+ * staging.  Allocates; not for capture. */
+mrr_status mrr_batch_create(mrr_batch** out);
+void mrr_batch_destroy(mrr_batch* b);
+
+/* Render frames[k] through ctxs[k] into outs[k] (as mrr_render), k < n <= 8, on one
+ * stream.  The contexts must be distinct (each frame uses its context's pools) and each
+ * frame must fit its context.  Replays a CUDA graph of the batch while the contexts,
+ * frame descriptors and outputs repeat. */
+mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n,
+                            void* stream);
+
+/* Autotuner of the batched launch: times chunk in {256, 1024, 4096} x grid_multiplier in
+ * {1, 2} (median of 5 after 2 warm-ups, CUDA events on `stream`), keeps the fastest in
+ * the batch and reports it in *out (may be NULL).  Synchronises `stream`. */
+mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, int n, void* stream,
+                              mrr_batch_tuning* out);
+
 /* Number of kernels this library has launched in this process (all contexts), for
  * accounting of GPU work in benchmarks. */
 uint64_t mrr_kernel_launches(void);

@@ -12,6 +12,9 @@ device memory and streams.  The functions carry the C names of include/mrr.h:
     mrr_render_host(ctx, host_frame, out_host)
     mrr_level_dims(W, H, level)         mrr_last_error(ctx)
     mrr_autotune(ctx, frame)            mrr_kernel_launches()
+    mrr_batch_create() -> Batch         mrr_batch_destroy(b)
+    mrr_render_batch(b, ctxs, frames, outs)   mrr_batch_autotune(b, ctxs, frames)
+    mrr_masks_static(cfg, edges, levels)
 
 Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
 ``python paper_1906_04576_gb300/_build.py``): there is no CPU fallback.
@@ -83,7 +86,22 @@ class mrr_tuning(ctypes.Structure):
                 ("shade_full_ms", ctypes.c_float), ("candidates", ctypes.c_int)]
 
 
+class mrr_batch_tuning(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int), ("grid_multiplier", ctypes.c_int), ("shade_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
+_lib.mrr_batch_create.argtypes = [ctypes.POINTER(_vp)]
+_lib.mrr_batch_create.restype = ctypes.c_int
+_lib.mrr_batch_destroy.argtypes = [_vp]
+_lib.mrr_batch_destroy.restype = None
+_lib.mrr_render_batch.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(_vp),
+                                  ctypes.c_int, _vp]
+_lib.mrr_render_batch.restype = ctypes.c_int
+_lib.mrr_batch_autotune.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(mrr_gbuffer), ctypes.c_int, _vp,
+                                    ctypes.POINTER(mrr_batch_tuning)]
+_lib.mrr_batch_autotune.restype = ctypes.c_int
 _lib.mrr_autotune.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, ctypes.POINTER(mrr_tuning)]
 _lib.mrr_autotune.restype = ctypes.c_int
 _lib.mrr_level_dims.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -364,6 +382,59 @@ def mrr_masks_static(cfg: dict, edges: torch.Tensor, levels: Levels, stream=None
     st = _lib.mrr_masks_static(ctypes.byref(c), _ptr(edges), ctypes.byref(lv), _stream(stream))
     if st != MRR_OK:
         raise MrrError(st, "mrr_masks_static")
+
+
+@dataclass
+class Batch:
+    handle: int
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.mrr_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = 0
+
+
+def mrr_batch_create() -> Batch:
+    h = _vp()
+    st = _lib.mrr_batch_create(ctypes.byref(h))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_batch_create")
+    return Batch(h.value)
+
+
+def mrr_batch_destroy(b: Batch) -> None:
+    if b.handle:
+        _lib.mrr_batch_destroy(b.handle)
+        b.handle = 0
+
+
+def _batch_args(ctxs, frames):
+    n = len(ctxs)
+    ca = (_vp * n)(*[c.handle for c in ctxs])
+    fa = (mrr_gbuffer * n)(*[f.struct() for f in frames])
+    return n, ca, fa
+
+
+def mrr_render_batch(b: Batch, ctxs: list, frames: list, outs: list, stream=None) -> None:
+    """Render frames[k] through ctxs[k] into outs[k] with one batched shading launch."""
+    n, ca, fa = _batch_args(ctxs, frames)
+    oa = (_vp * n)(*[_ptr(o) for o in outs])
+    st = _lib.mrr_render_batch(b.handle, ca, fa, oa, n, _stream(stream))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_render_batch")
+
+
+def mrr_batch_autotune(b: Batch, ctxs: list, frames: list, stream=None) -> dict:
+    n, ca, fa = _batch_args(ctxs, frames)
+    t = mrr_batch_tuning()
+    st = _lib.mrr_batch_autotune(b.handle, ca, fa, n, _stream(stream), ctypes.byref(t))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_batch_autotune")
+    return {k: getattr(t, k) for k, _ in mrr_batch_tuning._fields_}
 
 
 def mrr_kernel_launches() -> int:

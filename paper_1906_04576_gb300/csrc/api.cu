@@ -49,6 +49,24 @@ struct mrr_ctx {
   uint64_t graph_kernels = 0;
 };
 
+struct mrr_batch {
+  BatchItem* items_dev = nullptr;
+  BatchItem* staging = nullptr;        // pinned host copy the item upload reads
+  uint32_t* queue_head = nullptr;
+  cudaEvent_t staging_done = nullptr;  // the last upload from `staging` has finished
+  bool staging_pending = false;
+  int chunk = 1024, grid_mult = 1;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int key_n = 0;
+  mrr_ctx* key_ctx[MAX_BATCH] = {};
+  mrr_gbuffer key_frame[MAX_BATCH];
+  float* key_out[MAX_BATCH] = {};
+  int key_chunk = 0, key_grid = 0;
+  uint64_t key_kernels = 0;
+  std::string err;
+};
+
 namespace {
 
 constexpr int MAX_DIM = 16384;
@@ -596,6 +614,219 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
 }
 
 uint64_t mrr_kernel_launches(void) { return mrr::launch_counter().load(); }
+
+mrr_status mrr_batch_create(mrr_batch** out) {
+  if (!out) return MRR_EINVAL;
+  *out = nullptr;
+  mrr_batch* b = new (std::nothrow) mrr_batch();
+  if (!b) return MRR_ENOMEM;
+  bool ok = cudaMalloc(&b->items_dev, MAX_BATCH * sizeof(BatchItem)) == cudaSuccess &&
+            cudaMallocHost(&b->staging, MAX_BATCH * sizeof(BatchItem)) == cudaSuccess &&
+            cudaMalloc(&b->queue_head, sizeof(uint32_t)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->staging_done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    mrr_batch_destroy(b);
+    return MRR_ENOMEM;
+  }
+  *out = b;
+  return MRR_OK;
+}
+
+void mrr_batch_destroy(mrr_batch* b) {
+  if (!b) return;
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->staging_done) cudaEventDestroy(b->staging_done);
+  cudaFree(b->items_dev);
+  cudaFreeHost(b->staging);
+  cudaFree(b->queue_head);
+  delete b;
+}
+
+namespace {
+
+mrr_status batch_fail(mrr_batch* b, mrr_status st, const char* msg) {
+  b->err = msg;
+  return st;
+}
+
+mrr_status check_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n) {
+  if (!ctxs || !frames || n < 1 || n > MAX_BATCH) return batch_fail(b, MRR_EINVAL, "need 1..8 frames");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return batch_fail(b, MRR_EINVAL, "null context");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return batch_fail(b, MRR_EINVAL, "a context appears twice in the batch");
+    mrr_status st = check_gbuffer(ctxs[k], &frames[k]);
+    if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
+    if (frames[k].width > ctxs[k]->pool_W || frames[k].height > ctxs[k]->pool_H)
+      return batch_fail(b, MRR_EINVAL, "a frame exceeds its context's max size");
+    if (outs && (!outs[k] || !aligned(outs[k], ctxs[k]->cfg.effect == MRR_SSGI ? 16 : 4)))
+      return batch_fail(b, MRR_EINVAL, "output is NULL or misaligned");
+  }
+  return MRR_OK;
+}
+
+// The batch's launches: per-frame edges + masks, the item upload, one batched shading
+// launch, per-frame merges.  outs == NULL stops after the shading launch (tuning).
+mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n,
+                          int chunk, int grid, cudaStream_t s) {
+  mrr_levels lv[MAX_BATCH];
+  for (int k = 0; k < n; ++k) {
+    mrr_ctx* ctx = ctxs[k];
+    mrr_status st = edges_impl(ctx, &frames[k], ctx->edges, s);
+    if (st != MRR_OK) return st;
+    lv[k] = pool_levels(ctx, frames[k].width, frames[k].height);
+    st = masks_impl(ctx, ctx->edges, &lv[k], s);
+    if (st != MRR_OK) return st;
+  }
+  if (b->staging_pending) {  // the previous upload must have read `staging`
+    if (cudaEventSynchronize(b->staging_done) != cudaSuccess) return batch_fail(b, MRR_ECUDA, "event sync");
+    b->staging_pending = false;
+  }
+  for (int k = 0; k < n; ++k) {
+    mrr_ctx* ctx = ctxs[k];
+    BatchItem& it = b->staging[k];
+    std::memset(&it, 0, sizeof it);
+    it.p = make_shade_params(ctx, frames[k]);
+    it.in = make_frame_in(frames[k]);
+    it.precision = ctx->cfg.precision;
+    for (int i = 0; i < ctx->cfg.num_levels; ++i) {
+      if (!ctx->cfg.enabled[i]) continue;
+      const int q = it.lv.nlev++;
+      it.lv.level[q] = i;
+      it.lv.list[q] = ctx->worklist[i];
+      it.lv.c[q] = ctx->cbuf[i];
+      it.lv.Wi[q] = lv[k].width[i];
+      it.lv.Hi[q] = lv[k].height[i];
+    }
+    it.lv.counts = ctx->counts;
+  }
+  if (cudaMemcpyAsync(b->items_dev, b->staging, n * sizeof(BatchItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return batch_fail(b, MRR_ECUDA, "item upload");
+  if (launch_shade_batch(b->items_dev, n, b->queue_head, chunk, grid, s) != cudaSuccess)
+    return batch_fail(b, MRR_ECUDA, "batched shading launch");
+  if (outs) {
+    for (int k = 0; k < n; ++k) {
+      mrr_status st = merge_impl(ctxs[k], &lv[k], ctxs[k]->cbuf, outs[k], s);
+      if (st != MRR_OK) return st;
+    }
+  }
+  return MRR_OK;
+}
+
+bool batch_key_matches(const mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs,
+                       int n) {
+  if (!b->graph_exec || b->key_n != n || b->key_chunk != b->chunk || b->key_grid != b->grid_mult) return false;
+  for (int k = 0; k < n; ++k) {
+    const mrr_gbuffer key = canonical_key(&frames[k]);
+    if (b->key_ctx[k] != ctxs[k] || b->key_out[k] != outs[k] || std::memcmp(&key, &b->key_frame[k], sizeof key) != 0)
+      return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n,
+                            void* stream) {
+  if (!b) return MRR_EINVAL;
+  if (!outs) return batch_fail(b, MRR_EINVAL, "outs is NULL");
+  mrr_status st = check_batch(b, ctxs, frames, outs, n);
+  if (st != MRR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = batch_grid_blocks() * b->grid_mult;
+  if (!batch_key_matches(b, ctxs, frames, outs, n)) {
+    if (b->graph_exec) {
+      cudaGraphExecDestroy(b->graph_exec);
+      b->graph_exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return batch_fail(b, MRR_ECUDA, "begin capture");
+    const uint64_t before = launch_counter().load();
+    st = batch_launches(b, ctxs, frames, outs, n, b->chunk, grid, b->capture_stream);
+    const uint64_t captured = launch_counter().load() - before;
+    launch_counter().fetch_sub(captured);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (st != MRR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return batch_fail(b, MRR_ECUDA, "end capture");
+    e = cudaGraphInstantiate(&b->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->graph_exec = nullptr;
+      return batch_fail(b, MRR_ECUDA, "graph instantiate");
+    }
+    b->key_n = n;
+    for (int k = 0; k < n; ++k) {
+      b->key_ctx[k] = ctxs[k];
+      b->key_out[k] = outs[k];
+      b->key_frame[k] = canonical_key(&frames[k]);
+    }
+    b->key_chunk = b->chunk;
+    b->key_grid = b->grid_mult;
+    b->key_kernels = captured;
+  }
+  if (cudaGraphLaunch(b->graph_exec, s) != cudaSuccess) return batch_fail(b, MRR_ECUDA, "graph launch");
+  count_launches((int)b->key_kernels);
+  cudaEventRecord(b->staging_done, s);
+  b->staging_pending = true;
+  return MRR_OK;
+}
+
+mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, int n, void* stream,
+                              mrr_batch_tuning* out) {
+  if (!b) return MRR_EINVAL;
+  mrr_status st = check_batch(b, ctxs, frames, nullptr, n);
+  if (st != MRR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // masks and the item table once, then time the batched launch alone
+  st = batch_launches(b, ctxs, frames, nullptr, n, b->chunk, batch_grid_blocks() * b->grid_mult, s);
+  if (st != MRR_OK) return st;
+  cudaEventRecord(b->staging_done, s);
+  b->staging_pending = true;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return batch_fail(b, MRR_ECUDA, "event create");
+  const int chunks[3] = {256, 1024, 4096};
+  float best = 1e30f;
+  int best_chunk = b->chunk, best_mult = b->grid_mult, cand = 0;
+  for (int ci = 0; ci < 3; ++ci)
+    for (int mult = 1; mult <= 2; ++mult) {
+      float t[5];
+      const int grid = batch_grid_blocks() * mult;
+      for (int w = 0; w < 2; ++w) launch_shade_batch(b->items_dev, n, b->queue_head, chunks[ci], grid, s);
+      for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(e0, s);
+        launch_shade_batch(b->items_dev, n, b->queue_head, chunks[ci], grid, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      std::sort(t, t + 5);
+      ++cand;
+      if (t[2] < best) {
+        best = t[2];
+        best_chunk = chunks[ci];
+        best_mult = mult;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return batch_fail(b, MRR_ECUDA, "tuning launch");
+  b->chunk = best_chunk;
+  b->grid_mult = best_mult;
+  if (out) {
+    out->chunk = best_chunk;
+    out->grid_multiplier = best_mult;
+    out->shade_ms = best;
+    out->candidates = cand;
+  }
+  return MRR_OK;
+}
 
 mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tuning* out) {
   if (!ctx) return MRR_EINVAL;

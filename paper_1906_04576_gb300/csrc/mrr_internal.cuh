@@ -111,6 +111,16 @@ struct ShadeLevels {
   const uint32_t* counts;  // device, indexed by level; clamped to W_i * H_i when read
 };
 
+// One frame of a batched shading launch (k_batch.cu); an array of these lives in
+// device memory.
+constexpr int MAX_BATCH = 8;
+struct BatchItem {
+  ShadeParams p;
+  FrameIn in;
+  ShadeLevels lv;
+  int precision;
+};
+
 struct MergeParams {
   int W, H, L, C, half_store;
   int enabled[MRR_MAX_LEVELS];
@@ -133,6 +143,9 @@ cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int preci
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 
 int shade_grid_blocks();  // persistent grid size for the work-list shading kernel
+int batch_grid_blocks();  // resident CTAs of the batched shading kernel
+cudaError_t launch_shade_batch(const BatchItem* items_dev, int nitems, uint32_t* queue_head, int chunk, int grid,
+                               cudaStream_t s);
 
 // Kernels launched by this library in this process (every launcher adds its launches).
 std::atomic<uint64_t>& launch_counter();

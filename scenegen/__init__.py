@@ -209,7 +209,9 @@ WORKLOADS = {
     # soft shadows, 32 blocker + 64 PCF taps, 2048^2 shadow map, 4 levels, 2560x1440
     "ssm_1440p": dict(effect="ssm", width=2560, height=1440, n_boxes=64, n_spheres=16,
                       blocker_samples=32, pcf_samples=64, shadow_size=2048, levels=4),
-    # SSGI, 32 samples, radius 1.0, levels 1, 1/4, 1/8 (the 1/2 level disabled), 3840x2160
+    # SSGI, 32 samples, radius 1.0, levels 1, 1/4, 1/8 (the 1/2 level disabled), 3840x2160,
+    # FP16 storage; batched with SSAO-64 on the same frame in one shading launch
     "ssgi32_4k": dict(effect="ssgi", width=3840, height=2160, n_boxes=64, n_spheres=16,
-                      samples=32, radius=1.0, levels=4),
+                      samples=32, radius=1.0, levels=4, precision="fp16",
+                      batch_with=dict(effect="ssao", samples=64, radius=0.5, levels=4)),
 }
