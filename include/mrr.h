@@ -270,11 +270,70 @@ void mrr_batch_destroy(mrr_batch* b);
 mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n,
                             void* stream);
 
+/* Text of the batch's last failure ("" if none). */
+const char* mrr_batch_last_error(mrr_batch* b);
+
 /* Autotuner of the batched launch: times chunk in {256, 1024, 4096} x grid_multiplier in
  * {1, 2} (median of 5 after 2 warm-ups, CUDA events on `stream`), keeps the fastest in
  * the batch and reports it in *out (may be NULL).  Synchronises `stream`. */
 mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, int n, void* stream,
                               mrr_batch_tuning* out);
+
+/* Serving.  A server renders a stream of frame requests of mixed size and effect.  It
+ * keeps `slots` sets of device state resident (one context per enabled effect -- level
+ * pyramids, work lists, sub-images -- plus a stream and a batch object each); fewer if
+ * creating the next set would leave less than hbm_reserve bytes of free device memory.
+ * A scheduler thread admits pending requests in arrival order as slots free up, packs
+ * up to one request per effect into one batch (one persistent shading launch, see
+ * mrr_render_batch) and overlaps batches on the slots' streams.  Every result equals
+ * mrr_render of the same frame with the same configuration.  The paper renders frames
+ * one by one; this is the serving extension of its Sec. 3 pipeline. */
+typedef struct mrr_server mrr_server;
+
+typedef struct mrr_server_config {
+  mrr_config effect_cfg[3];   /* per effect, indexed by mrr_effect; max_width / max_height = the
+                                 largest frame served with that effect; the tables are copied */
+  int effect_enabled[3];      /* effects this server accepts */
+  int slots;                  /* batches in flight at most (0 = 4) */
+  size_t hbm_reserve;         /* free device memory (bytes) slot creation must leave untouched */
+  int max_queue;              /* pending requests beyond which mrr_submit returns MRR_EBUSY (0 = 1024) */
+  int mock_device_us;         /* test mode: no device work at all; a batch completes after this many
+                                 microseconds of host time (scheduler tests without a GPU) */
+} mrr_server_config;
+
+typedef struct mrr_request {
+  mrr_effect effect;
+  mrr_gbuffer frame;          /* device pointers; must stay valid until the request completes */
+  float* out_dev;             /* output as for mrr_render; written when the request completes */
+} mrr_request;
+
+typedef struct mrr_request_info_t {
+  int done;
+  mrr_status result;
+  int64_t submit_ns, start_ns, done_ns;  /* host steady clock: submitted, dispatched, completed */
+  float device_ms;                       /* device time of the batch the request ran in */
+} mrr_request_info_t;
+
+/* Create a server on the current device (allocates its slots); MRR_ENOMEM if not even
+ * one slot fits.  mrr_server_slots reports how many were created. */
+mrr_status mrr_server_create(const mrr_server_config* cfg, mrr_server** out);
+int mrr_server_slots(mrr_server* s);
+/* Stop the scheduler, wait for work in flight, free everything. */
+void mrr_server_destroy(mrr_server* s);
+
+/* Queue a request; *ticket identifies it.  MRR_EINVAL for an effect the server does not
+ * serve or a frame larger than its context allows; MRR_EBUSY when max_queue requests
+ * are already pending.  Thread-safe. */
+mrr_status mrr_submit(mrr_server* s, const mrr_request* r, uint64_t* ticket);
+/* Non-blocking: *done = 1 once the request has completed; *result its status. */
+mrr_status mrr_poll(mrr_server* s, uint64_t ticket, int* done, mrr_status* result);
+/* Block until the request completes (its status is returned) or timeout_ns elapses
+ * (MRR_ETIMEDOUT); timeout_ns < 0 waits without limit. */
+mrr_status mrr_wait(mrr_server* s, uint64_t ticket, int64_t timeout_ns);
+/* Timing record of a request (valid until mrr_release). */
+mrr_status mrr_request_info(mrr_server* s, uint64_t ticket, mrr_request_info_t* out);
+/* Forget a completed request's record. */
+mrr_status mrr_release(mrr_server* s, uint64_t ticket);
 
 /* Number of kernels this library has launched in this process (all contexts), for
  * accounting of GPU work in benchmarks. */

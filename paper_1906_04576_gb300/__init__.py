@@ -15,6 +15,7 @@ device memory and streams.  The functions carry the C names of include/mrr.h:
     mrr_batch_create() -> Batch         mrr_batch_destroy(b)
     mrr_render_batch(b, ctxs, frames, outs)   mrr_batch_autotune(b, ctxs, frames)
     mrr_masks_static(cfg, edges, levels)
+    mrr_server_create(cfgs) -> Server   mrr_submit / mrr_poll / mrr_wait / mrr_request_info / mrr_release
 
 Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
 ``python paper_1906_04576_gb300/_build.py``): there is no CPU fallback.
@@ -86,6 +87,20 @@ class mrr_tuning(ctypes.Structure):
                 ("shade_full_ms", ctypes.c_float), ("candidates", ctypes.c_int)]
 
 
+class mrr_server_config(ctypes.Structure):
+    _fields_ = [("effect_cfg", mrr_config * 3), ("effect_enabled", ctypes.c_int * 3), ("slots", ctypes.c_int),
+                ("hbm_reserve", ctypes.c_size_t), ("max_queue", ctypes.c_int), ("mock_device_us", ctypes.c_int)]
+
+
+class mrr_request(ctypes.Structure):
+    _fields_ = [("effect", ctypes.c_int), ("frame", mrr_gbuffer), ("out_dev", ctypes.c_void_p)]
+
+
+class mrr_request_info_t(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("result", ctypes.c_int), ("submit_ns", ctypes.c_int64),
+                ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64), ("device_ms", ctypes.c_float)]
+
+
 class mrr_batch_tuning(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int), ("grid_multiplier", ctypes.c_int), ("shade_ms", ctypes.c_float),
                 ("candidates", ctypes.c_int)]
@@ -102,6 +117,24 @@ _lib.mrr_render_batch.restype = ctypes.c_int
 _lib.mrr_batch_autotune.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(mrr_gbuffer), ctypes.c_int, _vp,
                                     ctypes.POINTER(mrr_batch_tuning)]
 _lib.mrr_batch_autotune.restype = ctypes.c_int
+_lib.mrr_batch_last_error.argtypes = [_vp]
+_lib.mrr_batch_last_error.restype = ctypes.c_char_p
+_lib.mrr_server_create.argtypes = [ctypes.POINTER(mrr_server_config), ctypes.POINTER(_vp)]
+_lib.mrr_server_create.restype = ctypes.c_int
+_lib.mrr_server_destroy.argtypes = [_vp]
+_lib.mrr_server_destroy.restype = None
+_lib.mrr_server_slots.argtypes = [_vp]
+_lib.mrr_server_slots.restype = ctypes.c_int
+_lib.mrr_submit.argtypes = [_vp, ctypes.POINTER(mrr_request), ctypes.POINTER(ctypes.c_uint64)]
+_lib.mrr_submit.restype = ctypes.c_int
+_lib.mrr_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+_lib.mrr_poll.restype = ctypes.c_int
+_lib.mrr_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64]
+_lib.mrr_wait.restype = ctypes.c_int
+_lib.mrr_request_info.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(mrr_request_info_t)]
+_lib.mrr_request_info.restype = ctypes.c_int
+_lib.mrr_release.argtypes = [_vp, ctypes.c_uint64]
+_lib.mrr_release.restype = ctypes.c_int
 _lib.mrr_autotune.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, ctypes.POINTER(mrr_tuning)]
 _lib.mrr_autotune.restype = ctypes.c_int
 _lib.mrr_level_dims.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -425,7 +458,7 @@ def mrr_render_batch(b: Batch, ctxs: list, frames: list, outs: list, stream=None
     oa = (_vp * n)(*[_ptr(o) for o in outs])
     st = _lib.mrr_render_batch(b.handle, ca, fa, oa, n, _stream(stream))
     if st != MRR_OK:
-        raise MrrError(st, "mrr_render_batch")
+        raise MrrError(st, "mrr_render_batch: " + _lib.mrr_batch_last_error(b.handle).decode())
 
 
 def mrr_batch_autotune(b: Batch, ctxs: list, frames: list, stream=None) -> dict:
@@ -433,8 +466,93 @@ def mrr_batch_autotune(b: Batch, ctxs: list, frames: list, stream=None) -> dict:
     t = mrr_batch_tuning()
     st = _lib.mrr_batch_autotune(b.handle, ca, fa, n, _stream(stream), ctypes.byref(t))
     if st != MRR_OK:
-        raise MrrError(st, "mrr_batch_autotune")
+        raise MrrError(st, "mrr_batch_autotune: " + _lib.mrr_batch_last_error(b.handle).decode())
     return {k: getattr(t, k) for k, _ in mrr_batch_tuning._fields_}
+
+
+@dataclass
+class Server:
+    handle: int
+    _keep: list = field(default_factory=list)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _lib.mrr_server_destroy(h)
+            except Exception:
+                pass
+            self.handle = 0
+
+
+def mrr_server_create(effect_cfgs: dict, slots: int = 4, hbm_reserve: int = 0, max_queue: int = 0,
+                      mock_device_us: int = 0) -> Server:
+    """effect_cfgs: {'ssao': cfg, 'ssm': cfg, 'ssgi': cfg} (any subset)."""
+    sc = mrr_server_config()
+    keep = []
+    for name, cfg in effect_cfgs.items():
+        c, k = make_config(cfg)
+        keep.append(k)
+        e = EFFECTS[name]
+        sc.effect_cfg[e] = c
+        sc.effect_enabled[e] = 1
+    sc.slots, sc.hbm_reserve, sc.max_queue, sc.mock_device_us = slots, hbm_reserve, max_queue, mock_device_us
+    h = _vp()
+    st = _lib.mrr_server_create(ctypes.byref(sc), ctypes.byref(h))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_server_create")
+    return Server(h.value)
+
+
+def mrr_server_destroy(s: Server) -> None:
+    if s.handle:
+        _lib.mrr_server_destroy(s.handle)
+        s.handle = 0
+
+
+def mrr_server_slots(s: Server) -> int:
+    return _lib.mrr_server_slots(s.handle)
+
+
+def mrr_submit(s: Server, effect: str, frame=None, out: torch.Tensor | None = None) -> int:
+    """Queue a request (frame: DeviceFrame or, in mock mode, (width, height)); returns its ticket."""
+    r = mrr_request()
+    r.effect = EFFECTS[effect]
+    if isinstance(frame, DeviceFrame):
+        r.frame = frame.struct()
+    elif frame is not None:
+        r.frame.width, r.frame.height = frame
+    r.out_dev = _ptr(out) if out is not None else None
+    t = ctypes.c_uint64()
+    st = _lib.mrr_submit(s.handle, ctypes.byref(r), ctypes.byref(t))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_submit")
+    return t.value
+
+
+def mrr_poll(s: Server, ticket: int):
+    done, res = ctypes.c_int(), ctypes.c_int()
+    st = _lib.mrr_poll(s.handle, ticket, ctypes.byref(done), ctypes.byref(res))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_poll")
+    return bool(done.value), res.value
+
+
+def mrr_wait(s: Server, ticket: int, timeout_ns: int = -1) -> int:
+    """Returns the request's status, or MRR_ETIMEDOUT."""
+    return _lib.mrr_wait(s.handle, ticket, timeout_ns)
+
+
+def mrr_request_info(s: Server, ticket: int) -> dict:
+    i = mrr_request_info_t()
+    st = _lib.mrr_request_info(s.handle, ticket, ctypes.byref(i))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_request_info")
+    return {k: getattr(i, k) for k, _ in mrr_request_info_t._fields_}
+
+
+def mrr_release(s: Server, ticket: int) -> None:
+    _check(None, _lib.mrr_release(s.handle, ticket)) if False else _lib.mrr_release(s.handle, ticket)
 
 
 def mrr_kernel_launches() -> int:

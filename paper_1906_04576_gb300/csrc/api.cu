@@ -675,14 +675,10 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
   for (int k = 0; k < n; ++k) {
     mrr_ctx* ctx = ctxs[k];
     mrr_status st = edges_impl(ctx, &frames[k], ctx->edges, s);
-    if (st != MRR_OK) return st;
+    if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
     lv[k] = pool_levels(ctx, frames[k].width, frames[k].height);
     st = masks_impl(ctx, ctx->edges, &lv[k], s);
-    if (st != MRR_OK) return st;
-  }
-  if (b->staging_pending) {  // the previous upload must have read `staging`
-    if (cudaEventSynchronize(b->staging_done) != cudaSuccess) return batch_fail(b, MRR_ECUDA, "event sync");
-    b->staging_pending = false;
+    if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
   }
   for (int k = 0; k < n; ++k) {
     mrr_ctx* ctx = ctxs[k];
@@ -709,8 +705,18 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
   if (outs) {
     for (int k = 0; k < n; ++k) {
       mrr_status st = merge_impl(ctxs[k], &lv[k], ctxs[k]->cbuf, outs[k], s);
-      if (st != MRR_OK) return st;
+      if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
     }
+  }
+  return MRR_OK;
+}
+
+// Wait until the last item upload has read `staging` (never while capturing: a
+// capturing thread may not wait on events).
+mrr_status wait_staging(mrr_batch* b) {
+  if (b->staging_pending) {
+    if (cudaEventSynchronize(b->staging_done) != cudaSuccess) return batch_fail(b, MRR_ECUDA, "event sync");
+    b->staging_pending = false;
   }
   return MRR_OK;
 }
@@ -741,6 +747,8 @@ mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffe
       cudaGraphExecDestroy(b->graph_exec);
       b->graph_exec = nullptr;
     }
+    st = wait_staging(b);
+    if (st != MRR_OK) return st;
     if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return batch_fail(b, MRR_ECUDA, "begin capture");
     const uint64_t before = launch_counter().load();
@@ -753,7 +761,7 @@ mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffe
       if (graph) cudaGraphDestroy(graph);
       return st;
     }
-    if (e != cudaSuccess) return batch_fail(b, MRR_ECUDA, "end capture");
+    if (e != cudaSuccess) return batch_fail(b, MRR_ECUDA, cudaGetErrorString(e));
     e = cudaGraphInstantiate(&b->graph_exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -777,6 +785,27 @@ mrr_status mrr_render_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffe
   return MRR_OK;
 }
 
+const char* mrr_batch_last_error(mrr_batch* b) { return b ? b->err.c_str() : "no batch"; }
+
+}  // extern "C"
+
+// Serving: enqueue a batch with direct launches (no graph: every serving batch has new
+// frames) on `stream`.  Not part of the C ABI.
+mrr_status mrr_batch_enqueue_direct(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames,
+                                    float* const* outs, int n, cudaStream_t stream) {
+  mrr_status st = check_batch(b, ctxs, frames, outs, n);
+  if (st != MRR_OK) return st;
+  st = wait_staging(b);
+  if (st != MRR_OK) return st;
+  st = batch_launches(b, ctxs, frames, outs, n, b->chunk, batch_grid_blocks() * b->grid_mult, stream);
+  if (st != MRR_OK) return st;
+  cudaEventRecord(b->staging_done, stream);
+  b->staging_pending = true;
+  return MRR_OK;
+}
+
+extern "C" {
+
 mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, int n, void* stream,
                               mrr_batch_tuning* out) {
   if (!b) return MRR_EINVAL;
@@ -784,6 +813,8 @@ mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuf
   if (st != MRR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // masks and the item table once, then time the batched launch alone
+  st = wait_staging(b);
+  if (st != MRR_OK) return st;
   st = batch_launches(b, ctxs, frames, nullptr, n, b->chunk, batch_grid_blocks() * b->grid_mult, s);
   if (st != MRR_OK) return st;
   cudaEventRecord(b->staging_done, s);

@@ -152,3 +152,7 @@ std::atomic<uint64_t>& launch_counter();
 inline void count_launches(int n) { launch_counter().fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 }  // namespace mrr
+
+// Serving uses the batch path without graph capture (api.cu).
+mrr_status mrr_batch_enqueue_direct(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames,
+                                    float* const* outs, int n, cudaStream_t stream);

@@ -214,4 +214,12 @@ WORKLOADS = {
     "ssgi32_4k": dict(effect="ssgi", width=3840, height=2160, n_boxes=64, n_spheres=16,
                       samples=32, radius=1.0, levels=4, precision="fp16",
                       batch_with=dict(effect="ssao", samples=64, radius=0.5, levels=4)),
+    # serving mix: Poisson arrivals at 400/s, uniform over these resolutions x effects
+    "serve_mix": dict(effect="mix", rate=400.0, requests=800,
+                      resolutions=[(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)],
+                      effects=[dict(effect="ssao", samples=64, radius=0.5, levels=4, precision="fp32"),
+                               dict(effect="ssm", blocker_samples=32, pcf_samples=64, shadow_size=2048, levels=4,
+                                    precision="fp32"),
+                               dict(effect="ssgi", samples=32, radius=1.0, levels=4, precision="fp16")],
+                      n_boxes=64, n_spheres=16, scenes_per_resolution=2, slots=4),
 }
