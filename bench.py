@@ -319,13 +319,19 @@ def run_serve(args, mrr, sg, wl, rank, world, dist):
     return 0
 
 
-def max_reduce(dist, x):
+def max_reduce(dist, x, device="cuda"):
+    """The maximum of x over all ranks (x itself without a process group)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mpix_s(world, steps, pixels_per_step, slowest_rank_ms):
+    """Throughput of the whole job: every rank's pixels over the slowest rank's time."""
+    return world * steps * pixels_per_step / (slowest_rank_ms * 1e-3) / 1e6
 
 
 def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
@@ -382,19 +388,15 @@ def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
     clocks = sampler.stop()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_reduce(dist, x)
 
     rmse = []
     for o, f_ in zip(outs, fulls):
         d = (o - f_)[..., :3] if o.dim() == 3 else (o - f_)
         rmse.append(float(torch.sqrt(torch.mean(d.double() ** 2)).item()))
-    px = world * args.steps * 2 * W * H
     sb, sf = max_over_ranks(sum(t_b)), max_over_ranks(sum(t_f))
-    value, fvalue = px / (sb * 1e-3) / 1e6, px / (sf * 1e-3) / 1e6
+    value = whole_job_mpix_s(world, args.steps, 2 * W * H, sb)
+    fvalue = whole_job_mpix_s(world, args.steps, 2 * W * H, sf)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -468,11 +470,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_reduce(dist, x)
 
     def timed(fn, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -568,9 +566,8 @@ def main():
 
     sum_multi = max_over_ranks(sum(t_multi))
     sum_full = max_over_ranks(sum(t_full))
-    px = world * args.steps * W * H
-    value = px / (sum_multi * 1e-3) / 1e6
-    full_value = px / (sum_full * 1e-3) / 1e6
+    value = whole_job_mpix_s(world, args.steps, W * H, sum_multi)
+    full_value = whole_job_mpix_s(world, args.steps, W * H, sum_full)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
