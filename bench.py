@@ -108,6 +108,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+SHADE_SOURCES = ["paper_1906_04576_gb300/csrc/k_shade.cu", "paper_1906_04576_gb300/csrc/shade_common.cuh",
+                 "paper_1906_04576_gb300/csrc/mrr_internal.cuh"]
+
+
+def shade_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SHADE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the work-list kernel from a committed ncu capture
+    (profiles/traffic_<workload>.json), only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d["dram_bytes_per_launch"] if d.get("sources_sha") == shade_sources_sha() else None
+
+
 def algorithmic_bytes(cfg, n_nonsky, n_sky):
     """Bytes the shading kernel must move per launch by definition of the effect:
     per non-sky texel its depth + normal, every sample's gathers and the store; per sky
@@ -586,7 +610,7 @@ def main():
             "rmse_vs_full_res": rmse,
             "shaded_texels": n_all, "shaded_fraction": round(n_all / (W * H), 5),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": measured_traffic(args.workload),
                          "kernel": "shade_levels_kernel", "kernel_ms": round(k_ms, 5),
                          "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": round(world * e2e_steps * W * H / e2e_s / 1e6, 3), "unit": "Mpix/s",

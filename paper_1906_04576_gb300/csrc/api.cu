@@ -888,10 +888,15 @@ mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tu
   cudaEvent_t e0, e1;
   MRR_CUDA(ctx, cudaEventCreate(&e0));
   MRR_CUDA(ctx, cudaEventCreate(&e1));
+  // a buffer larger than L2, rewritten before every timed launch so each one starts cold
+  const size_t flush_bytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) flush = nullptr;
   auto median_ms = [&](auto&& launch) -> float {
     float t[5];
     for (int w = 0; w < 2; ++w) launch();
     for (int r = 0; r < 5; ++r) {
+      if (flush) cudaMemsetAsync(flush, r, flush_bytes, s);
       cudaEventRecord(e0, s);
       launch();
       cudaEventRecord(e1, s);
@@ -941,6 +946,7 @@ mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tu
   cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(tmp);
+  cudaFree(flush);
   MRR_CUDA(ctx, cudaGetLastError());
   ctx->split_texel = best_lanes;
   ctx->split_pixel = best_pix;

@@ -114,10 +114,22 @@ __global__ void __launch_bounds__(256, 2) shade_full_kernel(ShadeParams p, Frame
   if (valid && (threadIdx.x & (SPLIT - 1)) == 0) store_value<EFFECT>(out, (size_t)y * p.v.W + x, v, false);
 }
 
+// Resident CTAs of one instantiation (SMs x CTAs per SM), computed once per instantiation.
+template <typename K> int resident_blocks(K kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, SHADE_THREADS, 0);
+  return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
+// `grid_mult` x the resident CTAs of this very instantiation: a persistent grid that is
+// one full wave (or a whole number of waves), never 1.2.
 template <int EFFECT, typename NT, typename SMT, int SPLIT>
-void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid,
+void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid_mult,
                      cudaStream_t s) {
-  shade_levels_kernel<EFFECT, NT, SMT, SPLIT><<<grid, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
+  static const int resident = resident_blocks(shade_levels_kernel<EFFECT, NT, SMT, SPLIT>);
+  shade_levels_kernel<EFFECT, NT, SMT, SPLIT><<<resident * grid_mult, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
 }
 
 template <int EFFECT, typename NT, typename SMT, int SPLIT>
@@ -128,7 +140,7 @@ void launch_full_t(const ShadeParams& p, const FrameIn& in, float* out, cudaStre
 
 template <typename NT, typename SMT>
 void levels_dispatch(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid,
-                     int split, cudaStream_t s) {
+                     int split, cudaStream_t s) {  // grid: multiple of the resident CTAs
   switch (p.effect) {
     case MRR_SSAO:
       if (split >= 4) launch_levels_t<MRR_SSAO, NT, SMT, 4>(p, in, lv, half_store, grid, s);
@@ -168,20 +180,7 @@ std::atomic<uint64_t>& launch_counter() {
   return n;
 }
 
-int shade_grid_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shade_levels_kernel<MRR_SSAO, float4, float, 1>,
-                                                  SHADE_THREADS, 0);
-    if (sms <= 0) sms = 1;
-    if (per_sm <= 0) per_sm = 1;
-    blocks = sms * per_sm;
-  }
-  return blocks;
-}
+int shade_grid_blocks() { return 1; }  // the launch scales the resident CTAs of its own variant
 
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
                                 int grid, int split, cudaStream_t s) {

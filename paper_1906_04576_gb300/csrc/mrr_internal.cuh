@@ -142,7 +142,7 @@ cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int preci
                               cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 
-int shade_grid_blocks();  // persistent grid size for the work-list shading kernel
+int shade_grid_blocks();  // grid multiplier base of the work-list kernel (grid = multiple of its resident CTAs)
 int batch_grid_blocks();  // resident CTAs of the batched shading kernel
 cudaError_t launch_shade_batch(const BatchItem* items_dev, int nitems, uint32_t* queue_head, int chunk, int grid,
                                cudaStream_t s);
