@@ -188,6 +188,11 @@ ShadeParams make_shade_params(const mrr_ctx* ctx, const mrr_gbuffer& g) {
   p.nb = c.blocker_samples;
   p.np = c.pcf_samples;
   std::memcpy(p.kernel, ctx->kernel, sizeof p.kernel);
+  for (int j = 0; j < MRR_MAX_SAMPLES; ++j) {
+    p.kx[j] = ctx->kernel[j].x;
+    p.ky[j] = ctx->kernel[j].y;
+    p.kz[j] = ctx->kernel[j].z;
+  }
   std::memcpy(p.btaps, ctx->btaps, sizeof p.btaps);
   std::memcpy(p.ptaps, ctx->ptaps, sizeof p.ptaps);
   return p;

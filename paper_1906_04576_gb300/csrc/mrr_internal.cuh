@@ -50,7 +50,8 @@ struct ShadeParams {
   float radius, ao_bias, gi_min_dist2;
   float light_half, shadow_bias;
   int nb, np;
-  float4 kernel[MRR_MAX_SAMPLES];
+  float4 kernel[MRR_MAX_SAMPLES];                  // (x, y, z, 0) per sample
+  float kx[MRR_MAX_SAMPLES], ky[MRR_MAX_SAMPLES], kz[MRR_MAX_SAMPLES];  // the same, split for paired loads
   float2 btaps[MRR_MAX_TAPS];
   float2 ptaps[MRR_MAX_TAPS];
 };
