@@ -32,6 +32,7 @@ struct mrr_ctx {
   uint32_t* counts = nullptr;
   uint32_t* chunk_counts = nullptr;
   size_t chunk_cap = 0;
+  float* lut0 = nullptr;  // level 0's horizontal blur table (device), see MaskParams
   // pools of mrr_render_host
   float* h_depth = nullptr;
   void* h_normal = nullptr;
@@ -245,6 +246,7 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
     m.stencil[i] = lv->stencil[i];
   }
   m.label = lv->label;
+  m.lut0 = ctx->lut0;
   MRR_CUDA(ctx, launch_masks(m, E, s));
   // work lists of every enabled level in one two-pass compaction
   CompactParams cp;
@@ -424,6 +426,7 @@ void free_pools(mrr_ctx* ctx) {
   }
   cudaFree(ctx->counts);
   cudaFree(ctx->chunk_counts);
+  cudaFree(ctx->lut0);
   cudaFree(ctx->h_depth);
   cudaFree(ctx->h_normal);
   cudaFree(ctx->h_color);
@@ -448,6 +451,20 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
       MRR_CUDA(ctx, cudaMalloc(&ctx->cbuf[i], n * cbytes(c)));
     }
     chunks += (n + COMPACT_CHUNK - 1) / COMPACT_CHUNK;
+  }
+  // level 0's horizontal blur for every (2R+1)-bit window, summed exactly as the
+  // definition sums it: ascending taps, s = s + g[t] for every set tap, in float
+  if (c.enabled[0] && c.num_levels > 1 && !c.force_level0 && ctx->R[0] > 0 && (1 << (2 * ctx->R[0] + 1)) <= MASK_LUT_MAX) {
+    const int n = 1 << (2 * ctx->R[0] + 1);
+    float host[MASK_LUT_MAX];
+    for (int b = 0; b < n; ++b) {
+      float acc = 0.0f;
+      for (int t = 0; t <= 2 * ctx->R[0]; ++t)
+        if ((b >> t) & 1) acc = acc + ctx->gauss[0][t];
+      host[b] = acc;
+    }
+    MRR_CUDA(ctx, cudaMalloc(&ctx->lut0, n * sizeof(float)));
+    MRR_CUDA(ctx, cudaMemcpy(ctx->lut0, host, n * sizeof(float), cudaMemcpyHostToDevice));
   }
   MRR_CUDA(ctx, cudaMalloc(&ctx->counts, MRR_MAX_LEVELS * sizeof(uint32_t)));
   MRR_CUDA(ctx, cudaMemset(ctx->counts, 0, MRR_MAX_LEVELS * sizeof(uint32_t)));

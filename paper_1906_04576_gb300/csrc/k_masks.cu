@@ -41,12 +41,22 @@ template <> struct LevelShape<-1> {
   static constexpr int OFF = 0;
 };
 
+constexpr int EW = (ES + 31) / 32;      // 32-bit words per staged edge row
+
 struct MaskSmem {
   uint8_t E[ES][ES];
+  uint32_t Ebits[ES][EW + 1];           // the same rows as bit masks (one spare word for shifts)
   uint8_t D[DMAX * DMAX];
   float h[DMAX * TS];
   uint8_t S[S_TOTAL];
+  float lut[MASK_LUT_MAX];
 };
+
+// Bits [c, c + n) of staged edge row r (n <= 32), bit 0 = column c.
+__device__ __forceinline__ uint32_t ebits_window(const MaskSmem& sm, int r, int c) {
+  const int w = c >> 5, o = c & 31;
+  return __funnelshift_r(sm.Ebits[r][w], sm.Ebits[r][w + 1], o);
+}
 
 // Level I with blur radius R (both compile-time): D over the tile + R halo, the two
 // blur passes, the stencil with nesting from level P (P < 0: none), and the stores.
@@ -59,6 +69,29 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
   float g[2 * R + 1];
 #pragma unroll
   for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[I][t];
+  bool blur;
+  if (I == 0) {
+    // level 0: D is the edge image itself, so each horizontal window is a slice of a
+    // staged bit row; the table (or the taps over the window's bits) gives its sum
+    int anyh = 0;
+    constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
+    const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
+    for (int k = tid; k < DN * Ti; k += MTHREADS) {
+      const int r = k / Ti, c = k - r * Ti;
+      const uint32_t win = ebits_window(sm, MG - R + r, MG - R + c) & WMASK;
+      float s = 0.0f;
+      if (use_lut) {
+        s = sm.lut[win];
+      } else {
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t)
+          if ((win >> t) & 1u) s = s + g[t];
+      }
+      sm.h[k] = s;
+      anyh |= win != 0u;
+    }
+    blur = __syncthreads_or(anyh) != 0;
+  } else {
   // D_I over the tile and its R halo; E outside the image is staged as 0
   int anyd = 0;
   for (int k = tid; k < DN * DN; k += MTHREADS) {
@@ -76,7 +109,7 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
     anyd |= v;
   }
   // no edge within reach of the tile: a_I = 0 here and the blur passes add only zeros
-  const bool blur = __syncthreads_or(anyd) != 0;
+  blur = __syncthreads_or(anyd) != 0;
   if (blur) {
   // horizontal pass: with D in {0,1}, fma(g, D, s) is s + g where D is set and s elsewhere
   for (int k = tid; k < DN * Ti; k += MTHREADS) {
@@ -89,6 +122,7 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
     sm.h[k] = s;
   }
   __syncthreads();
+  }
   }
   // vertical pass, stencil, nesting, stores
   uint8_t* Si = sm.S + LevelShape<I>::OFF;
@@ -198,6 +232,21 @@ __global__ void __launch_bounds__(MTHREADS) masks_kernel(MaskParams m, const uin
       const int y = y0 - MG + r, x = x0 - MG + c;
       sm.E[r][c] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(E + (size_t)y * W + x) : 0;
     }
+  }
+  __syncthreads();
+  // bit rows of the staged edge image (bit c of word c/32 = column c) and the level-0 table
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < ES; r += MTHREADS / 32) {
+#pragma unroll
+      for (int w = 0; w <= EW; ++w) {
+        const int c = w * 32 + lane;
+        const uint32_t b = __ballot_sync(0xffffffffu, c < ES && sm.E[r][c] != 0);
+        if (lane == 0) sm.Ebits[r][w] = b;
+      }
+    }
+    if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
+      for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   }
   __syncthreads();
   all_levels(m, sm, x0, y0);

@@ -84,7 +84,11 @@ struct MaskParams {
   float* alpha[MRR_MAX_LEVELS];
   uint8_t* stencil[MRR_MAX_LEVELS];
   uint8_t* label;                // [H][W] or null
+  // level 0's horizontal blur as a table: lut0[b] = the ascending-tap sum of g over the
+  // set bits of the (2R+1)-bit window b (null: sum the taps directly; R <= 5 only)
+  const float* lut0;
 };
+constexpr int MASK_LUT_MAX = 2048;
 
 // Work-list compaction of all levels in one launch: level l owns chunks
 // [chunk_begin[l], chunk_begin[l+1]) of COMPACT_CHUNK texels each.
