@@ -1,16 +1,18 @@
 // k_masks.cu -- the per-level masks of Sec. 3.1 / Table 1, the stencil of Sec. 4.1 and
 // the dense work lists that replace the stencil test on the GPU.
 //
-// masks_kernel: ONE launch computes every level.  A CTA owns a 32x32 full-resolution
-//   tile (16x16 at level 1, 8x8 at level 2, ...) and stages the edge image of the tile
-//   plus a 24-pixel halo in shared memory once.  For each blurred level i it forms the
-//   downsampled edge image D_i (block maximum) over the tile and an R_i halo, blurs it
-//   horizontally then vertically (taps in ascending order, one fused multiply-add each,
-//   the Gaussian held in registers), sets S_i = [a_i > 0] OR-ed with the set texels of
-//   the previous enabled finer level inside the block (inclusive nesting, Fig. 2/3 --
-//   the children of a texel always lie in the same tile), and writes a_i, S_i.  The
-//   coarsest level is written as a = 1, S = 1; disabled levels as 0.  Finally every
-//   pixel's owning level (the finest enabled level whose stencil covers it).
+// masks_kernel: ONE launch computes every level, bit-parallel.  A CTA owns a 32x32
+//   full-resolution tile (16x16 at level 1, 8x8 at level 2, ...) and stages the edge
+//   image of the tile plus a 24-pixel halo as bit rows (one ballot per 32 pixels).  For
+//   each blurred level i it forms the downsampled edge image D_i (block maximum: the OR
+//   of 2^i staged rows, each group of 2^i bits OR-ed into one) over the tile and an R_i
+//   halo, takes the horizontal blur of every texel from its (2R_i+1)-bit window (at
+//   level 0 through a table of the exact window sums), the vertical blur with one fused
+//   multiply-add per tap in ascending order, sets S_i = [a_i > 0] OR-ed with its children
+//   in the previous enabled finer level (inclusive nesting, Fig. 2/3 -- children always
+//   lie in the same tile) and writes a_i, S_i.  The coarsest level is written as a = 1,
+//   S = 1; disabled levels as 0.  Finally every pixel's owning level (the finest enabled
+//   level whose stencil covers it), read from the stencil bit rows.
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
 //   every level's stencil into a row-major list of (y << 16) | x.  Pass 1 counts the set
 //   texels of each 4096-texel chunk; pass 2 gives each chunk its exclusive prefix (a
@@ -24,166 +26,236 @@ namespace mrr {
 
 namespace {
 
-constexpr int TS = MASK_TILE;            // 32
-constexpr int MG = MASK_MARGIN;          // 24
-constexpr int ES = TS + 2 * MG;          // 80: staged edge image side
+constexpr int TS = MASK_TILE;            // 32: tile side (full-resolution pixels)
+constexpr int MG = MASK_MARGIN;          // 24: halo rows above / below the tile
+constexpr int ER = TS + 2 * MG;          // 80 staged edge rows
+constexpr int EWORDS = 3;                // 96 staged edge columns: [x0 - 32, x0 + 64)
+constexpr int EX = 32;                   // column of the tile's first pixel in the staged rows
 constexpr int MAXR = 6;
-constexpr int DMAX = TS + 2 * MAXR;      // 44: largest D region side (level 0)
-constexpr int MTHREADS = 256;            // as 32 x 8
-constexpr int S_TOTAL = TS * TS + (TS / 2) * (TS / 2) + (TS / 4) * (TS / 4) + (TS / 8) * (TS / 8);
-
-template <int I> struct LevelShape {  // level I of a tile: side, smem stencil offset
-  static constexpr int T = TS >> I;
-  static constexpr int OFF = I == 0 ? 0 : LevelShape<I - 1>::OFF + (TS >> (I - 1)) * (TS >> (I - 1));
-};
-template <> struct LevelShape<-1> {
-  static constexpr int T = 0;
-  static constexpr int OFF = 0;
-};
-
-constexpr int EW = (ES + 31) / 32;      // 32-bit words per staged edge row
+constexpr int DROWS = TS / 2 + 2 * MAXR; // 28: largest D region side above level 0 (level 1)
+constexpr int MTHREADS = 256;            // 8 warps
+constexpr int ROWS0 = TS / (MTHREADS / 32);  // level-0 tile rows per warp
+static_assert(ER % (MTHREADS / 32) == 0, "edge rows split evenly over the warps");
+static_assert(DROWS <= 32, "a D row of a level above 0 fits one word");
 
 struct MaskSmem {
-  uint8_t E[ES][ES];
-  uint32_t Ebits[ES][EW + 1];           // the same rows as bit masks (one spare word for shifts)
-  uint8_t D[DMAX * DMAX];
-  float h[DMAX * TS];
-  uint8_t S[S_TOTAL];
+  uint4 E[ER];                           // edge rows as bits: word w bit b = column 32 w + b (w = 3: zero)
+  uint32_t D[DROWS];                     // D_i rows of the current level >= 1 as bits
+  float h[DROWS * TS / 2];               // horizontal pass of the current level >= 1
+  float g[MRR_MAX_LEVELS][16];           // the Gaussians of Table 1
+  uint32_t S[MRR_MAX_LEVELS][TS];        // stencil rows of every level as bits (tile texels only)
   float lut[MASK_LUT_MAX];
 };
 
-// Bits [c, c + n) of staged edge row r (n <= 32), bit 0 = column c.
-__device__ __forceinline__ uint32_t ebits_window(const MaskSmem& sm, int r, int c) {
-  const int w = c >> 5, o = c & 31;
-  return __funnelshift_r(sm.Ebits[r][w], sm.Ebits[r][w + 1], o);
+// Sum of the taps g[t] whose bit t is set in win, in ascending t, one rounding per add.
+__device__ __forceinline__ float window_sum(uint32_t win, const float* g) {
+  float s = 0.0f;
+  while (win) {
+    const int t = __ffs(win) - 1;
+    s = s + g[t];
+    win &= win - 1u;
+  }
+  return s;
 }
 
-// Level I with blur radius R (both compile-time): D over the tile + R halo, the two
-// blur passes, the stencil with nesting from level P (P < 0: none), and the stores.
-template <int I, int R, int P>
-__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  constexpr int Ti = LevelShape<I>::T, DN = Ti + 2 * R, BS = 1 << I;
-  const int tid = threadIdx.x;
-  const int q0x = x0 >> I, q0y = y0 >> I;
-  const int Wi = m.Wi[I], Hi = m.Hi[I];
+// One bit per aligned group of G bits: bit j of the result is the OR of bits
+// [G j, G j + G) of w.
+template <int G>
+__device__ __forceinline__ uint32_t group_or(uint32_t w) {
+  static_assert(G == 2 || G == 4, "levels 1 and 2");
+  uint32_t x;
+  if (G == 2) {
+    x = (w | (w >> 1)) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+  } else {
+    x = w | (w >> 1);
+    x = (x | (x >> 2)) & 0x11111111u;
+    x = (x | (x >> 3)) & 0x03030303u;
+    x = (x | (x >> 6)) & 0x000F000Fu;
+    x = (x | (x >> 12)) & 0x000000FFu;
+  }
+  return x;
+}
+
+// Row t of D_I over the D region (DN = Ti + 2R texels from level row q0y - R and level
+// column q0x - R): the OR of the 2^I staged rows of the block row, each aligned group of
+// 2^I bits reduced to one.  Edges outside the image are staged as zeros, so blocks outside
+// the level give 0, as the block maximum must.
+template <int I, int R>
+__device__ __forceinline__ uint32_t d_row(const MaskSmem& sm, int t) {
+  constexpr int G = 1 << I, DN = (TS >> I) + 2 * R;
+  constexpr int row0 = MG - R * G, col0 = EX - R * G;
+  static_assert(row0 >= 0 && col0 >= 0 && col0 % G == 0, "halo inside the staged rows");
+  uint4 e = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    const uint4 w = sm.E[row0 + t * G + k];
+    e.x |= w.x;
+    e.y |= w.y;
+    e.z |= w.z;
+  }
+  const unsigned long long full = (unsigned long long)group_or<G>(e.x) |
+                                  ((unsigned long long)group_or<G>(e.y) << (32 / G)) |
+                                  ((unsigned long long)group_or<G>(e.z) << (64 / G));
+  return (uint32_t)(full >> (col0 / G)) & ((1u << DN) - 1u);
+}
+
+// Ballot per-lane stencil decisions of a (Ti x Ti) level into row bit masks; texel
+// k = r * Ti + c is handled by thread k.
+template <int Ti>
+__device__ __forceinline__ void store_rows(uint32_t* rows, int k, bool st) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t b = __ballot_sync(0xffffffffu, st);
+  if (k >= Ti * Ti) return;  // the whole row group lies past the level's last texel
+  if (Ti >= 32) {
+    if (lane == 0) rows[k / Ti] = b;
+  } else if ((lane % Ti) == 0) {
+    rows[k / Ti] = (b >> lane) & ((1u << (Ti & 31)) - 1u);
+  }
+}
+
+// Level 0 with radius R: D_0 is the edge image itself.  Warp w owns tile rows
+// [ROWS0 w, ROWS0 w + ROWS0), lane = column; the lane takes the horizontal sums of the
+// ROWS0 + 2R rows it needs from their bit windows (a table of exact window sums where
+// one is given) and the vertical taps from registers.
+template <int R>
+__device__ __forceinline__ void level0_blur(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  constexpr int NH = ROWS0 + 2 * R;
+  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ty0 = ROWS0 * warp;
+  const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
+  const int b = EX - R + lane;           // first staged column of the lane's window
+  const int k = b >> 5, sh = b & 31;
+  float h[NH];
+  uint32_t any = 0;
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    const uint4 row = sm.E[MG + ty0 - R + j];
+    const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
+    const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
+    any |= win;
+    h[j] = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
+  }
+  const bool blur = __any_sync(0xffffffffu, any != 0u);
   float g[2 * R + 1];
 #pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[I][t];
-  bool blur;
-  if (I == 0) {
-    // level 0: D is the edge image itself, so each horizontal window is a slice of a
-    // staged bit row; the table (or the taps over the window's bits) gives its sum
-    int anyh = 0;
-    constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
-    const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
-    for (int k = tid; k < DN * Ti; k += MTHREADS) {
-      const int r = k / Ti, c = k - r * Ti;
-      const uint32_t win = ebits_window(sm, MG - R + r, MG - R + c) & WMASK;
-      float s = 0.0f;
-      if (use_lut) {
-        s = sm.lut[win];
-      } else {
+  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[0][t];
+  const int x = x0 + lane;
 #pragma unroll
-        for (int t = 0; t <= 2 * R; ++t)
-          if ((win >> t) & 1u) s = s + g[t];
-      }
-      sm.h[k] = s;
-      anyh |= win != 0u;
-    }
-    blur = __syncthreads_or(anyh) != 0;
-  } else {
-  // D_I over the tile and its R halo; E outside the image is staged as 0
-  int anyd = 0;
-  for (int k = tid; k < DN * DN; k += MTHREADS) {
-    const int r = k / DN, c = k - r * DN;
-    const int qx = q0x - R + c, qy = q0y - R + r;
-    uint8_t v = 0;
-    if (qx >= 0 && qx < Wi && qy >= 0 && qy < Hi) {
-      const uint8_t* e = &sm.E[qy * BS - (y0 - MG)][qx * BS - (x0 - MG)];
-#pragma unroll
-      for (int by = 0; by < BS; ++by)
-#pragma unroll
-        for (int bx = 0; bx < BS; ++bx) v |= e[by * ES + bx];
-    }
-    sm.D[k] = v;
-    anyd |= v;
-  }
-  // no edge within reach of the tile: a_I = 0 here and the blur passes add only zeros
-  blur = __syncthreads_or(anyd) != 0;
-  if (blur) {
-  // horizontal pass: with D in {0,1}, fma(g, D, s) is s + g where D is set and s elsewhere
-  for (int k = tid; k < DN * Ti; k += MTHREADS) {
-    const int r = k / Ti, c = k - r * Ti;
-    const uint8_t* d = &sm.D[r * DN + c];
-    float s = 0.0f;
-#pragma unroll
-    for (int t = 0; t <= 2 * R; ++t)
-      if (d[t]) s = s + g[t];
-    sm.h[k] = s;
-  }
-  __syncthreads();
-  }
-  }
-  // vertical pass, stencil, nesting, stores
-  uint8_t* Si = sm.S + LevelShape<I>::OFF;
-  for (int k = tid; k < Ti * Ti; k += MTHREADS) {
-    const int r = k / Ti, c = k - r * Ti;
-    const int qx = q0x + c, qy = q0y + r;
+  for (int rr = 0; rr < ROWS0; ++rr) {
     float s = 0.0f;
     if (blur) {
 #pragma unroll
-      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], sm.h[(r + t) * Ti + c], s);
+      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], h[rr + t], s);
     }
-    uint8_t st = s > 0.0f ? 1 : 0;
-    if (P >= 0) {
-      constexpr int F = P >= 0 ? I - P : 0, TP = P >= 0 ? LevelShape<(P >= 0 ? P : 0)>::T : 1;
-      const uint8_t* Sp = sm.S + LevelShape<(P >= 0 ? P : 0)>::OFF + (r << F) * TP + (c << F);
-#pragma unroll
-      for (int dy = 0; dy < (1 << F); ++dy)
-#pragma unroll
-        for (int dx = 0; dx < (1 << F); ++dx) st |= Sp[dy * TP + dx];
-    }
-    const bool inside = qx < Wi && qy < Hi;
-    Si[k] = inside ? st : 0;
+    const int y = y0 + ty0 + rr;
+    const bool inside = x < m.W && y < m.H;
     if (inside) {
-      m.alpha[I][(size_t)qy * Wi + qx] = s;
-      m.stencil[I][(size_t)qy * Wi + qx] = st;
+      m.alpha[0][(size_t)y * m.W + x] = s;
+      m.stencil[0][(size_t)y * m.W + x] = s > 0.0f ? 1 : 0;
+    }
+    const uint32_t bits = __ballot_sync(0xffffffffu, inside && s > 0.0f);
+    if (lane == 0) sm.S[0][ty0 + rr] = bits;
+  }
+}
+
+// Level I >= 1 with blur radius R, nesting from level P (P < 0: none).
+template <int I, int R, int P>
+__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  constexpr int Ti = TS >> I, DN = Ti + 2 * R;
+  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
+  const int tid = threadIdx.x;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  const int Wi = m.Wi[I], Hi = m.Hi[I];
+  uint32_t d = 0;
+  if (tid < DN) {
+    d = d_row<I, R>(sm, tid);
+    sm.D[tid] = d;
+  }
+  // no edge within reach of the tile: a_I = 0 here and both passes would add only zeros
+  const bool blur = __syncthreads_or(d != 0u) != 0;
+  if (blur) {
+    for (int k = tid; k < DN * Ti; k += MTHREADS) {
+      const int r = k / Ti, c = k - r * Ti;
+      sm.h[k] = window_sum((sm.D[r] >> c) & WMASK, sm.g[I]);
     }
   }
   __syncthreads();
+  for (int base = 0; base < Ti * Ti; base += MTHREADS) {
+    const int k = base + tid;
+    const int r = k / Ti, c = k - r * Ti;
+    const bool mine = k < Ti * Ti;
+    float s = 0.0f;
+    if (mine && blur) {
+#pragma unroll
+      for (int t = 0; t <= 2 * R; ++t) s = fmaf(m.g[I][t], sm.h[(r + t) * Ti + c], s);
+    }
+    bool st = s > 0.0f;
+    if (P >= 0 && mine) {
+      // inclusive nesting: any set child in the previous enabled finer level
+      constexpr int F = P >= 0 ? I - P : 0, GP = 1 << F;
+      uint32_t rows = 0;
+#pragma unroll
+      for (int j = 0; j < GP; ++j) rows |= sm.S[P >= 0 ? P : 0][r * GP + j];
+      st = st || ((rows >> (c * GP)) & ((1u << GP) - 1u)) != 0u;
+    }
+    const int qx = q0x + c, qy = q0y + r;
+    const bool inside = mine && qx < Wi && qy < Hi;
+    st = st && inside;
+    if (inside) {
+      m.alpha[I][(size_t)qy * Wi + qx] = s;
+      m.stencil[I][(size_t)qy * Wi + qx] = st ? 1 : 0;
+    }
+    store_rows<Ti>(sm.S[I], k, st);
+  }
 }
 
 template <int I, int P>
 __device__ __forceinline__ void blur_dispatch(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  switch (m.R[I]) {
-    case 1: blur_level<I, 1, P>(m, sm, x0, y0); break;
-    case 2: blur_level<I, 2, P>(m, sm, x0, y0); break;
-    case 3: blur_level<I, 3, P>(m, sm, x0, y0); break;
-    case 4: blur_level<I, 4, P>(m, sm, x0, y0); break;
-    case 5: blur_level<I, 5, P>(m, sm, x0, y0); break;
-    default: blur_level<I, 6, P>(m, sm, x0, y0); break;
+  if (I == 0) {
+    switch (m.R[0]) {
+      case 1: level0_blur<1>(m, sm, x0, y0); break;
+      case 2: level0_blur<2>(m, sm, x0, y0); break;
+      case 3: level0_blur<3>(m, sm, x0, y0); break;
+      case 4: level0_blur<4>(m, sm, x0, y0); break;
+      case 5: level0_blur<5>(m, sm, x0, y0); break;
+      default: level0_blur<6>(m, sm, x0, y0); break;
+    }
+    return;
+  }
+  constexpr int J = I > 0 ? I : 1;
+  switch (m.R[J]) {
+    case 1: blur_level<J, 1, P>(m, sm, x0, y0); break;
+    case 2: blur_level<J, 2, P>(m, sm, x0, y0); break;
+    case 3: blur_level<J, 3, P>(m, sm, x0, y0); break;
+    case 4: blur_level<J, 4, P>(m, sm, x0, y0); break;
+    case 5: blur_level<J, 5, P>(m, sm, x0, y0); break;
+    default: blur_level<J, 6, P>(m, sm, x0, y0); break;
   }
 }
 
-// Level I written as a constant (mode 1: a = 1, S = 1; mode 2: a = 0, S = 0).
+// Level I written as a constant (mode 1: a = 1, S = 1; mode 2: a = 0, S = 0).  Reads no
+// shared memory, so it needs no barrier before it.
 template <int I>
 __device__ __forceinline__ void fill_level(const MaskParams& m, MaskSmem& sm, int x0, int y0, int mode) {
-  constexpr int Ti = LevelShape<I>::T;
+  constexpr int Ti = TS >> I;
   const int q0x = x0 >> I, q0y = y0 >> I;
   const float av = mode == 1 ? 1.0f : 0.0f;
   const uint8_t sv = mode == 1 ? 1 : 0;
-  uint8_t* Si = sm.S + LevelShape<I>::OFF;
-  for (int k = threadIdx.x; k < Ti * Ti; k += MTHREADS) {
+  for (int base = 0; base < Ti * Ti; base += MTHREADS) {
+    const int k = base + threadIdx.x;
     const int r = k / Ti, c = k - r * Ti;
-    const int qx = q0x + c, qy = q0y + r;
-    const bool inside = qx < m.Wi[I] && qy < m.Hi[I];
-    Si[k] = inside ? sv : 0;
+    const bool inside = k < Ti * Ti && q0x + c < m.Wi[I] && q0y + r < m.Hi[I];
     if (inside && m.alpha[I]) {
-      m.alpha[I][(size_t)qy * m.Wi[I] + qx] = av;
-      m.stencil[I][(size_t)qy * m.Wi[I] + qx] = sv;
+      m.alpha[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = av;
+      m.stencil[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = sv;
     }
+    store_rows<Ti>(sm.S[I], k, inside && mode == 1);
   }
-  __syncthreads();
 }
 
 // Level I, whose previous enabled finer level is P (-1: none).
@@ -195,7 +267,9 @@ __device__ __forceinline__ void do_level(const MaskParams& m, MaskSmem& sm, int 
 }
 
 // The levels in order; blurred levels are 0..2 (the coarsest, at most 3, is a fill).
-// `prev` tracks the previous enabled level for nesting (disabled levels are skipped).
+// Shared-memory order: level I's stencil rows are written before level I+1's first
+// barrier and read after it; D and h of level I+1 are written after level I's last
+// reads of them (its second barrier, and level I+1's first).
 __device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   do_level<0, -1>(m, sm, x0, y0);
   if (m.L < 2) return;
@@ -211,56 +285,75 @@ __device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, in
   fill_level<3>(m, sm, x0, y0, m.mode[3]);  // level 3 can only be the coarsest
 }
 
-__global__ void __launch_bounds__(MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
+__global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
   __shared__ MaskSmem sm;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
   const int W = m.W, H = m.H;
-  // stage the edge image of the tile + margin (zero outside the image)
-  if ((W & 3) == 0) {
-    constexpr int Q = ES / 4;
-    for (int k = threadIdx.x; k < ES * Q; k += MTHREADS) {
-      const int r = k / Q, c = (k - r * Q) * 4;
-      const int y = y0 - MG + r, x = x0 - MG + c;  // x and W multiples of 4: all 4 in or all out
-      uchar4 v = make_uchar4(0, 0, 0, 0);
-      if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uchar4*>(E + (size_t)y * W + x));
-      *reinterpret_cast<uchar4*>(&sm.E[r][c]) = v;
-    }
-  } else {
-    for (int k = threadIdx.x; k < ES * ES; k += MTHREADS) {
-      const int r = k / ES, c = k - r * ES;
-      const int y = y0 - MG + r, x = x0 - MG + c;
-      sm.E[r][c] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(E + (size_t)y * W + x) : 0;
-    }
-  }
-  __syncthreads();
-  // bit rows of the staged edge image (bit c of word c/32 = column c) and the level-0 table
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < ES; r += MTHREADS / 32) {
+  // stage the edge rows y0-24 .. y0+55, columns x0-32 .. x0+63, as bits (zero outside the image)
+  uint32_t* Ew = reinterpret_cast<uint32_t*>(sm.E);
+  if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
+    // 16 pixels per 16-byte load (segments lie wholly inside or outside the image);
+    // every load of the CTA is issued before the first is used
+    constexpr int SEGS = EWORDS * 2, TASKS = ER * SEGS, ROUNDS = (TASKS + MTHREADS - 1) / MTHREADS;
+    uint4 v[ROUNDS];
 #pragma unroll
-      for (int w = 0; w <= EW; ++w) {
-        const int c = w * 32 + lane;
-        const uint32_t b = __ballot_sync(0xffffffffu, c < ES && sm.E[r][c] != 0);
-        if (lane == 0) sm.Ebits[r][w] = b;
-      }
+    for (int j = 0; j < ROUNDS; ++j) {
+      const int k = threadIdx.x + j * MTHREADS;
+      const int r = k / SEGS, sg = k - r * SEGS;
+      const int y = y0 - MG + r, x = x0 - EX + 16 * sg;
+      v[j] = make_uint4(0u, 0u, 0u, 0u);
+      if (k < TASKS && y >= 0 && y < H && x >= 0 && x < W)
+        v[j] = __ldg(reinterpret_cast<const uint4*>(E + (size_t)y * W + x));
     }
-    if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
-      for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
+#pragma unroll
+    for (int j = 0; j < ROUNDS; ++j) {
+      const int k = threadIdx.x + j * MTHREADS;
+      if (k >= TASKS) break;
+      const int r = k / SEGS, sg = k - r * SEGS;
+      // one bit per nonzero byte: byte flags 0/1 gathered into a nibble by one multiply
+      const uint32_t q0 = (__vcmpne4(v[j].x, 0u) & 0x01010101u) * 0x01020408u;
+      const uint32_t q1 = (__vcmpne4(v[j].y, 0u) & 0x01010101u) * 0x01020408u;
+      const uint32_t q2 = (__vcmpne4(v[j].z, 0u) & 0x01010101u) * 0x01020408u;
+      const uint32_t q3 = (__vcmpne4(v[j].w, 0u) & 0x01010101u) * 0x01020408u;
+      const uint32_t bits = (q0 >> 24) | ((q1 >> 24) << 4) | ((q2 >> 24) << 8) | ((q3 >> 24) << 12);
+      reinterpret_cast<uint16_t*>(Ew + 4 * r)[sg] = (uint16_t)bits;
+    }
+    if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
+  } else {
+#pragma unroll
+    for (int j = 0; j < ER / (MTHREADS / 32); ++j) {
+      const int r = warp + j * (MTHREADS / 32);
+      const int y = y0 - MG + r;
+      const bool row_in = y >= 0 && y < H;
+#pragma unroll
+      for (int w = 0; w < EWORDS; ++w) {
+        const int x = x0 - EX + 32 * w + lane;
+        const bool e = row_in && x >= 0 && x < W && __ldg(E + (size_t)y * W + x) != 0;
+        const uint32_t b = __ballot_sync(0xffffffffu, e);
+        if (lane == 0) Ew[4 * r + w] = b;
+      }
+      if (lane == 0) Ew[4 * r + EWORDS] = 0u;
+    }
   }
+  if (threadIdx.x < MRR_MAX_LEVELS * 16) {
+    const int i = threadIdx.x >> 4, t = threadIdx.x & 15;
+    sm.g[i][t] = t < 2 * MAXR + 1 ? m.g[i][t] : 0.0f;
+  }
+  if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
+    for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   __syncthreads();
   all_levels(m, sm, x0, y0);
   if (m.label) {
-    for (int r = ty; r < TS; r += 8) {
-      const int y = y0 + r, x = x0 + tx;
+    __syncthreads();
+    for (int r = warp; r < TS; r += MTHREADS / 32) {
+      const int y = y0 + r, x = x0 + lane;
       if (y >= H || x >= W) continue;
       uint8_t lab = 0xFF;
 #pragma unroll
       for (int i = MRR_MAX_LEVELS - 1; i >= 0; --i) {
         if (i >= m.L || m.mode[i] == 2) continue;
-        const int Ti = TS >> i;
-        const int off = i == 0 ? 0 : (i == 1 ? LevelShape<1>::OFF : (i == 2 ? LevelShape<2>::OFF : LevelShape<3>::OFF));
-        if (sm.S[off + (r >> i) * Ti + (tx >> i)]) lab = (uint8_t)i;
+        if ((sm.S[i][r >> i] >> (lane >> i)) & 1u) lab = (uint8_t)i;
       }
       m.label[(size_t)y * W + x] = lab;
     }
