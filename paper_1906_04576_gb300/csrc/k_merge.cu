@@ -1,18 +1,20 @@
 // k_merge.cu -- upsampling and blending of the sub-images (Sec. 4.2, Eq. (1)).
 //
-// A CTA owns a 32x32 tile of full-resolution pixels, 4 per lane (rows ty, ty+8, ...,
-// a warp row is 32 consecutive pixels).  Level texel q sits at full-resolution position
+// A CTA owns a 32x32 tile of full-resolution pixels; warp w owns the 4 consecutive rows
+// 4w .. 4w+3 and lane x the column.  Level texel q sits at full-resolution position
 // 2^i q + o_i, so pixel p reads level coordinate u = (p - o_i) / 2^i, whose floor and
 // fraction are exactly (p - o_i) >> i and ((p - o_i) & (2^i - 1)) * 2^-i; the taps
-// floor(u), floor(u)+1 are clamped to the level.  For every level above 0 the CTA
-// stages the (clamped) taps its tile can touch -- a_i, S_i, c_i for at most
-// (32/2^i + 2)^2 texels -- in shared memory once, and skips the level for the whole
-// tile when none of those texels is rendered (then a_i = 0 there, so alpha = 0).
-// Level 0 (one tap, weight 1) is read straight from global memory, c only where
-// alpha > 0.  Per pixel, from the coarsest level down: a_i is interpolated plainly,
-// c_i over rendered taps with renormalised weights, alpha = min(w_i a_i, 1) and
-// c' = c_i alpha + c' (1 - alpha).  A tap of weight 0 adds +0 either way, and the
-// renormalising division is skipped when the weight sum is exactly 1 (x / 1 = x).
+// floor(u), floor(u)+1 are clamped to the level.  For every level above 0 the CTA stages
+// the (clamped) taps its tile can touch -- at most (32/2^i + 2)^2 texels -- in shared
+// memory once: a_i, the stencil as 0/1 and c_i with unrendered texels replaced by 0, so
+// that w * c and w * s are exactly the terms a rendered tap adds and +0 otherwise.  The
+// 4 rows of a warp touch only 4 / 3 / 2 footprint rows of levels 1 / 2 / 3, which the lane
+// reads once into registers.  A level none of whose staged a_i is positive is skipped
+// for the tile (alpha = 0 there).  Level 0 (one tap, weight 1) is read from global memory,
+// c only where it is blended.  Per pixel, from the coarsest level down: a_i interpolated
+// plainly, c_i over rendered taps with renormalised weights, alpha = min(w_i a_i, 1) and
+// c' = c_i alpha + c' (1 - alpha); the coarsest level is taken as is.  The renormalising
+// division is skipped when the weight sum is exactly 1 (x / 1 = x).
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -20,7 +22,26 @@ namespace mrr {
 namespace {
 
 constexpr int MT = 32;                  // tile side (pixels)
-constexpr int FP = MT / 2 + 2;          // largest footprint side (level 1): 18
+constexpr int RPW = MT / 8;             // consecutive pixel rows per warp
+constexpr int MTHR = 256;
+
+template <int I> struct Lv {
+  static constexpr int side = (MT >> I) + 2;   // footprint side of the tile at level I
+  static constexpr int off = I <= 1 ? 0 : (I == 2 ? ((MT >> 1) + 2) * ((MT >> 1) + 2)
+                                                  : ((MT >> 1) + 2) * ((MT >> 1) + 2) + ((MT >> 2) + 2) * ((MT >> 2) + 2));
+  static constexpr int o = I == 0 ? 0 : (1 << (I - 1));
+  static constexpr int mask = (1 << I) - 1;
+  // footprint rows that the RPW rows of a warp touch (tap rows included)
+  static constexpr int nr = I == 1 ? 4 : (I == 2 ? 3 : 2);
+};
+constexpr int NTAP = Lv<3>::off + Lv<3>::side * Lv<3>::side;  // 460
+
+template <int C> struct MergeSmem {
+  float a[NTAP];
+  float s[NTAP];
+  float cz[C == 4 ? 3 : 1][NTAP];
+  int any[MTHR / 32];
+};
 
 template <typename CT> __device__ __forceinline__ float3 load_c(const void* c, size_t i, int C);
 
@@ -38,103 +59,157 @@ template <> __device__ __forceinline__ float3 load_c<__half>(const void* c, size
   return make_float3(__low2float(xy), __high2float(xy), __low2float(zw));
 }
 
-struct LevelTile {
-  float a[FP * FP];
-  float c[FP * FP][3];
-  uint8_t s[FP * FP];
-};
-
-struct MergeSmem {
-  LevelTile lt[MRR_MAX_LEVELS - 1];   // levels 1..3
-  int org_x[MRR_MAX_LEVELS], org_y[MRR_MAX_LEVELS], side[MRR_MAX_LEVELS];
-  int any[MRR_MAX_LEVELS];
-};
-
-constexpr int ROWS = MT / 8;  // pixel rows per lane
-
-// Stage the (clamped) taps of level I that the tile can touch; returns via sm.any[I]
-// whether any of them is rendered.
+// One staged footprint entry kk of level I: the clamped texel's stencil, a and c.
 template <typename CT, int C, int I>
-__device__ __forceinline__ void stage_level(const MergeParams& p, MergeSmem& sm, int X0, int Y0) {
-  constexpr int o = 1 << (I - 1);
-  // X0 is a multiple of MT, so the footprint is (MT >> I) + 2 texels on each side
-  constexpr int side = (MT >> I) + 2, rows = side;
-  const int fx0 = (X0 - o) >> I, fy0 = (Y0 - o) >> I;
-  LevelTile& t = sm.lt[I - 1];
+__device__ __forceinline__ void load_entry(const MergeParams& p, int X0, int Y0, int kk, uint8_t& st, float& av,
+                                           float3& cv) {
+  constexpr int side = Lv<I>::side;
+  const int ly = kk / side, lx = kk - ly * side;
   const int Wi = p.Wi[I], Hi = p.Hi[I];
-  int any = 0;
-  for (int k = threadIdx.x; k < side * rows; k += 256) {
-    const int ly = k / side, lx = k - ly * side;
-    const int qx = min(max(fx0 + lx, 0), Wi - 1), qy = min(max(fy0 + ly, 0), Hi - 1);
-    const size_t q = (size_t)qy * Wi + qx;
-    const uint8_t st = __ldg(p.stencil[I] + q);
-    t.s[k] = st;
-    t.a[k] = __ldg(p.alpha[I] + q);
-    if (st) {
-      const float3 v = load_c<CT>(p.c[I], q, C);
-      t.c[k][0] = v.x;
-      t.c[k][1] = v.y;
-      t.c[k][2] = v.z;
-    }
-    any |= st;
-  }
-  if (threadIdx.x == 0) {
-    sm.org_x[I] = fx0;
-    sm.org_y[I] = fy0;
-    sm.side[I] = side;
-  }
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) sm.any[I] = any;
+  // footprint origin: (X0 - o_I) >> I = X0 / 2^I - 1, X0 being a multiple of 32
+  const int qx = min(max((X0 >> I) - 1 + lx, 0), Wi - 1);
+  const int qy = min(max((Y0 >> I) - 1 + ly, 0), Hi - 1);
+  const size_t q = (size_t)qy * Wi + qx;
+  st = __ldg(p.stencil[I] + q);
+  av = __ldg(p.alpha[I] + q);
+  cv = load_c<CT>(p.c[I], q, C);  // unrendered texels hold stale values, replaced by 0 below
 }
 
-// Eq. (1) for level I (compile-time) on the lane's ROWS pixels of column x.
-template <int C, int I>
-__device__ __forceinline__ void blend_rows(const MergeParams& p, const MergeSmem& sm, int x, int Y0, int ty,
-                                           bool first, float (&c)[ROWS][3]) {
-  constexpr int o = 1 << (I - 1), mask = (1 << I) - 1;
+// Stage the footprints of the enabled levels 1..L-1 (level 1: 324 entries, level 2: 100,
+// level 3: 36, over two rounds of the CTA's threads); every load is issued before the
+// first is used.  Leaves per warp in sm.any bit I when a staged a_I is positive and bit
+// 4 + I when a staged texel of level I is not rendered.
+template <typename CT, int C, int L>
+__device__ __forceinline__ void stage(const MergeParams& p, MergeSmem<C>& sm, int X0, int Y0) {
+  constexpr int N1 = Lv<1>::side * Lv<1>::side, N2 = Lv<2>::side * Lv<2>::side, N3 = Lv<3>::side * Lv<3>::side;
+  static_assert(N1 >= MTHR && N1 + N2 + N3 <= 2 * MTHR, "two staging rounds");
+  const int t = threadIdx.x;
+  uint8_t st[2] = {0, 0};
+  float av[2] = {0.f, 0.f};
+  float3 cv[2] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f)};
+  int lev[2] = {0, 0}, ent[2] = {0, 0};
+  // round 0: level-1 entry t (level 1 exists when L > 1)
+  if (L > 1 && p.enabled[1]) {
+    load_entry<CT, C, 1>(p, X0, Y0, t, st[0], av[0], cv[0]);
+    lev[0] = 1;
+    ent[0] = t;
+  }
+  // round 1: the rest of level 1, then levels 2 and 3
+  if (t < N1 - MTHR) {
+    if (L > 1 && p.enabled[1]) {
+      load_entry<CT, C, 1>(p, X0, Y0, MTHR + t, st[1], av[1], cv[1]);
+      lev[1] = 1;
+      ent[1] = MTHR + t;
+    }
+  } else if (t < N1 - MTHR + N2) {
+    if (L > 2 && p.enabled[2]) {
+      load_entry<CT, C, (L > 2 ? 2 : 1)>(p, X0, Y0, t - (N1 - MTHR), st[1], av[1], cv[1]);
+      lev[1] = 2;
+      ent[1] = Lv<2>::off + t - (N1 - MTHR);
+    }
+  } else if (t < N1 - MTHR + N2 + N3) {
+    if (L > 3) {
+      load_entry<CT, C, (L > 3 ? 3 : 1)>(p, X0, Y0, t - (N1 - MTHR + N2), st[1], av[1], cv[1]);
+      lev[1] = 3;
+      ent[1] = Lv<3>::off + t - (N1 - MTHR + N2);
+    }
+  }
+  int any = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (lev[j] == 0) continue;
+    const int k = ent[j];
+    const bool on = st[j] != 0;
+    sm.a[k] = av[j];
+    sm.s[k] = on ? 1.0f : 0.0f;
+    sm.cz[0][k] = on ? cv[j].x : 0.0f;
+    if (C == 4) {
+      sm.cz[C == 4 ? 1 : 0][k] = on ? cv[j].y : 0.0f;
+      sm.cz[C == 4 ? 2 : 0][k] = on ? cv[j].z : 0.0f;
+    }
+    if (av[j] > 0.0f) any |= 1 << lev[j];
+    if (!on) any |= 16 << lev[j];
+  }
+  any = __reduce_or_sync(0xffffffffu, any);
+  if ((threadIdx.x & 31) == 0) sm.any[threadIdx.x >> 5] = any;
+}
+
+// Blend of level I >= 1 into the lane's RPW pixels (FIRST: the coarsest level, taken as
+// is).  ALLON: every staged texel of the level is rendered, so the weight sum is exactly 1.
+template <int C, int I, bool FIRST>
+__device__ __forceinline__ void blend_level(const MergeParams& p, const MergeSmem<C>& sm, int lane, int warp,
+                                            bool allon, float (&c)[RPW][3]) {
+  constexpr int side = Lv<I>::side, off = Lv<I>::off, o = Lv<I>::o, mask = Lv<I>::mask, NR = Lv<I>::nr;
   const float inv = __int_as_float((127 - I) << 23);  // 2^-I
-  const LevelTile& t = sm.lt[I - 1];
-  constexpr int side = (MT >> I) + 2;
-  const int tx = x - o;
-  const float fx = (float)(tx & mask) * inv;
+  const int lx = ((lane - o) >> I) + 1;
+  const float fx = (float)((lane - o) & mask) * inv;
   const float gx = 1.0f - fx;
-  const int lx = (tx >> I) - sm.org_x[I];
+  const int fb = ((RPW * warp - o) >> I) + 1;  // first footprint row of the warp
+  const int base = off + fb * side + lx;
+  float aL[NR], aR[NR];
+  if (!FIRST) {
+    uint32_t nz = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      aL[j] = sm.a[base + j * side];
+      aR[j] = sm.a[base + j * side + 1];
+      nz |= __float_as_uint(aL[j]) | __float_as_uint(aR[j]);
+    }
+    if (nz == 0u) return;  // every tap +0: alpha = 0 for all the lane's pixels
+  }
   const float weight = p.weight[I];
 #pragma unroll
-  for (int rr = 0; rr < ROWS; ++rr) {
-    const int y = Y0 + ty + 8 * rr;
-    const int tyy = y - o;
-    const float fy = (float)(tyy & mask) * inv;
+  for (int rr = 0; rr < RPW; ++rr) {
+    // footprint row of the pixel row relative to fb, and its fraction: the same for
+    // every warp at levels 1 and 2 (RPW w is a multiple of 2^I); the row offset is 0 at
+    // level 3, whose fraction depends on the warp's parity
+    const int d = ((rr - o) >> I) - ((-o) >> I);
+    const int fyi = I <= 2 ? ((rr - o) & mask) : ((RPW * warp + rr - o) & mask);
+    const float fy = (float)fyi * inv;
     const float gy = 1.0f - fy;
-    const int base = ((tyy >> I) - sm.org_y[I]) * side + lx;
-    const int idx[4] = {base, base + 1, base + side, base + side + 1};
-    const float w[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
-    // every tap is added (a weight of 0 adds +0); unrendered taps add +0 through a select
-    float ahat = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) ahat = ahat + w[k] * t.a[idx[k]];
-    const float wa = weight * ahat;
-    const float alpha = (1.0f < wa) ? 1.0f : wa;
-    if (!first && !(alpha > 0.0f)) continue;
-    float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
+    float alpha = 0.0f;
+    if (!FIRST) {
+      // all four taps +0: ahat = +0 and alpha = 0
+      if ((__float_as_uint(aL[d]) | __float_as_uint(aR[d]) | __float_as_uint(aL[d + 1]) |
+           __float_as_uint(aR[d + 1])) == 0u)
+        continue;
+    }
+    const float w0 = gx * gy, w1 = fx * gy, w2 = gx * fy, w3 = fx * fy;
+    if (!FIRST) {
+      float ahat = 0.0f;
+      ahat = ahat + w0 * aL[d];
+      ahat = ahat + w1 * aR[d];
+      ahat = ahat + w2 * aL[d + 1];
+      ahat = ahat + w3 * aR[d + 1];
+      const float wa = weight * ahat;
+      alpha = (1.0f < wa) ? 1.0f : wa;
+      if (!(alpha > 0.0f)) continue;
+    }
+    const int t0 = base + d * side;
+    const int idx[4] = {t0, t0 + 1, t0 + side, t0 + side + 1};
+    const float w[4] = {w0, w1, w2, w3};
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const bool on = t.s[idx[k]] != 0;
-      n0 = n0 + (on ? w[k] * t.c[idx[k]][0] : 0.0f);
+      n0 = n0 + w[k] * sm.cz[0][idx[k]];
       if (C == 4) {
-        n1 = n1 + (on ? w[k] * t.c[idx[k]][1] : 0.0f);
-        n2 = n2 + (on ? w[k] * t.c[idx[k]][2] : 0.0f);
-      }
-      den = den + (on ? w[k] : 0.0f);
-    }
-    if (den != 1.0f) {
-      n0 = n0 / den;
-      if (C == 4) {
-        n1 = n1 / den;
-        n2 = n2 / den;
+        n1 = n1 + w[k] * sm.cz[C == 4 ? 1 : 0][idx[k]];
+        n2 = n2 + w[k] * sm.cz[C == 4 ? 2 : 0][idx[k]];
       }
     }
-    if (first) {
+    if (!allon) {
+      float den = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) den = den + w[k] * sm.s[idx[k]];
+      if (den != 1.0f) {
+        n0 = n0 / den;
+        if (C == 4) {
+          n1 = n1 / den;
+          n2 = n2 / den;
+        }
+      }
+    }
+    if (FIRST) {
       c[rr][0] = n0;
       c[rr][1] = n1;
       c[rr][2] = n2;
@@ -150,45 +225,52 @@ __device__ __forceinline__ void blend_rows(const MergeParams& p, const MergeSmem
 }
 
 template <typename CT, int C, int L>
-__global__ void __launch_bounds__(256) merge_kernel(MergeParams p, float* __restrict__ out) {
-  __shared__ MergeSmem sm;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+__global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __restrict__ out) {
+  __shared__ MergeSmem<C> sm;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int X0 = blockIdx.x * MT, Y0 = blockIdx.y * MT;
-  if (L > 1 && p.enabled[1]) stage_level<CT, C, 1>(p, sm, X0, Y0);
-  if (L > 2 && p.enabled[2]) stage_level<CT, C, (L > 2 ? 2 : 1)>(p, sm, X0, Y0);
-  if (L > 3) stage_level<CT, C, (L > 3 ? 3 : 1)>(p, sm, X0, Y0);
-  __syncthreads();
   const int W = p.W, H = p.H;
-  const int x = X0 + tx;
-  if (x >= W) return;
-  float c[ROWS][3] = {};
-  // coarsest level first, then the finer enabled levels that the tile touches
-  bool first = true;
-  if (L == 4) {
-    blend_rows<C, (L == 4 ? 3 : 1)>(p, sm, x, Y0, ty, true, c);
-    first = false;
-  }
-  if (L >= 3 && p.enabled[2] && (first || sm.any[2])) {
-    blend_rows<C, (L >= 3 ? 2 : 1)>(p, sm, x, Y0, ty, first, c);
-    first = false;
-  }
-  if (L >= 2 && p.enabled[1] && (first || sm.any[1])) {
-    blend_rows<C, 1>(p, sm, x, Y0, ty, first, c);
-    first = false;
-  }
-  if (p.enabled[0]) {
+  const int x = X0 + lane;
+  // level 0 taps first: they need no shared memory
+  float a0[RPW];
+  uint8_t s0[RPW];
+  const bool en0 = p.enabled[0] != 0;
 #pragma unroll
-    for (int rr = 0; rr < ROWS; ++rr) {
-      const int y = Y0 + ty + 8 * rr;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int y = Y0 + RPW * warp + rr;
+    a0[rr] = 0.0f;
+    s0[rr] = 0;
+    if (en0 && x < W && y < H) {
+      a0[rr] = __ldg(p.alpha[0] + (size_t)y * W + x);
+      s0[rr] = __ldg(p.stencil[0] + (size_t)y * W + x);
+    }
+  }
+  if (L > 1) stage<CT, C, L>(p, sm, X0, Y0);
+  __syncthreads();
+  if (x >= W) return;
+  int any = 0;
+#pragma unroll
+  for (int k = 0; k < MTHR / 32; ++k) any |= sm.any[k];
+  float c[RPW][3] = {};
+  // coarsest level first, then the finer enabled levels whose footprint holds a_i > 0
+  if (L == 4) blend_level<C, (L == 4 ? 3 : 1), true>(p, sm, lane, warp, !(any & 128), c);
+  if (L == 3) blend_level<C, (L == 3 ? 2 : 1), true>(p, sm, lane, warp, !(any & 64), c);
+  if (L > 3 && p.enabled[2] && (any & 4)) blend_level<C, (L > 3 ? 2 : 1), false>(p, sm, lane, warp, !(any & 64), c);
+  if (L == 2) blend_level<C, 1, true>(p, sm, lane, warp, !(any & 32), c);
+  if (L > 2 && p.enabled[1] && (any & 2)) blend_level<C, 1, false>(p, sm, lane, warp, !(any & 32), c);
+  if (en0) {
+    const bool first = L == 1;
+#pragma unroll
+    for (int rr = 0; rr < RPW; ++rr) {
+      const int y = Y0 + RPW * warp + rr;
       if (y >= H) break;
       const size_t q = (size_t)y * W + x;
-      const float a0 = __ldg(p.alpha[0] + q);
-      const float ahat = 0.0f + 1.0f * a0;
+      const float ahat = 0.0f + 1.0f * a0[rr];
       const float wa = p.weight[0] * ahat;
       const float alpha = (1.0f < wa) ? 1.0f : wa;
       if (!first && !(alpha > 0.0f)) continue;
       float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
-      if (__ldg(p.stencil[0] + q)) {
+      if (s0[rr]) {
         const float3 v = load_c<CT>(p.c[0], q, C);
         n0 = v.x;
         n1 = v.y;
@@ -214,8 +296,8 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeParams p, float* __rest
     }
   }
 #pragma unroll
-  for (int rr = 0; rr < ROWS; ++rr) {
-    const int y = Y0 + ty + 8 * rr;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int y = Y0 + RPW * warp + rr;
     if (y >= H) break;
     const size_t o = (size_t)y * W + x;
     if (C == 4)
@@ -229,10 +311,10 @@ template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
   dim3 grid((p.W + MT - 1) / MT, (p.H + MT - 1) / MT);
   switch (p.L) {
-    case 1: merge_kernel<CT, C, 1><<<grid, 256, 0, s>>>(p, out); break;
-    case 2: merge_kernel<CT, C, 2><<<grid, 256, 0, s>>>(p, out); break;
-    case 3: merge_kernel<CT, C, 3><<<grid, 256, 0, s>>>(p, out); break;
-    default: merge_kernel<CT, C, 4><<<grid, 256, 0, s>>>(p, out); break;
+    case 1: merge_kernel<CT, C, 1><<<grid, MTHR, 0, s>>>(p, out); break;
+    case 2: merge_kernel<CT, C, 2><<<grid, MTHR, 0, s>>>(p, out); break;
+    case 3: merge_kernel<CT, C, 3><<<grid, MTHR, 0, s>>>(p, out); break;
+    default: merge_kernel<CT, C, 4><<<grid, MTHR, 0, s>>>(p, out); break;
   }
 }
 
