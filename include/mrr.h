@@ -342,6 +342,13 @@ uint64_t mrr_kernel_launches(void);
 /* Text of the last failure on this context ("" if none); valid until the next call. */
 const char* mrr_last_error(mrr_ctx* ctx);
 
+/* Device-side fault bits of the context: kernels that wait on asynchronous tile loads
+ * give up after about a second and record a bit here instead of waiting for ever (bit 0:
+ * edge detection, bit 1: upsample/merge); their output for that frame is then invalid.
+ * Synchronises the device, copies the word to *flags and, if `clear` is nonzero, resets
+ * it.  Not part of the paper's method; it makes a stalled load visible to the host. */
+mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear);
+
 #ifdef __cplusplus
 }
 #endif

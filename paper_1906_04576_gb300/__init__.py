@@ -153,6 +153,7 @@ _lib.mrr_masks_static.argtypes = [ctypes.POINTER(mrr_config), _vp, ctypes.POINTE
 _lib.mrr_masks_static.restype = ctypes.c_int
 _lib.mrr_kernel_launches.argtypes = []
 _lib.mrr_kernel_launches.restype = ctypes.c_uint64
+_lib.mrr_fault_flags.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
@@ -557,6 +558,13 @@ def mrr_release(s: Server, ticket: int) -> None:
 
 def mrr_kernel_launches() -> int:
     return int(_lib.mrr_kernel_launches())
+
+
+def mrr_fault_flags(ctx: Context, clear: bool = False) -> int:
+    """Device fault bits of the context (0: no tile load has stalled)."""
+    v = ctypes.c_uint32(0)
+    _check(ctx, _lib.mrr_fault_flags(ctx.handle, ctypes.byref(v), int(clear)))
+    return int(v.value)
 
 
 def mrr_upsample_merge(ctx: Context, levels: Levels, c_list: list, out: torch.Tensor, stream=None) -> None:

@@ -33,6 +33,7 @@ struct mrr_ctx {
   uint32_t* chunk_counts = nullptr;
   size_t chunk_cap = 0;
   float* lut0 = nullptr;  // level 0's horizontal blur table (device), see MaskParams
+  uint32_t* fault = nullptr;  // device fault word (bits of tma.cuh)
   // pools of mrr_render_host
   float* h_depth = nullptr;
   void* h_normal = nullptr;
@@ -285,6 +286,7 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.depth_rel = ctx->cfg.depth_rel;
   p.normal_cos = ctx->cfg.normal_cos;
   p.shadow_bias = ctx->cfg.shadow_bias;
+  p.fault = ctx->fault;
   const int h = ctx->cfg.precision == MRR_FP16;
   MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
   return MRR_OK;
@@ -427,6 +429,7 @@ void free_pools(mrr_ctx* ctx) {
   cudaFree(ctx->counts);
   cudaFree(ctx->chunk_counts);
   cudaFree(ctx->lut0);
+  cudaFree(ctx->fault);
   cudaFree(ctx->h_depth);
   cudaFree(ctx->h_normal);
   cudaFree(ctx->h_color);
@@ -468,6 +471,8 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
   }
   MRR_CUDA(ctx, cudaMalloc(&ctx->counts, MRR_MAX_LEVELS * sizeof(uint32_t)));
   MRR_CUDA(ctx, cudaMemset(ctx->counts, 0, MRR_MAX_LEVELS * sizeof(uint32_t)));
+  MRR_CUDA(ctx, cudaMalloc(&ctx->fault, sizeof(uint32_t)));
+  MRR_CUDA(ctx, cudaMemset(ctx->fault, 0, sizeof(uint32_t)));
   ctx->chunk_cap = chunks;
   MRR_CUDA(ctx, cudaMalloc(&ctx->chunk_counts, chunks * sizeof(uint32_t)));
   return MRR_OK;
@@ -537,6 +542,7 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
     return st == MRR_ECUDA ? MRR_ENOMEM : st;
   }
   ctx->shade_grid = shade_grid_blocks();
+  edges_prepare();
   if (c.lanes_per_texel) ctx->split_texel = c.lanes_per_texel;
   if (c.lanes_per_pixel) ctx->split_pixel = c.lanes_per_pixel;
   ctx->use_graph = c.no_graph == 0;
@@ -551,6 +557,14 @@ void mrr_destroy(mrr_ctx* ctx) {
 }
 
 const char* mrr_last_error(mrr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear) {
+  if (!ctx || !flags) return MRR_EINVAL;
+  MRR_CUDA(ctx, cudaDeviceSynchronize());
+  MRR_CUDA(ctx, cudaMemcpy(flags, ctx->fault, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (clear) MRR_CUDA(ctx, cudaMemset(ctx->fault, 0, sizeof(uint32_t)));
+  return MRR_OK;
+}
 
 mrr_status mrr_edges(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* edges_dev, void* stream) {
   if (!ctx) return MRR_EINVAL;

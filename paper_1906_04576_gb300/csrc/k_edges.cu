@@ -4,12 +4,21 @@
 // edges_direct_kernel (SSAO, SSGI): each lane reads its pixel and its 4 neighbours
 //   straight from global memory; the neighbours' lines are the block's own rows, so
 //   they are L1 hits and DRAM sees each G-buffer texel about once.
+// edges_tma_kernel (SSAO, SSGI; rows a multiple of 16 bytes): a persistent CTA walks
+//   32x16 output tiles; the tile's depth and normals plus a one-pixel halo arrive by TMA
+//   into a ring of four shared-memory stages, so three tiles are in flight while one is
+//   tested.  Same tests and arithmetic as edges_direct_kernel, read from shared memory.
 // edges_kernel (soft shadows): the tile and a one-pixel halo of depth, normals and the
 //   one-sample hard shadow of Sec. 3.1 are staged in shared memory, so each staged
 //   texel's hard shadow (a reconstruction, a light-space projection and a shadow-map
 //   read) is computed once, not once per neighbour test.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "mrr_internal.cuh"
 #include "shade_common.cuh"
+#include "tma.cuh"
 
 namespace mrr {
 
@@ -146,15 +155,197 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
   }
 }
 
+// ---- TMA-staged edge detection (SSAO, SSGI)
+constexpr int ETW = 32, ETH = 16, ESTAGES = 4, ETHREADS = 256;
+constexpr int DOFF = 4, DW = ETW + 2 * DOFF;             // depth staged from x0 - 4 (16-byte start)
+constexpr uint32_t DBYTES = DW * (ETH + 2) * 4;          // 2880
+template <typename NT> struct EdgeTma;
+template <> struct EdgeTma<float4> {
+  static constexpr int NOFF = 1, NW = ETW + 2;           // normals staged from x0 - 1
+  static constexpr uint32_t NBYTES = NW * (ETH + 2) * 16;
+};
+template <> struct EdgeTma<half4> {
+  static constexpr int NOFF = 2, NW = ETW + 4;           // from x0 - 2 (16-byte start)
+  static constexpr uint32_t NBYTES = NW * (ETH + 2) * 8;
+};
+constexpr uint32_t pad128(uint32_t b) { return (b + 127u) / 128u * 128u; }
+template <typename NT> constexpr uint32_t stage_bytes() { return pad128(EdgeTma<NT>::NBYTES) + pad128(DBYTES); }
+template <typename NT> constexpr uint32_t edges_tma_smem() { return ESTAGES * stage_bytes<NT>() + 64 + 128; }
+
+__device__ __forceinline__ float3 smem_normal(const float4* s, int i) {
+  const float4 v = s[i];
+  return make_float3(v.x, v.y, v.z);
+}
+__device__ __forceinline__ float3 smem_normal(const half4* s, int i) {
+  const uint2 raw = reinterpret_cast<const uint2*>(s)[i];
+  const __half2 xy = *reinterpret_cast<const __half2*>(&raw.x);
+  const __half2 zw = *reinterpret_cast<const __half2*>(&raw.y);
+  return make_float3(__low2float(xy), __high2float(xy), __low2float(zw));
+}
+
+template <typename NT>
+__global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_constant__ CUtensorMap tm_n,
+                                                             const __grid_constant__ CUtensorMap tm_d, EdgeParams p,
+                                                             uint8_t* __restrict__ E) {
+  using T = EdgeTma<NT>;
+  constexpr uint32_t NP = pad128(T::NBYTES), SB = stage_bytes<NT>();
+  extern __shared__ unsigned char edges_dsm[];
+  unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(edges_dsm) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sbase + ESTAGES * SB);
+  const int W = p.v.W, H = p.v.H;
+  const int gx = (W + ETW - 1) / ETW, gy = (H + ETH - 1) / ETH;
+  const int ntiles = gx * gy;
+  const int nlocal = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ESTAGES; ++s) mbar_init(&full[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: start the loads of the k-th tile of this CTA into stage k % ESTAGES
+  auto issue = [&](int k) {
+    const int s = k % ESTAGES;
+    const int t = (int)blockIdx.x + k * (int)gridDim.x;
+    const int x0 = (t % gx) * ETW, y0 = (t / gx) * ETH;
+    unsigned char* st = sbase + s * SB;
+    mbar_arrive_expect_tx(&full[s], T::NBYTES + DBYTES);
+    tma_load_2d(st, &tm_n, &full[s], (x0 - T::NOFF) * 4, y0 - 1);
+    tma_load_2d(st + NP, &tm_d, &full[s], x0 - DOFF, y0 - 1);
+  };
+  if (threadIdx.x == 0)
+    for (int k = 0; k < min(ESTAGES, nlocal); ++k) issue(k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float farp = p.v.farp;
+  int k = 0;
+  bool ok = true;
+  for (; k < nlocal; ++k) {
+    const int s = k % ESTAGES;
+    ok = mbar_wait(&full[s], (uint32_t)(k / ESTAGES) & 1u);
+    if (ok) {
+      const int t = (int)blockIdx.x + k * (int)gridDim.x;
+      const int x0 = (t % gx) * ETW, y0 = (t / gx) * ETH;
+      const NT* sn = reinterpret_cast<const NT*>(sbase + s * SB);
+      const float* sd = reinterpret_cast<const float*>(sbase + s * SB + NP);
+      // the lane's two vertically adjacent pixels (rows r0, r0 + 1 of the tile)
+      const int r0 = 2 * warp, x = x0 + lane, y = y0 + r0;
+      const int ly = r0 + 1, cd = lane + DOFF, cn = lane + T::NOFF;
+      const float du = sd[(ly - 1) * DW + cd], d0 = sd[ly * DW + cd], d1 = sd[(ly + 1) * DW + cd],
+                  dd = sd[(ly + 2) * DW + cd];
+      const float dl0 = sd[ly * DW + cd - 1], dr0 = sd[ly * DW + cd + 1];
+      const float dl1 = sd[(ly + 1) * DW + cd - 1], dr1 = sd[(ly + 1) * DW + cd + 1];
+      const float3 nu = smem_normal(sn, (ly - 1) * T::NW + cn), n0 = smem_normal(sn, ly * T::NW + cn);
+      const float3 n1 = smem_normal(sn, (ly + 1) * T::NW + cn), nd = smem_normal(sn, (ly + 2) * T::NW + cn);
+      const float3 nl0 = smem_normal(sn, ly * T::NW + cn - 1), nr0 = smem_normal(sn, ly * T::NW + cn + 1);
+      const float3 nl1 = smem_normal(sn, (ly + 1) * T::NW + cn - 1), nr1 = smem_normal(sn, (ly + 1) * T::NW + cn + 1);
+      // n_p . n_q for both pixels at once (two independent IEEE products and sums in the
+      // order x, y, z -- the same bits as the scalar expression, products commuting)
+      const float2 N0x = make_float2(n0.x, n1.x), N0y = make_float2(n0.y, n1.y), N0z = make_float2(n0.z, n1.z);
+      auto dot2 = [&](float3 a, float3 b) {
+        const float2 px = __fmul2_rn(N0x, make_float2(a.x, b.x));
+        const float2 py = __fmul2_rn(N0y, make_float2(a.y, b.y));
+        const float2 pz = __fmul2_rn(N0z, make_float2(a.z, b.z));
+        return __fadd2_rn(__fadd2_rn(px, py), pz);
+      };
+      const float2 hl = dot2(nl0, nl1), hr = dot2(nr0, nr1), vu = dot2(nu, n0), vd = dot2(n1, nd);
+      const float cosT = p.normal_cos, farp2 = farp;
+      const bool hasl = x > 0, hasr = x < W - 1;
+      const bool hasu0 = y > 0, hasd1 = y + 1 < H - 1;
+      // Laplacians along x for both rows and along y
+      // a - b is a + (-b) exactly; -2 d is exact
+      const float2 m2d = __fmul2_rn(make_float2(-2.0f, -2.0f), make_float2(d0, d1));
+      const float2 lapx = __fadd2_rn(__fadd2_rn(make_float2(dl0, dl1), make_float2(dr0, dr1)), m2d);
+      const float2 lapy = __fadd2_rn(__fadd2_rn(make_float2(du, d0), make_float2(d1, dd)), m2d);
+      const float2 thr = __fmul2_rn(make_float2(p.depth_rel, p.depth_rel), make_float2(d0, d1));
+      // pixel 0: up neighbour row r0 - 1, down neighbour pixel 1
+      bool e0 = (hasl && (dl0 >= farp2 || hl.x < cosT)) || (hasr && (dr0 >= farp2 || hr.x < cosT)) ||
+                (hasu0 && (du >= farp2 || vu.x < cosT)) || (y + 1 < H && (d1 >= farp2 || vd.x < cosT)) ||
+                (hasl && hasr && fabsf(lapx.x) > thr.x) || (hasu0 && y + 1 < H && fabsf(lapy.x) > thr.x);
+      // pixel 1: up neighbour pixel 0, down neighbour row r0 + 2
+      bool e1 = (hasl && (dl1 >= farp2 || hl.y < cosT)) || (hasr && (dr1 >= farp2 || hr.y < cosT)) ||
+                (d0 >= farp2 || vu.y < cosT) || (hasd1 && (dd >= farp2 || vd.y < cosT)) ||
+                (hasl && hasr && fabsf(lapx.y) > thr.y) || (hasd1 && fabsf(lapy.y) > thr.y);
+      e0 = e0 && d0 < farp2;
+      e1 = e1 && d1 < farp2;
+      if (x < W) {
+        if (y < H) E[(size_t)y * W + x] = e0 ? 1 : 0;
+        if (y + 1 < H) E[(size_t)(y + 1) * W + x] = e1 ? 1 : 0;
+      }
+    }
+    // every thread is done with stage s before it is refilled; a failed wait anywhere
+    // ends the CTA's walk
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0 && k + ESTAGES < nlocal) issue(k + ESTAGES);
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(p.fault, FAULT_EDGES_WAIT);
+    // the loads of tiles k .. k + ESTAGES - 1 may still be in flight: let them land
+    // (again with a limit) before the CTA's shared memory is released
+    for (int j = k; j < min(k + ESTAGES, nlocal); ++j) mbar_wait(&full[j % ESTAGES], (uint32_t)(j / ESTAGES) & 1u);
+  }
+}
+
+template <typename NT>
+int edges_tma_grid() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(edges_tma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edges_tma_smem<NT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_tma_kernel<NT>, ETHREADS, edges_tma_smem<NT>());
+    blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }
+  return blocks;
+}
+
+// Tensor maps of the frame's normals and depth for the TMA kernel; false when the frame's
+// layout does not allow TMA (rows not a multiple of 16 bytes, unaligned base).
+template <typename NT>
+bool edge_maps(const EdgeParams& p, const float* depth, const void* normal, CUtensorMap* tn, CUtensorMap* td) {
+  const int W = p.v.W, H = p.v.H;
+  if (W % 4 != 0 || (reinterpret_cast<uintptr_t>(depth) & 15) || (reinterpret_cast<uintptr_t>(normal) & 15))
+    return false;
+  using T = EdgeTma<NT>;
+  // normals as a plane of 4 W scalars per row, so that one box row is 4 NW contiguous scalars
+  const uint64_t dims[2] = {4 * (uint64_t)W, (uint64_t)H}, strides[1] = {(uint64_t)W * sizeof(NT)};
+  const uint32_t box[2] = {4 * (uint32_t)T::NW, ETH + 2};
+  const bool ok = encode_tensor_map(tn, sizeof(NT) == 16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                    2, normal, dims, strides, box);
+  const uint64_t ddims[2] = {(uint64_t)W, (uint64_t)H}, dstrides[1] = {(uint64_t)W * 4};
+  const uint32_t dbox[2] = {DW, ETH + 2};
+  return ok && encode_tensor_map(td, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, depth, ddims, dstrides, dbox);
+}
+
+template <typename NT>
+bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* normal, uint8_t* E, cudaStream_t s) {
+  CUtensorMap tn, td;
+  if (!p.fault || !edge_maps<NT>(p, depth, normal, &tn, &td)) return false;
+  const int tiles = ((p.v.W + ETW - 1) / ETW) * ((p.v.H + ETH - 1) / ETH);
+  const int grid = min(tiles, edges_tma_grid<NT>());
+  edges_tma_kernel<NT><<<grid, ETHREADS, edges_tma_smem<NT>(), s>>>(tn, td, p, E);
+  return true;
+}
+
 }  // namespace
+
+void edges_prepare() {
+  edges_tma_grid<float4>();
+  edges_tma_grid<half4>();
+}
 
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
   if (!p.ssm) {
-    dim3 dgrid((p.v.W + TX - 1) / TX, (p.v.H + TY * ER - 1) / (TY * ER));
-    if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);
-    else edges_direct_kernel<float4><<<dgrid, block, 0, s>>>(p, depth, (const float4*)normal, E);
+    const bool tma = half_normal ? launch_edges_tma<half4>(p, depth, normal, E, s)
+                                 : launch_edges_tma<float4>(p, depth, normal, E, s);
+    if (!tma) {
+      dim3 dgrid((p.v.W + TX - 1) / TX, (p.v.H + TY * ER - 1) / (TY * ER));
+      if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);
+      else edges_direct_kernel<float4><<<dgrid, block, 0, s>>>(p, depth, (const float4*)normal, E);
+    }
   } else if (half_normal) {
     if (half_smap)
       edges_kernel<half4, __half><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const __half*)smap, E);
@@ -168,6 +359,35 @@ cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* no
   }
   count_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace mrr
+
+namespace mrr {
+
+bool encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* base,
+                       const uint64_t* dims, const uint64_t* strides, const uint32_t* box) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  if (!encode || rank < 1 || rank > 5) return false;
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) gs[i] = strides[i];
+  return encode(map, type, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace mrr

@@ -69,6 +69,7 @@ struct EdgeParams {
   LightC L;
   float depth_rel, normal_cos, shadow_bias;
   int ssm;
+  uint32_t* fault;  // device fault word of the context (tma.cuh)
 };
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
@@ -147,6 +148,7 @@ cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int preci
                               cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 
+void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)
 int shade_grid_blocks();  // grid multiplier base of the work-list kernel (grid = multiple of its resident CTAs)
 int batch_grid_blocks();  // resident CTAs of the batched shading kernel
 cudaError_t launch_shade_batch(const BatchItem* items_dev, int nitems, uint32_t* queue_head, int chunk, int grid,

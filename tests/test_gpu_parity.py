@@ -137,6 +137,24 @@ def test_ssao_ragged_sizes(mrr, W, H, seed):
     check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=64))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("W,H", [(100, 37), (36, 18), (4, 1), (1924, 33), (64, 300)])
+def test_edges_tile_staged_sizes(mrr, W, H, precision):
+    """Rows a multiple of 16 bytes take the TMA-staged edge kernel: partial 32x16 tiles,
+    one-pixel frames and halos outside the image all match the oracle bit for bit."""
+    import torch
+    fr = sg.gbuffer(W + H, W, H, 24, 8)
+    cfg = make_cfg("ssao", 4, W, H, precision)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr, precision)
+    edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    mrr.mrr_edges(ctx, dev, edges)
+    ref = orc.edges(oracle_inputs(fr, precision), cfg, "f32")
+    assert np.array_equal(edges.cpu().numpy(), ref)
+    assert mrr.mrr_fault_flags(ctx) == 0
+    mrr.mrr_destroy(ctx)
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_ssao_fp16_storage(mrr, seed):
     fr = sg.gbuffer(seed, 190, 110, 20, 6)
