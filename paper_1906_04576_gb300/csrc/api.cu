@@ -227,13 +227,12 @@ mrr_status check_levels(mrr_ctx* ctx, const mrr_levels* lv, bool need_lists) {
   return MRR_OK;
 }
 
-mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cudaStream_t s) {
+MaskParams mask_params(const mrr_ctx* ctx, const mrr_levels* lv) {
   const mrr_config& c = ctx->cfg;
-  const int W = lv->width[0], H = lv->height[0];
   MaskParams m;
   std::memset(&m, 0, sizeof m);
-  m.W = W;
-  m.H = H;
+  m.W = lv->width[0];
+  m.H = lv->height[0];
   m.L = c.num_levels;
   for (int i = 0; i < c.num_levels; ++i) {
     if (!c.enabled[i]) m.mode[i] = 2;
@@ -248,6 +247,13 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
   }
   m.label = lv->label;
   m.lut0 = ctx->lut0;
+  return m;
+}
+
+mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cudaStream_t s) {
+  const mrr_config& c = ctx->cfg;
+  const int W = lv->width[0], H = lv->height[0];
+  const MaskParams m = mask_params(ctx, lv);
   MRR_CUDA(ctx, launch_masks(m, E, s));
   // work lists of every enabled level in one two-pass compaction
   CompactParams cp;
@@ -277,7 +283,8 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
   return MRR_OK;
 }
 
-mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream_t s) {
+mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream_t s, uint32_t* zero = nullptr,
+                      int zero_words = 0) {
   EdgeParams p;
   std::memset(&p, 0, sizeof p);
   p.v = make_view(g->width, g->height, g->cam);
@@ -287,6 +294,8 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.normal_cos = ctx->cfg.normal_cos;
   p.shadow_bias = ctx->cfg.shadow_bias;
   p.fault = ctx->fault;
+  p.zero = zero;
+  p.zero_words = zero_words;
   const int h = ctx->cfg.precision == MRR_FP16;
   MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
   return MRR_OK;
@@ -308,7 +317,8 @@ mrr_levels pool_levels(mrr_ctx* ctx, int W, int H) {
   return lv;
 }
 
-mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s) {
+mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
+                      bool skip_level0 = false) {
   const mrr_config& cf = ctx->cfg;
   MergeParams mp;
   std::memset(&mp, 0, sizeof mp);
@@ -326,6 +336,7 @@ mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
     mp.stencil[i] = lv->stencil[i];
     mp.c[i] = c[i];
   }
+  if (skip_level0) mp.enabled[0] = 0;
   MRR_CUDA(ctx, launch_merge(mp, out, s));
   return MRR_OK;
 }
@@ -389,7 +400,70 @@ mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStrea
   return MRR_OK;
 }
 
+// A frame fits the context's pools (level buffers and work lists).
+bool fits_pools(const mrr_ctx* ctx, int W, int H) {
+  for (int i = 0; i < ctx->cfg.num_levels; ++i)
+    if ((size_t)level_dim(W, i) * level_dim(H, i) > (size_t)level_dim(ctx->pool_W, i) * level_dim(ctx->pool_H, i))
+      return false;
+  return true;
+}
+
+mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s);
+
+// With at least two levels: edges (also clearing the per-level counts), masks that also
+// write the work lists, the levels above 0, their merge, and level 0 shaded straight into
+// the merged image -- level 0's c_0, a_0 and S_0 never reach memory, and no compaction
+// launch is needed.
 mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
+  const mrr_config& c = ctx->cfg;
+  const int W = g->width, H = g->height;
+  if (c.num_levels < 2) return render_launches_staged(ctx, g, out, s);
+  if (!fits_pools(ctx, W, H)) return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size", W, H);
+  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS);
+  if (st != MRR_OK) return st;
+  mrr_levels lv = pool_levels(ctx, W, H);
+  MaskParams m = mask_params(ctx, &lv);
+  m.label = nullptr;
+  m.a0c = ctx->alpha[0];
+  for (int i = 0; i < c.num_levels; ++i) m.list[i] = c.enabled[i] ? ctx->worklist[i] : nullptr;
+  m.counts = ctx->counts;
+  MRR_CUDA(ctx, launch_masks(m, ctx->edges, s));
+  ShadeParams p = make_shade_params(ctx, *g);
+  const FrameIn in = make_frame_in(*g);
+  ShadeLevels sl;
+  std::memset(&sl, 0, sizeof sl);
+  for (int i = 1; i < c.num_levels; ++i) {
+    if (!c.enabled[i]) continue;
+    const int k = sl.nlev++;
+    sl.level[k] = i;
+    sl.list[k] = ctx->worklist[i];
+    sl.c[k] = ctx->cbuf[i];
+    sl.Wi[k] = lv.width[i];
+    sl.Hi[k] = lv.height[i];
+  }
+  sl.counts = ctx->counts;
+  MRR_CUDA(ctx, launch_shade_levels(p, in, c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
+  st = merge_impl(ctx, &lv, ctx->cbuf, out, s, true);
+  if (st != MRR_OK || !c.enabled[0]) return st;
+  ShadeLevels s0;
+  std::memset(&s0, 0, sizeof s0);
+  s0.nlev = 1;
+  s0.level[0] = 0;
+  s0.list[0] = ctx->worklist[0];
+  s0.c[0] = ctx->cbuf[0];
+  s0.Wi[0] = W;
+  s0.Hi[0] = H;
+  s0.counts = ctx->counts;
+  s0.blend_out = out;
+  s0.blend_a = ctx->alpha[0];
+  s0.blend_w = c.weight[0];
+  s0.blend_C = channels(c);
+  MRR_CUDA(ctx, launch_shade_levels(p, in, c.precision, s0, ctx->shade_grid, ctx->split_texel, s));
+  return MRR_OK;
+}
+
+// One level only (level 0 is the coarsest): edges, masks, compaction, shading, merge.
+mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const int W = g->width, H = g->height;
   mrr_status st = edges_impl(ctx, g, ctx->edges, s);
   if (st != MRR_OK) return st;

@@ -27,6 +27,15 @@ namespace {
 constexpr int TX = 32, TY = 8;
 constexpr int SX = TX + 2, SY = TY + 2;
 
+// Words a frame's later kernels need at zero (the mask kernel's look-back state), set by
+// whichever edge kernel runs first in the frame; the grid-stride covers any grid shape.
+__device__ __forceinline__ void zero_words(const EdgeParams& p) {
+  if (!p.zero) return;
+  const int nthr = gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+  const int tid = ((blockIdx.y * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  for (int i = tid; i < p.zero_words; i += nthr) p.zero[i] = 0u;
+}
+
 template <typename NT, typename SMT>
 __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float* __restrict__ depth,
                                                         const NT* __restrict__ normal,
@@ -34,6 +43,7 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   __shared__ float sd[SY][SX];
   __shared__ float snx[SY][SX], sny[SY][SX], snz[SY][SX];
   __shared__ uint8_t shs[SY][SX];
+  zero_words(p);
   const int W = p.v.W, H = p.v.H;
   const int x0 = blockIdx.x * TX - 1, y0 = blockIdx.y * TY - 1;
   const int tid = threadIdx.y * TX + threadIdx.x;
@@ -100,6 +110,7 @@ template <typename NT>
 __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, const float* __restrict__ depth,
                                                                const NT* __restrict__ normal,
                                                                uint8_t* __restrict__ E) {
+  zero_words(p);
   const int W = p.v.W, H = p.v.H;
   const int x = blockIdx.x * TX + threadIdx.x;
   const int y0 = (blockIdx.y * TY + threadIdx.y) * ER;
@@ -192,6 +203,7 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
   extern __shared__ unsigned char edges_dsm[];
   unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(edges_dsm) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(sbase + ESTAGES * SB);
+  zero_words(p);
   const int W = p.v.W, H = p.v.H;
   const int gx = (W + ETW - 1) / ETW, gy = (H + ETH - 1) / ETH;
   const int ntiles = gx * gy;

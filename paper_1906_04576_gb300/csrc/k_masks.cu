@@ -1,7 +1,8 @@
 // k_masks.cu -- the per-level masks of Sec. 3.1 / Table 1, the stencil of Sec. 4.1 and
 // the dense work lists that replace the stencil test on the GPU.
 //
-// masks_kernel: ONE launch computes every level, bit-parallel.  A CTA owns a 32x32
+// masks_kernel: ONE launch computes every level, bit-parallel (and, for a whole frame,
+//   the work lists too -- see frame_lists).  A CTA owns a 32x32
 //   full-resolution tile (16x16 at level 1, 8x8 at level 2, ...) and stages the edge
 //   image of the tile plus a 24-pixel halo as bit rows (one ballot per 32 pixels).  For
 //   each blurred level i it forms the downsampled edge image D_i (block maximum: the OR
@@ -45,6 +46,11 @@ struct MaskSmem {
   float g[MRR_MAX_LEVELS][16];           // the Gaussians of Table 1
   uint32_t S[MRR_MAX_LEVELS][TS];        // stencil rows of every level as bits (tile texels only)
   float lut[MASK_LUT_MAX];
+  // frame mode: level 0's a over the tile, per-row prefix counts and the tile's first
+  // list position per level
+  float a0t[TS][TS];
+  uint32_t rowpre[MRR_MAX_LEVELS][TS];
+  uint32_t excl[MRR_MAX_LEVELS];
 };
 
 // Sum of the taps g[t] whose bit t is set in win, in ascending t, one rounding per add.
@@ -154,7 +160,9 @@ __device__ __forceinline__ void level0_blur(const MaskParams& m, MaskSmem& sm, i
     }
     const int y = y0 + ty0 + rr;
     const bool inside = x < m.W && y < m.H;
-    if (inside) {
+    if (m.a0c) {
+      sm.a0t[ty0 + rr][lane] = s;
+    } else if (inside) {
       m.alpha[0][(size_t)y * m.W + x] = s;
       m.stencil[0][(size_t)y * m.W + x] = s > 0.0f ? 1 : 0;
     }
@@ -250,7 +258,9 @@ __device__ __forceinline__ void fill_level(const MaskParams& m, MaskSmem& sm, in
     const int k = base + threadIdx.x;
     const int r = k / Ti, c = k - r * Ti;
     const bool inside = k < Ti * Ti && q0x + c < m.Wi[I] && q0y + r < m.Hi[I];
-    if (inside && m.alpha[I]) {
+    if (I == 0 && m.a0c) {
+      if (k < Ti * Ti) sm.a0t[r][c] = av;
+    } else if (inside && m.alpha[I]) {
       m.alpha[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = av;
       m.stencil[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = sv;
     }
@@ -285,11 +295,69 @@ __device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, in
   fill_level<3>(m, sm, x0, y0, m.mode[3]);  // level 3 can only be the coarsest
 }
 
+// ---- frame mode: the work lists of every enabled level, written by the mask kernel
+//
+// Each tile reserves room for its set texels of each level with one atomicAdd on the
+// level's count (zero before the launch), then writes them there in tile-local
+// row-major order.  The order of the tiles within a list is whatever order the tiles
+// reached their atomics; shading never depends on it (every entry is shaded and stored
+// on its own), and the count is exact.
+__device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
+      const uint32_t pc = (i < m.L && lane < (TS >> i)) ? (uint32_t)__popc(sm.S[i][lane]) : 0u;
+      uint32_t inc = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (lane < (TS >> i)) sm.rowpre[i][lane] = inc - pc;
+      const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
+      if (lane == 0 && i < m.L && m.mode[i] != 2) sm.excl[i] = cnt ? atomicAdd(m.counts + i, cnt) : 0u;
+    }
+  }
+  __syncthreads();
+  // level 0: warp w owns rows ROWS0 w .. ROWS0 w + ROWS0 - 1, lane = column
+  if (m.mode[0] != 2) {
+    const size_t cap = (size_t)m.Wi[0] * m.Hi[0];
+#pragma unroll
+    for (int rr = 0; rr < ROWS0; ++rr) {
+      const int r = ROWS0 * warp + rr;
+      const uint32_t bits = sm.S[0][r];
+      if ((bits >> lane) & 1u) {
+        const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(bits & ((1u << lane) - 1u));
+        if (pos < cap) {
+          m.list[0][pos] = ((uint32_t)(y0 + r) << 16) | (uint32_t)(x0 + lane);
+          m.a0c[pos] = sm.a0t[r][lane];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < MRR_MAX_LEVELS; ++i) {
+    if (i >= m.L || m.mode[i] == 2) continue;
+    const int Ti = TS >> i;
+    const int k = threadIdx.x;
+    if (k >= Ti * Ti) continue;
+    const int r = k / Ti, c = k - r * Ti;
+    const uint32_t bits = sm.S[i][r];
+    if ((bits >> c) & 1u) {
+      const size_t pos = (size_t)sm.excl[i] + sm.rowpre[i][r] + __popc(bits & ((1u << c) - 1u));
+      if (pos < (size_t)m.Wi[i] * m.Hi[i])
+        m.list[i][pos] = ((uint32_t)((y0 >> i) + r) << 16) | (uint32_t)((x0 >> i) + c);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
   __shared__ MaskSmem sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
   const int W = m.W, H = m.H;
+  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
   // stage the edge rows y0-24 .. y0+55, columns x0-32 .. x0+63, as bits (zero outside the image)
   uint32_t* Ew = reinterpret_cast<uint32_t*>(sm.E);
   if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
@@ -344,6 +412,7 @@ __global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const 
     for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   __syncthreads();
   all_levels(m, sm, x0, y0);
+  if (m.a0c) frame_lists(m, sm, x0, y0);
   if (m.label) {
     __syncthreads();
     for (int r = warp; r < TS; r += MTHREADS / 32) {

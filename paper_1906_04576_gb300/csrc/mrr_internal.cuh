@@ -70,6 +70,8 @@ struct EdgeParams {
   float depth_rel, normal_cos, shadow_bias;
   int ssm;
   uint32_t* fault;  // device fault word of the context (tma.cuh)
+  uint32_t* zero;   // words the launch sets to 0 for the next kernel (may be null)
+  int zero_words;
 };
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
@@ -88,6 +90,12 @@ struct MaskParams {
   // level 0's horizontal blur as a table: lut0[b] = the ascending-tap sum of g over the
   // set bits of the (2R+1)-bit window b (null: sum the taps directly; R <= 5 only)
   const float* lut0;
+  // Frame mode (a0c non-null): the kernel also writes every enabled level's work list
+  // (tiles in any order, texels of a tile in row-major order), level 0's a only as a0c
+  // (aligned with level 0's list), and neither alpha[0] nor stencil[0].
+  float* a0c;
+  uint32_t* list[MRR_MAX_LEVELS];
+  uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
 };
 constexpr int MASK_LUT_MAX = 2048;
 
@@ -115,6 +123,13 @@ struct ShadeLevels {
   void* c[MRR_MAX_LEVELS];
   int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
   const uint32_t* counts;  // device, indexed by level; clamped to W_i * H_i when read
+  // Level-0 blend (a single level-0 list): instead of storing c_0, blend it into the
+  // merged output of the coarser levels by Eq. (1), with alpha = min(w_0 a_0, 1) and a_0
+  // read from blend_a at the entry's list position.
+  float* blend_out;
+  const float* blend_a;
+  float blend_w;
+  int blend_C;
 };
 
 // One frame of a batched shading launch (k_batch.cu); an array of these lives in

@@ -111,6 +111,7 @@ def check_frame(mrr, fr, cfg, precision="fp32", check_full=True):
     mrr.mrr_render(ctx, dev, out2)
     torch.cuda.synchronize()
     assert torch.equal(out, out2)
+    assert mrr.mrr_fault_flags(ctx) == 0
     if check_full:
         full = mrr.alloc_output(ctx, W, H)
         mrr.mrr_render_full(ctx, dev, full)
