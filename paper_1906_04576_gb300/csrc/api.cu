@@ -25,6 +25,7 @@ struct mrr_ctx {
   // pools of mrr_render / mrr_masks, sized for max_width x max_height
   int pool_W = 0, pool_H = 0;
   uint8_t* edges = nullptr;
+  uint32_t* ebits = nullptr;  // mrr_render's bit-packed edge image
   float* alpha[MRR_MAX_LEVELS] = {};
   uint8_t* stencil[MRR_MAX_LEVELS] = {};
   uint32_t* worklist[MRR_MAX_LEVELS] = {};
@@ -284,7 +285,7 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
 }
 
 mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream_t s, uint32_t* zero = nullptr,
-                      int zero_words = 0) {
+                      int zero_words = 0, uint32_t* ebits = nullptr) {
   EdgeParams p;
   std::memset(&p, 0, sizeof p);
   p.v = make_view(g->width, g->height, g->cam);
@@ -296,6 +297,8 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.fault = ctx->fault;
   p.zero = zero;
   p.zero_words = zero_words;
+  p.ebits = ebits;
+  p.ewords = (g->width + 31) / 32;
   const int h = ctx->cfg.precision == MRR_FP16;
   MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
   return MRR_OK;
@@ -419,12 +422,14 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   const int W = g->width, H = g->height;
   if (c.num_levels < 2) return render_launches_staged(ctx, g, out, s);
   if (!fits_pools(ctx, W, H)) return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size", W, H);
-  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS);
+  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS, ctx->ebits);
   if (st != MRR_OK) return st;
   mrr_levels lv = pool_levels(ctx, W, H);
   MaskParams m = mask_params(ctx, &lv);
   m.label = nullptr;
   m.a0c = ctx->alpha[0];
+  m.ebits = ctx->ebits;
+  m.ewords = (W + 31) / 32;
   for (int i = 0; i < c.num_levels; ++i) m.list[i] = c.enabled[i] ? ctx->worklist[i] : nullptr;
   m.counts = ctx->counts;
   MRR_CUDA(ctx, launch_masks(m, ctx->edges, s));
@@ -494,6 +499,7 @@ void free_pools(mrr_ctx* ctx) {
   ctx->graph_exec = nullptr;
   ctx->capture_stream = nullptr;
   cudaFree(ctx->edges);
+  cudaFree(ctx->ebits);
   for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
     cudaFree(ctx->alpha[i]);
     cudaFree(ctx->stencil[i]);
@@ -518,6 +524,7 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
   ctx->pool_H = H;
   const size_t npx = (size_t)W * H;
   MRR_CUDA(ctx, cudaMalloc(&ctx->edges, npx));
+  MRR_CUDA(ctx, cudaMalloc(&ctx->ebits, (size_t)((W + 31) / 32) * H * sizeof(uint32_t)));
   size_t chunks = 0;
   for (int i = 0; i < c.num_levels; ++i) {
     const size_t n = (size_t)level_dim(W, i) * level_dim(H, i);

@@ -36,6 +36,19 @@ __device__ __forceinline__ void zero_words(const EdgeParams& p) {
   for (int i = tid; i < p.zero_words; i += nthr) p.zero[i] = 0u;
 }
 
+// Store the edge flag e of pixel (x, y): one byte per pixel, or -- bit-packed output --
+// one ballot per 32 pixels of a row (bit b of word w = pixel 32 w + b; bits past the
+// image's last column are 0).  All 32 lanes of the warp call it together for one row y
+// with x = x0 + lane, x0 a multiple of 32; `valid` is false outside the image.
+__device__ __forceinline__ void store_edge(const EdgeParams& p, uint8_t* E, int x, int y, bool valid, bool e) {
+  if (p.ebits) {
+    const uint32_t b = __ballot_sync(0xffffffffu, valid && e);
+    if ((threadIdx.x & 31) == 0 && x < p.v.W && y < p.v.H) p.ebits[(size_t)y * p.ewords + (x >> 5)] = b;
+  } else if (valid) {
+    E[(size_t)y * p.v.W + x] = e ? 1 : 0;
+  }
+}
+
 template <typename NT, typename SMT>
 __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float* __restrict__ depth,
                                                         const NT* __restrict__ normal,
@@ -67,11 +80,11 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   }
   __syncthreads();
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-  if (x >= W || y >= H) return;
+  const bool valid = x < W && y < H;
   const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
   const float d = sd[ly][lx];
   uint8_t e = 0;
-  if (d < p.v.farp) {
+  if (valid && d < p.v.farp) {
     const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
     const float nx = snx[ly][lx], ny = sny[ly][lx], nz = snz[ly][lx];
     const uint8_t hs = shs[ly][lx];
@@ -97,7 +110,7 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
       if (fabsf(lap) > p.depth_rel * d) e = 1;
     }
   }
-  E[(size_t)y * W + x] = e;
+  store_edge(p, E, x, y, valid, e != 0);
 }
 
 // edges_direct_kernel: a lane owns a column of ER vertically adjacent pixels.  Every
@@ -114,16 +127,18 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
   const int W = p.v.W, H = p.v.H;
   const int x = blockIdx.x * TX + threadIdx.x;
   const int y0 = (blockIdx.y * TY + threadIdx.y) * ER;
-  if (x >= W || y0 >= H) return;
+  // lanes past the right edge read the last column and store nothing (every lane of the
+  // warp reaches the bit-packed store)
+  const int xc = min(x, W - 1);
   const float farp = p.v.farp;
-  const int xl = max(x - 1, 0), xr = min(x + 1, W - 1);
+  const int xl = max(xc - 1, 0), xr = min(xc + 1, W - 1);
   float dc[ER + 2], dl[ER], dr[ER];
   float3 nc[ER + 2], nl[ER], nr[ER];
 #pragma unroll
   for (int r = -1; r <= ER; ++r) {
     const int y = min(max(y0 + r, 0), H - 1);
-    dc[r + 1] = __ldg(depth + y * W + x);
-    nc[r + 1] = load_normal(normal, y * W + x);
+    dc[r + 1] = __ldg(depth + y * W + xc);
+    nc[r + 1] = load_normal(normal, y * W + xc);
   }
 #pragma unroll
   for (int r = 0; r < ER; ++r) {
@@ -136,10 +151,10 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
 #pragma unroll
   for (int r = 0; r < ER; ++r) {
     const int y = y0 + r;
-    if (y >= H) break;
+    const bool valid = x < W && y < H;
     const float d = dc[r + 1];
     uint8_t e = 0;
-    if (d < farp) {
+    if (valid && d < farp) {
       const float3 n = nc[r + 1];
       const bool has[4] = {x > 0, x < W - 1, y > 0, y < H - 1};
       const float dn[4] = {dl[r], dr[r], dc[r], dc[r + 2]};
@@ -162,7 +177,7 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
         if (fabsf(lap) > p.depth_rel * d) e = 1;
       }
     }
-    E[y * W + x] = e;
+    store_edge(p, E, x, y, valid, e != 0);
   }
 }
 
@@ -231,7 +246,8 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
   bool ok = true;
   for (; k < nlocal; ++k) {
     const int s = k % ESTAGES;
-    ok = mbar_wait(&full[s], (uint32_t)(k / ESTAGES) & 1u);
+    // warp-uniform: the bit-packed store below is a whole-warp ballot
+    ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)(k / ESTAGES) & 1u));
     if (ok) {
       const int t = (int)blockIdx.x + k * (int)gridDim.x;
       const int x0 = (t % gx) * ETW, y0 = (t / gx) * ETH;
@@ -277,10 +293,8 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
                 (hasl && hasr && fabsf(lapx.y) > thr.y) || (hasd1 && fabsf(lapy.y) > thr.y);
       e0 = e0 && d0 < farp2;
       e1 = e1 && d1 < farp2;
-      if (x < W) {
-        if (y < H) E[(size_t)y * W + x] = e0 ? 1 : 0;
-        if (y + 1 < H) E[(size_t)(y + 1) * W + x] = e1 ? 1 : 0;
-      }
+      store_edge(p, E, x, y, x < W && y < H, e0);
+      store_edge(p, E, x, y + 1, x < W && y + 1 < H, e1);
     }
     // every thread is done with stage s before it is refilled; a failed wait anywhere
     // ends the CTA's walk

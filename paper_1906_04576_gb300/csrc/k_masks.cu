@@ -306,6 +306,7 @@ __device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, i
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (warp == 0) {
+    uint32_t mine = 0;  // lane i: level i's count
 #pragma unroll
     for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
       const uint32_t pc = (i < m.L && lane < (TS >> i)) ? (uint32_t)__popc(sm.S[i][lane]) : 0u;
@@ -317,8 +318,10 @@ __device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, i
       }
       if (lane < (TS >> i)) sm.rowpre[i][lane] = inc - pc;
       const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
-      if (lane == 0 && i < m.L && m.mode[i] != 2) sm.excl[i] = cnt ? atomicAdd(m.counts + i, cnt) : 0u;
+      if (lane == i) mine = cnt;
     }
+    // the levels' reservations go out together (one round trip, not four)
+    if (lane < m.L && m.mode[lane] != 2) sm.excl[lane] = mine ? atomicAdd(m.counts + lane, mine) : 0u;
   }
   __syncthreads();
   // level 0: warp w owns rows ROWS0 w .. ROWS0 w + ROWS0 - 1, lane = column
@@ -360,7 +363,17 @@ __global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const 
   const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
   // stage the edge rows y0-24 .. y0+55, columns x0-32 .. x0+63, as bits (zero outside the image)
   uint32_t* Ew = reinterpret_cast<uint32_t*>(sm.E);
-  if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
+  if (m.ebits) {
+    // bit-packed edge image: the three words of each staged row
+    for (int k = threadIdx.x; k < ER * EWORDS; k += MTHREADS) {
+      const int r = k / EWORDS, w = k - r * EWORDS;
+      const int y = y0 - MG + r, wx = (x0 >> 5) - 1 + w;
+      uint32_t v = 0u;
+      if (y >= 0 && y < H && wx >= 0 && wx < m.ewords) v = __ldg(m.ebits + (size_t)y * m.ewords + wx);
+      Ew[4 * r + w] = v;
+    }
+    if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
+  } else if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
     // 16 pixels per 16-byte load (segments lie wholly inside or outside the image);
     // every load of the CTA is issued before the first is used
     constexpr int SEGS = EWORDS * 2, TASKS = ER * SEGS, ROUNDS = (TASKS + MTHREADS - 1) / MTHREADS;

@@ -72,6 +72,8 @@ struct EdgeParams {
   uint32_t* fault;  // device fault word of the context (tma.cuh)
   uint32_t* zero;   // words the launch sets to 0 for the next kernel (may be null)
   int zero_words;
+  uint32_t* ebits;  // non-null: write the edge image bit-packed here, ewords words per row
+  int ewords;
 };
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
@@ -94,6 +96,8 @@ struct MaskParams {
   // (tiles in any order, texels of a tile in row-major order), level 0's a only as a0c
   // (aligned with level 0's list), and neither alpha[0] nor stencil[0].
   float* a0c;
+  const uint32_t* ebits;  // non-null: the edge image bit-packed (ewords words per row), read instead of E
+  int ewords;
   uint32_t* list[MRR_MAX_LEVELS];
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
 };
