@@ -321,7 +321,7 @@ mrr_levels pool_levels(mrr_ctx* ctx, int W, int H) {
 }
 
 mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
-                      bool skip_level0 = false) {
+                      bool compact_level0 = false) {
   const mrr_config& cf = ctx->cfg;
   MergeParams mp;
   std::memset(&mp, 0, sizeof mp);
@@ -339,8 +339,22 @@ mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
     mp.stencil[i] = lv->stencil[i];
     mp.c[i] = c[i];
   }
-  if (skip_level0) mp.enabled[0] = 0;
+  if (compact_level0) mp.enabled[0] = 0;  // blended afterwards from level 0's list
   MRR_CUDA(ctx, launch_merge(mp, out, s));
+  if (compact_level0 && cf.enabled[0]) {
+    Blend0Params bp;
+    std::memset(&bp, 0, sizeof bp);
+    bp.W = mp.W;
+    bp.H = mp.H;
+    bp.C = mp.C;
+    bp.half_store = mp.half_store;
+    bp.weight = cf.weight[0];
+    bp.list = ctx->worklist[0];
+    bp.count = ctx->counts;
+    bp.a0c = ctx->alpha[0];
+    bp.c0c = ctx->cbuf[0];
+    MRR_CUDA(ctx, launch_blend0(bp, out, s));
+  }
   return MRR_OK;
 }
 
@@ -413,10 +427,11 @@ bool fits_pools(const mrr_ctx* ctx, int W, int H) {
 
 mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s);
 
-// With at least two levels: edges (also clearing the per-level counts), masks that also
-// write the work lists, the levels above 0, their merge, and level 0 shaded straight into
-// the merged image -- level 0's c_0, a_0 and S_0 never reach memory, and no compaction
-// launch is needed.
+// With at least two levels: edges (also clearing the per-level counts; the edge image
+// bit-packed), masks that also write the work lists and level 0's a_0 list-aligned, one
+// shading launch over every level (level 0's c_0 list-aligned too), the merge of the
+// levels above 0, and level 0 blended in over its list.  Level 0's full-resolution a_0,
+// S_0 and c_0 never reach memory, and no compaction launch is needed.
 mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const mrr_config& c = ctx->cfg;
   const int W = g->width, H = g->height;
@@ -434,10 +449,9 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   m.counts = ctx->counts;
   MRR_CUDA(ctx, launch_masks(m, ctx->edges, s));
   ShadeParams p = make_shade_params(ctx, *g);
-  const FrameIn in = make_frame_in(*g);
   ShadeLevels sl;
   std::memset(&sl, 0, sizeof sl);
-  for (int i = 1; i < c.num_levels; ++i) {
+  for (int i = 0; i < c.num_levels; ++i) {
     if (!c.enabled[i]) continue;
     const int k = sl.nlev++;
     sl.level[k] = i;
@@ -445,26 +459,11 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
     sl.c[k] = ctx->cbuf[i];
     sl.Wi[k] = lv.width[i];
     sl.Hi[k] = lv.height[i];
+    if (i == 0) sl.compact |= 1 << k;
   }
   sl.counts = ctx->counts;
-  MRR_CUDA(ctx, launch_shade_levels(p, in, c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
-  st = merge_impl(ctx, &lv, ctx->cbuf, out, s, true);
-  if (st != MRR_OK || !c.enabled[0]) return st;
-  ShadeLevels s0;
-  std::memset(&s0, 0, sizeof s0);
-  s0.nlev = 1;
-  s0.level[0] = 0;
-  s0.list[0] = ctx->worklist[0];
-  s0.c[0] = ctx->cbuf[0];
-  s0.Wi[0] = W;
-  s0.Hi[0] = H;
-  s0.counts = ctx->counts;
-  s0.blend_out = out;
-  s0.blend_a = ctx->alpha[0];
-  s0.blend_w = c.weight[0];
-  s0.blend_C = channels(c);
-  MRR_CUDA(ctx, launch_shade_levels(p, in, c.precision, s0, ctx->shade_grid, ctx->split_texel, s));
-  return MRR_OK;
+  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
+  return merge_impl(ctx, &lv, ctx->cbuf, out, s, true);
 }
 
 // One level only (level 0 is the coarsest): edges, masks, compaction, shading, merge.

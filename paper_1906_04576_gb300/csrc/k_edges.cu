@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
 
 // ---- TMA-staged edge detection (SSAO, SSGI)
 constexpr int ETW = 32, ETH = 16, ESTAGES = 4, ETHREADS = 256;
+static_assert(ETH % (2 * (ETHREADS / 32)) == 0, "whole pixel pairs per warp");
 constexpr int DOFF = 4, DW = ETW + 2 * DOFF;             // depth staged from x0 - 4 (16-byte start)
 constexpr uint32_t DBYTES = DW * (ETH + 2) * 4;          // 2880
 template <typename NT> struct EdgeTma;
@@ -253,8 +254,10 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       const int x0 = (t % gx) * ETW, y0 = (t / gx) * ETH;
       const NT* sn = reinterpret_cast<const NT*>(sbase + s * SB);
       const float* sd = reinterpret_cast<const float*>(sbase + s * SB + NP);
+#pragma unroll
+      for (int pr = 0; pr < ETH / (2 * (ETHREADS / 32)); ++pr) {
       // the lane's two vertically adjacent pixels (rows r0, r0 + 1 of the tile)
-      const int r0 = 2 * warp, x = x0 + lane, y = y0 + r0;
+      const int r0 = 2 * warp + 2 * (ETHREADS / 32) * pr, x = x0 + lane, y = y0 + r0;
       const int ly = r0 + 1, cd = lane + DOFF, cn = lane + T::NOFF;
       const float du = sd[(ly - 1) * DW + cd], d0 = sd[ly * DW + cd], d1 = sd[(ly + 1) * DW + cd],
                   dd = sd[(ly + 2) * DW + cd];
@@ -295,6 +298,7 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       e1 = e1 && d1 < farp2;
       store_edge(p, E, x, y, x < W && y < H, e0);
       store_edge(p, E, x, y + 1, x < W && y + 1 < H, e1);
+      }
     }
     // every thread is done with stage s before it is refilled; a failed wait anywhere
     // ends the CTA's walk

@@ -321,7 +321,11 @@ __device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, i
       if (lane == i) mine = cnt;
     }
     // the levels' reservations go out together (one round trip, not four)
-    if (lane < m.L && m.mode[lane] != 2) sm.excl[lane] = mine ? atomicAdd(m.counts + lane, mine) : 0u;
+    uint32_t start = 0u;
+    if (lane < m.L && m.mode[lane] != 2) {
+      start = mine ? atomicAdd(m.counts + lane, mine) : 0u;
+      sm.excl[lane] = start;
+    }
   }
   __syncthreads();
   // level 0: warp w owns rows ROWS0 w .. ROWS0 w + ROWS0 - 1, lane = column

@@ -308,6 +308,31 @@ __global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __res
 }
 
 template <typename CT, int C>
+__global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __restrict__ out) {
+  const uint32_t n = min(__ldg(p.count), (uint32_t)p.W * (uint32_t)p.H);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t e = __ldg(p.list + k);
+    const int x = (int)(e & 0xFFFFu), y = (int)(e >> 16);
+    if (x >= p.W || y >= p.H) continue;
+    // as the merge kernel blends level 0: one tap of weight 1, a rendered texel
+    const float ahat = 0.0f + 1.0f * __ldg(p.a0c + k);
+    const float wa = p.weight * ahat;
+    const float alpha = (1.0f < wa) ? 1.0f : wa;
+    if (!(alpha > 0.0f)) continue;
+    const float3 v = load_c<CT>(p.c0c, k, C);
+    const float om = 1.0f - alpha;
+    const size_t o = (size_t)y * p.W + x;
+    if (C == 4) {
+      float4* q = reinterpret_cast<float4*>(out) + o;
+      const float4 c = *q;
+      *q = make_float4(v.x * alpha + c.x * om, v.y * alpha + c.y * om, v.z * alpha + c.z * om, 0.0f);
+    } else {
+      out[o] = v.x * alpha + out[o] * om;
+    }
+  }
+}
+
+template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
   dim3 grid((p.W + MT - 1) / MT, (p.H + MT - 1) / MT);
   switch (p.L) {
@@ -319,6 +344,30 @@ void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
 }
 
 }  // namespace
+
+int blend0_grid() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = (sms > 0 ? sms : 1) * 8;
+  }
+  return blocks;
+}
+
+cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s) {
+  const int grid = blend0_grid();
+  if (p.C == 4) {
+    if (p.half_store) blend0_kernel<__half, 4><<<grid, 256, 0, s>>>(p, out);
+    else blend0_kernel<float, 4><<<grid, 256, 0, s>>>(p, out);
+  } else {
+    if (p.half_store) blend0_kernel<__half, 1><<<grid, 256, 0, s>>>(p, out);
+    else blend0_kernel<float, 1><<<grid, 256, 0, s>>>(p, out);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s) {
   if (p.C == 4) {

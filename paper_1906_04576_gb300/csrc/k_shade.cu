@@ -55,33 +55,6 @@ __device__ __forceinline__ void store_value(void* c, size_t i, float3 v, bool ha
   }
 }
 
-// Eq. (1) for level 0 at pixel px, in place of storing c_0: the value is first rounded as
-// a stored binary16 sub-image would round it, then blended exactly as the merge kernel
-// blends level 0 (one tap of weight 1, alpha = min(w_0 a_0, 1), skipped when alpha <= 0).
-template <int EFFECT>
-__device__ __forceinline__ void blend_level0(const ShadeLevels& lv, uint32_t entry, size_t px, float3 v,
-                                             bool half_store) {
-  if (half_store) {
-    v.x = __half2float(__float2half_rn(v.x));
-    v.y = __half2float(__float2half_rn(v.y));
-    v.z = __half2float(__float2half_rn(v.z));
-  }
-  const float a0 = __ldg(lv.blend_a + entry);
-  const float ahat = 0.0f + 1.0f * a0;
-  const float wa = lv.blend_w * ahat;
-  const float alpha = (1.0f < wa) ? 1.0f : wa;
-  if (!(alpha > 0.0f)) return;
-  const float om = 1.0f - alpha;
-  if (EFFECT == MRR_SSGI) {
-    float4* o = reinterpret_cast<float4*>(lv.blend_out) + px;
-    const float4 c = *o;
-    *o = make_float4(v.x * alpha + c.x * om, v.y * alpha + c.y * om, v.z * alpha + c.z * om, 0.0f);
-  } else {
-    float* o = lv.blend_out + px;
-    *o = v.x * alpha + *o * om;
-  }
-}
-
 template <int EFFECT, typename NT, typename SMT, int SPLIT>
 __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv,
                                                                      int half_store) {
@@ -127,10 +100,9 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadePar
       y = min((qy << i) + o, H - 1);
     }
     const float3 v = effect_at<EFFECT, NT, SMT, SPLIT>(p, in, x, y, valid);
-    if (valid && sub == 0) {
-      if (lv.blend_out) blend_level0<EFFECT>(lv, g - s_pre[k], (size_t)y * W + x, v, half_store != 0);
-      else store_value<EFFECT>(s_c[k], (size_t)qy * s_W[k] + qx, v, half_store != 0);
-    }
+    if (valid && sub == 0)
+      store_value<EFFECT>(s_c[k], ((lv.compact >> k) & 1) ? (size_t)(g - s_pre[k]) : (size_t)qy * s_W[k] + qx, v,
+                          half_store != 0);
   }
 }
 

@@ -127,13 +127,9 @@ struct ShadeLevels {
   void* c[MRR_MAX_LEVELS];
   int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
   const uint32_t* counts;  // device, indexed by level; clamped to W_i * H_i when read
-  // Level-0 blend (a single level-0 list): instead of storing c_0, blend it into the
-  // merged output of the coarser levels by Eq. (1), with alpha = min(w_0 a_0, 1) and a_0
-  // read from blend_a at the entry's list position.
-  float* blend_out;
-  const float* blend_a;
-  float blend_w;
-  int blend_C;
+  // bit k set: slot k stores its values at the entry's list position (a list-aligned,
+  // compact sub-image) instead of at texel (qy, qx)
+  int compact;
 };
 
 // One frame of a batched shading launch (k_batch.cu); an array of these lives in
@@ -156,6 +152,17 @@ struct MergeParams {
   const void* c[MRR_MAX_LEVELS];
 };
 
+// Level 0's part of Eq. (1) over level 0's work list, after the coarser levels are merged
+// into `out`: entry k (pixel list[k]) has a_0 = a0c[k] and c_0 at position k of c0c.
+struct Blend0Params {
+  int W, H, C, half_store;
+  float weight;
+  const uint32_t* list;
+  const uint32_t* count;  // device: entries in the list
+  const float* a0c;
+  const void* c0c;
+};
+
 // ---- launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s);
@@ -166,6 +173,7 @@ cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int pre
 cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
                               cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
+cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s);
 
 void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)
 int shade_grid_blocks();  // grid multiplier base of the work-list kernel (grid = multiple of its resident CTAs)
