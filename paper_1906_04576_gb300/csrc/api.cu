@@ -427,6 +427,26 @@ bool fits_pools(const mrr_ctx* ctx, int W, int H) {
 
 mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s);
 
+// The frame path's first two launches (at least two levels): edges, bit-packed, also
+// clearing the per-level counts; masks that also write every enabled level's work list
+// and level 0's a_0 list-aligned (into the level-0 alpha pool).
+mrr_status frame_masks(mrr_ctx* ctx, const mrr_gbuffer* g, mrr_levels* lv, cudaStream_t s) {
+  const mrr_config& c = ctx->cfg;
+  const int W = g->width, H = g->height;
+  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS, ctx->ebits);
+  if (st != MRR_OK) return st;
+  *lv = pool_levels(ctx, W, H);
+  MaskParams m = mask_params(ctx, lv);
+  m.label = nullptr;
+  m.a0c = ctx->alpha[0];
+  m.ebits = ctx->ebits;
+  m.ewords = (W + 31) / 32;
+  for (int i = 0; i < c.num_levels; ++i) m.list[i] = c.enabled[i] ? ctx->worklist[i] : nullptr;
+  m.counts = ctx->counts;
+  MRR_CUDA(ctx, launch_masks(m, ctx->edges, s));
+  return MRR_OK;
+}
+
 // With at least two levels: edges (also clearing the per-level counts; the edge image
 // bit-packed), masks that also write the work lists and level 0's a_0 list-aligned, one
 // shading launch over every level (level 0's c_0 list-aligned too), the merge of the
@@ -437,17 +457,9 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   const int W = g->width, H = g->height;
   if (c.num_levels < 2) return render_launches_staged(ctx, g, out, s);
   if (!fits_pools(ctx, W, H)) return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size", W, H);
-  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS, ctx->ebits);
+  mrr_levels lv;
+  mrr_status st = frame_masks(ctx, g, &lv, s);
   if (st != MRR_OK) return st;
-  mrr_levels lv = pool_levels(ctx, W, H);
-  MaskParams m = mask_params(ctx, &lv);
-  m.label = nullptr;
-  m.a0c = ctx->alpha[0];
-  m.ebits = ctx->ebits;
-  m.ewords = (W + 31) / 32;
-  for (int i = 0; i < c.num_levels; ++i) m.list[i] = c.enabled[i] ? ctx->worklist[i] : nullptr;
-  m.counts = ctx->counts;
-  MRR_CUDA(ctx, launch_masks(m, ctx->edges, s));
   ShadeParams p = make_shade_params(ctx, *g);
   ShadeLevels sl;
   std::memset(&sl, 0, sizeof sl);
@@ -788,12 +800,21 @@ mrr_status check_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* fr
 mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames, float* const* outs, int n,
                           int chunk, int grid, cudaStream_t s) {
   mrr_levels lv[MAX_BATCH];
+  bool framed[MAX_BATCH];  // the frame path (at least two levels) or the staged one
   for (int k = 0; k < n; ++k) {
     mrr_ctx* ctx = ctxs[k];
-    mrr_status st = edges_impl(ctx, &frames[k], ctx->edges, s);
-    if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
-    lv[k] = pool_levels(ctx, frames[k].width, frames[k].height);
-    st = masks_impl(ctx, ctx->edges, &lv[k], s);
+    framed[k] = ctx->cfg.num_levels >= 2;
+    mrr_status st;
+    if (framed[k]) {
+      if (!fits_pools(ctx, frames[k].width, frames[k].height))
+        return batch_fail(b, MRR_EINVAL, "frame exceeds its context's max size");
+      st = frame_masks(ctx, &frames[k], &lv[k], s);
+    } else {
+      st = edges_impl(ctx, &frames[k], ctx->edges, s);
+      if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
+      lv[k] = pool_levels(ctx, frames[k].width, frames[k].height);
+      st = masks_impl(ctx, ctx->edges, &lv[k], s);
+    }
     if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
   }
   for (int k = 0; k < n; ++k) {
@@ -811,6 +832,7 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
       it.lv.c[q] = ctx->cbuf[i];
       it.lv.Wi[q] = lv[k].width[i];
       it.lv.Hi[q] = lv[k].height[i];
+      if (i == 0 && framed[k]) it.lv.compact |= 1 << q;
     }
     it.lv.counts = ctx->counts;
   }
@@ -820,7 +842,7 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     return batch_fail(b, MRR_ECUDA, "batched shading launch");
   if (outs) {
     for (int k = 0; k < n; ++k) {
-      mrr_status st = merge_impl(ctxs[k], &lv[k], ctxs[k]->cbuf, outs[k], s);
+      mrr_status st = merge_impl(ctxs[k], &lv[k], ctxs[k]->cbuf, outs[k], s, framed[k]);
       if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
     }
   }

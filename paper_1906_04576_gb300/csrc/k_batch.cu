@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) shade_batch_kernel(const Bat
       float3 v;
       if (it.precision == MRR_FP16) v = batch_effect<half4, __half>(it.p, it.in, x, y);
       else v = batch_effect<float4, float>(it.p, it.in, x, y);
-      batch_store(it.lv.c[k], (size_t)qy * it.lv.Wi[k] + qx, v, it.p.effect, it.precision == MRR_FP16);
+      const size_t at = ((it.lv.compact >> k) & 1) ? (size_t)(g - s_pre[s]) : (size_t)qy * it.lv.Wi[k] + qx;
+      batch_store(it.lv.c[k], at, v, it.p.effect, it.precision == MRR_FP16);
     }
   }
 }
