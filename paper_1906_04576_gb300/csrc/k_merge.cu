@@ -224,6 +224,45 @@ __device__ __forceinline__ void blend_level(const MergeParams& p, const MergeSme
   }
 }
 
+// The coarsest level when it is level 3 and every staged texel is rendered (the weight sum
+// is then exactly 1): a warp's four rows read the same four texels, only the vertical
+// weight differs, so the lane reads the taps once and takes two rows at a time in packed
+// FP32x2 (each half one correctly rounded multiply or add: the scalar form's bits).
+template <int C>
+__device__ __forceinline__ void first_level3(const MergeSmem<C>& sm, int lane, int warp, float (&c)[RPW][3]) {
+  constexpr int I = 3, side = Lv<3>::side, off = Lv<3>::off, o = Lv<3>::o, mask = Lv<3>::mask;
+  constexpr int NCH = C == 4 ? 3 : 1;
+  const float inv = 0.125f;  // 2^-3
+  const int lx = ((lane - o) >> I) + 1;
+  const float fx = (float)((lane - o) & mask) * inv;
+  const float gx = 1.0f - fx;
+  const int t0 = off + (((RPW * warp - o) >> I) + 1) * side + lx;
+  float tap[NCH][4];
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    tap[ch][0] = sm.cz[ch][t0];
+    tap[ch][1] = sm.cz[ch][t0 + 1];
+    tap[ch][2] = sm.cz[ch][t0 + side];
+    tap[ch][3] = sm.cz[ch][t0 + side + 1];
+  }
+  const float2 gx2 = make_float2(gx, gx), fx2 = make_float2(fx, fx);
+#pragma unroll
+  for (int rr = 0; rr < RPW; rr += 2) {
+    const float2 fy = make_float2((float)((RPW * warp + rr - o) & mask) * inv,
+                                  (float)((RPW * warp + rr + 1 - o) & mask) * inv);
+    const float2 gy = make_float2(1.0f - fy.x, 1.0f - fy.y);
+    const float2 w[4] = {__fmul2_rn(gx2, gy), __fmul2_rn(fx2, gy), __fmul2_rn(gx2, fy), __fmul2_rn(fx2, fy)};
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      float2 n = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) n = __fadd2_rn(n, __fmul2_rn(w[k], make_float2(tap[ch][k], tap[ch][k])));
+      c[rr][ch] = n.x;
+      c[rr + 1][ch] = n.y;
+    }
+  }
+}
+
 template <typename CT, int C, int L>
 __global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __restrict__ out) {
   __shared__ MergeSmem<C> sm;
@@ -253,7 +292,10 @@ __global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __res
   for (int k = 0; k < MTHR / 32; ++k) any |= sm.any[k];
   float c[RPW][3] = {};
   // coarsest level first, then the finer enabled levels whose footprint holds a_i > 0
-  if (L == 4) blend_level<C, (L == 4 ? 3 : 1), true>(p, sm, lane, warp, !(any & 128), c);
+  if (L == 4) {
+    if (!(any & 128)) first_level3<C>(sm, lane, warp, c);
+    else blend_level<C, (L == 4 ? 3 : 1), true>(p, sm, lane, warp, false, c);
+  }
   if (L == 3) blend_level<C, (L == 3 ? 2 : 1), true>(p, sm, lane, warp, !(any & 64), c);
   if (L > 3 && p.enabled[2] && (any & 4)) blend_level<C, (L > 3 ? 2 : 1), false>(p, sm, lane, warp, !(any & 64), c);
   if (L == 2) blend_level<C, 1, true>(p, sm, lane, warp, !(any & 32), c);
