@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "full-res-equiv Mpix/s multires vs plain full-res at RMSE<=1e-2; p50/p99 frame ms"
 FLUSH_BYTES = 256 << 20
+SCENES = 24  # seeded scenes per configuration, in rotation over the timed steps
 
 
 def dist_env():
@@ -171,7 +172,7 @@ def make_frame(sg, wl, seed):
                       shadow_size=wl.get("shadow_size", 0))
 
 
-def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=60):
+def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
     """The oracle, as it stands, rendering whole frames of the workload on the host cores
     until about budget_s seconds of CPU work have been spent."""
     import oracle as orc
@@ -193,10 +194,19 @@ def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=60):
         times.append(time.perf_counter() - t)
         n += 1
     total = sum(times)
+    cores = orc.num_threads()
+    # one frame on a single host thread, beside the all-cores figure
+    orc.set_threads(1)
+    t = time.perf_counter()
+    orc.render(fr, cfg, "f32")
+    t1 = time.perf_counter() - t
+    orc.set_threads(cores)
     return {"value": round(n * wl["width"] * wl["height"] / total / 1e6, 4), "unit": "Mpix/s",
-            "cores": orc.num_threads(), "kind": "oracle",
+            "cores": cores, "kind": "oracle",
             "sample": f"{n} whole {wl['width']}x{wl['height']} frames of {name} (float oracle, OpenMP over rows)",
-            "seconds": round(total, 3)}
+            "seconds": round(total, 3),
+            "single_thread": {"value": round(wl["width"] * wl["height"] / t1 / 1e6, 4), "unit": "Mpix/s",
+                              "sample": "one frame on one host thread"}}
 
 
 def run_reference(args):
@@ -480,13 +490,26 @@ def main():
     prec = cfg["precision"]
     if "batch_with" in wl:
         return run_batch(args, mrr, sg, wl, cfg, rank, world, dist)
-    fr = make_frame(sg, wl, rank)
+    # SCENES seeded scenes (seeds SCENES*rank .. +SCENES-1), all resident; before each timed
+    # step the next one is copied into the frame buffers the renders read (outside the
+    # events), so every step is a different scene while the captured launches stay valid
+    frames = [make_frame(sg, wl, SCENES * rank + k) for k in range(SCENES)]
+    fr = frames[0]
     ctx = mrr.mrr_create(cfg)
+    scenes = [mrr.upload_frame(f, prec) for f in frames]
     dev = mrr.upload_frame(fr, prec)
     out = mrr.alloc_output(ctx, W, H)
     full = mrr.alloc_output(ctx, W, H)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+
+    def load_scene(k):
+        src = scenes[k % SCENES]
+        dev.depth.copy_(src.depth)
+        dev.normal.copy_(src.normal)
+        dev.color.copy_(src.color)
+        if dev.shadow_map is not None:
+            dev.shadow_map.copy_(src.shadow_map)
 
     def barrier():
         torch.cuda.synchronize()
@@ -499,7 +522,8 @@ def main():
     def timed(fn, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
-        for s, e in ev:
+        for k, (s, e) in enumerate(ev):
+            load_scene(k)
             flush.zero_()
             s.record(stream)
             fn()
@@ -524,8 +548,9 @@ def main():
     launches = mrr.mrr_kernel_launches() - l0
     t_full = timed(render_full, args.steps)
 
-    # dominant kernel: the work-list shading launch of the same frame, timed alone with
-    # CUDA events on the launching stream
+    # dominant kernel: the work-list shading launch of scene 0, timed alone with CUDA
+    # events on the launching stream
+    load_scene(0)
     edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
     levels = mrr.alloc_levels(W, H, cfg["num_levels"], with_label=False)
     subs = mrr.alloc_subimages(ctx, W, H)
@@ -562,12 +587,24 @@ def main():
         h2d += host.shadow_map.numel() * host.shadow_map.element_size()
     d2h = out_h.numel() * 4
 
-    # quality gate: RMSE of the multi-resolution image against full-resolution shading
-    mrr.mrr_render(ctx, dev, out, stream)
-    mrr.mrr_render_full(ctx, dev, full, stream)
+    # quality gate: RMSE of the multi-resolution image against full-resolution shading,
+    # every scene (the gate is the worst one); texels shaded per scene
+    rmses, shaded = [], []
+    for k in range(SCENES):
+        load_scene(k)
+        mrr.mrr_render(ctx, dev, out, stream)
+        mrr.mrr_render_full(ctx, dev, full, stream)
+        mrr.mrr_edges(ctx, dev, edges, stream)
+        mrr.mrr_masks(ctx, edges, levels, stream)
+        torch.cuda.synchronize()
+        diff = (out - full)[..., :3] if out.dim() == 3 else (out - full)
+        rmses.append(float(torch.sqrt(torch.mean(diff.double() ** 2)).item()))
+        shaded.append(int(levels.counts[: cfg["num_levels"]].sum().item()))
+    rmse = max(rmses)
+    load_scene(0)
+    mrr.mrr_edges(ctx, dev, edges, stream)
+    mrr.mrr_masks(ctx, edges, levels, stream)
     torch.cuda.synchronize()
-    diff = (out - full)[..., :3] if out.dim() == 3 else (out - full)
-    rmse = float(torch.sqrt(torch.mean(diff.double() ** 2)).item())
 
     counts = levels.counts.cpu().tolist()
     depth_host = fr.depth
@@ -601,13 +638,15 @@ def main():
             "dtype": "f16-storage/f32" if prec == "fp16" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "width": W, "height": H, "effect": cfg["effect"],
                        "samples": cfg.get("samples"), "levels": cfg["num_levels"], "precision": prec,
-                       "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, seed = rank",
+                       "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
+                                f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",
                        "l2": "flushed (256 MiB write) before every timed step, outside the events",
                        "parallelism": f"replicas x{world}"},
             "full_res": {"value": round(full_value, 3), "unit": "Mpix/s", "p50_ms": round(pct(t_full, 0.5), 5),
                          "p99_ms": round(pct(t_full, 0.99), 5)},
             "speedup_vs_full_res": round(value / full_value, 4),
-            "rmse_vs_full_res": rmse,
+            "rmse_vs_full_res": rmse, "rmse_mean": round(statistics.mean(rmses), 6),
+            "shaded_texels_mean": round(statistics.mean(shaded), 1),
             "shaded_texels": n_all, "shaded_fraction": round(n_all / (W * H), 5),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": measured_traffic(args.workload),
@@ -615,7 +654,7 @@ def main():
                          "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": round(world * e2e_steps * W * H / e2e_s / 1e6, 3), "unit": "Mpix/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "api": "mrr_render_host (pinned host buffers, copies and sync inside)"},
+                    "api": "mrr_render_host (pinned host buffers, copies and sync inside; scene 0)"},
             "gpu_launches": int(launches),
             "tuning": tuning,
             "clocks": clocks,
