@@ -96,7 +96,8 @@ typedef struct mrr_config {
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the
  * tangent of half the vertical field of view, near and far.  View space is
- * (right, up, -forward).  Linear depth is the distance along forward. */
+ * (right, up, -forward).  Linear depth is the distance along forward.  The frame's camera
+ * must satisfy 2^-60 <= near_plane < far_plane <= 2^60 (MRR_EINVAL otherwise). */
 typedef struct mrr_camera {
   float eye[3], right[3], up[3], forward[3];
   float tan_half_fov, near_plane, far_plane;
@@ -348,6 +349,16 @@ const char* mrr_last_error(mrr_ctx* ctx);
  * Synchronises the device, copies the word to *flags and, if `clear` is nonzero, resets
  * it.  Not part of the paper's method; it makes a stalled load visible to the host. */
 mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear);
+
+/* Diagnostic: the effect kernels project sample points with their own correctly rounded
+ * reciprocal (Newton-Raphson refinement of the hardware estimate) instead of IEEE
+ * division.  This runs it over every float whose bit pattern lies in [first_bits,
+ * last_bits], and over their negatives, on the current device, compares each result bit
+ * for bit with IEEE division and stores the number of differences in *mismatches (0 over
+ * [2^-64, 2^64) is the claim the projections rely on).  Synchronous; allocates 8 bytes
+ * of device memory for the count.  MRR_EINVAL for a NULL pointer or last < first.  Not
+ * part of the paper's method. */
+mrr_status mrr_check_reciprocal(uint32_t first_bits, uint32_t last_bits, uint64_t* mismatches);
 
 #ifdef __cplusplus
 }

@@ -154,6 +154,7 @@ _lib.mrr_masks_static.restype = ctypes.c_int
 _lib.mrr_kernel_launches.argtypes = []
 _lib.mrr_kernel_launches.restype = ctypes.c_uint64
 _lib.mrr_fault_flags.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+_lib.mrr_check_reciprocal.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
@@ -558,6 +559,13 @@ def mrr_release(s: Server, ticket: int) -> None:
 
 def mrr_kernel_launches() -> int:
     return int(_lib.mrr_kernel_launches())
+
+
+def mrr_check_reciprocal(first_bits: int, last_bits: int) -> int:
+    """Mismatches of the kernels' reciprocal against IEEE division over a range of floats."""
+    n = ctypes.c_uint64(0)
+    _check(None, _lib.mrr_check_reciprocal(first_bits, last_bits, ctypes.byref(n)))
+    return int(n.value)
 
 
 def mrr_fault_flags(ctx: Context, clear: bool = False) -> int:

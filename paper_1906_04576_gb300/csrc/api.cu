@@ -73,6 +73,9 @@ struct mrr_batch {
 namespace {
 
 constexpr int MAX_DIM = 16384;
+// camera depth range: every projected sample depth then lies where the kernels'
+// reciprocal is the correctly rounded one (2^-64 <= d < 2^64)
+constexpr float CAM_MIN_NEAR = 0x1p-60f, CAM_MAX_FAR = 0x1p60f;
 
 mrr_status fail(mrr_ctx* ctx, mrr_status st, const char* fmt, ...) {
   if (ctx) {
@@ -160,8 +163,9 @@ mrr_status check_gbuffer(mrr_ctx* ctx, const mrr_gbuffer* g, bool need_device_al
   if (!g->depth || !g->normal) return fail(ctx, MRR_EINVAL, "depth and normal planes are required");
   if (need_device_align && !aligned(g->normal, ctx->cfg.precision == MRR_FP16 ? 8 : 16))
     return fail(ctx, MRR_EINVAL, "normal plane is not aligned to its element size");
-  if (!(g->cam.tan_half_fov > 0.f) || !(g->cam.near_plane > 0.f) || !(g->cam.far_plane > g->cam.near_plane))
-    return fail(ctx, MRR_EINVAL, "camera needs tan_half_fov > 0 and 0 < near < far");
+  if (!(g->cam.tan_half_fov > 0.f) || !(g->cam.near_plane >= CAM_MIN_NEAR) || !(g->cam.far_plane > g->cam.near_plane) ||
+      !(g->cam.far_plane <= CAM_MAX_FAR))
+    return fail(ctx, MRR_EINVAL, "camera needs tan_half_fov > 0 and 2^-60 <= near < far <= 2^60");
   if (ctx->cfg.effect == MRR_SSGI) {
     if (!g->color) return fail(ctx, MRR_EINVAL, "SSGI needs the direct-light colour plane");
     if (need_device_align && !aligned(g->color, 8)) return fail(ctx, MRR_EINVAL, "colour plane not 8-byte aligned");
@@ -649,6 +653,20 @@ void mrr_destroy(mrr_ctx* ctx) {
 }
 
 const char* mrr_last_error(mrr_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+mrr_status mrr_check_reciprocal(uint32_t first_bits, uint32_t last_bits, uint64_t* mismatches) {
+  if (!mismatches || last_bits < first_bits) return MRR_EINVAL;
+  unsigned long long* bad = nullptr;
+  if (cudaMalloc(&bad, sizeof *bad) != cudaSuccess) return MRR_ENOMEM;
+  unsigned long long host = 0;
+  bool ok = cudaMemset(bad, 0, sizeof *bad) == cudaSuccess &&
+            launch_check_reciprocal(first_bits, last_bits, bad, nullptr) == cudaSuccess &&
+            cudaMemcpy(&host, bad, sizeof host, cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(bad);
+  if (!ok) return MRR_ECUDA;
+  *mismatches = host;
+  return MRR_OK;
+}
 
 mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear) {
   if (!ctx || !flags) return MRR_EINVAL;

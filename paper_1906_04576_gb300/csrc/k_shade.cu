@@ -177,6 +177,25 @@ void full_dispatch(const ShadeParams& p, const FrameIn& in, float* out, int spli
 
 }  // namespace
 
+__global__ void check_reciprocal_kernel(uint32_t first, uint32_t last, unsigned long long* bad) {
+  unsigned long long n = 0;
+  for (uint64_t b = (uint64_t)first + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b <= last;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    const float x = __uint_as_float((uint32_t)b);
+    const float2 two = rcp_rn2(make_float2(x, -x));
+    const uint32_t want = __float_as_uint(__frcp_rn(x));
+    n += (__float_as_uint(rcp_rn(x)) != want) + (__float_as_uint(two.x) != want) +
+         (__float_as_uint(two.y) != (want ^ 0x80000000u));
+  }
+  if (n) atomicAdd(bad, n);
+}
+
+cudaError_t launch_check_reciprocal(uint32_t first, uint32_t last, unsigned long long* bad, cudaStream_t s) {
+  check_reciprocal_kernel<<<152 * 16, 256, 0, s>>>(first, last, bad);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 std::atomic<uint64_t>& launch_counter() {
   static std::atomic<uint64_t> n{0};
   return n;

@@ -173,6 +173,9 @@ cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int pre
 cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
                               cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
+// bit patterns [first, last] as floats x: counts into *bad every x where the kernels'
+// reciprocal of x or of -x differs from IEEE division
+cudaError_t launch_check_reciprocal(uint32_t first, uint32_t last, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s);
 
 void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)
