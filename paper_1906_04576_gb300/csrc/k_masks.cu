@@ -34,8 +34,9 @@ constexpr int EWORDS = 3;                // 96 staged edge columns: [x0 - 32, x0
 constexpr int EX = 32;                   // column of the tile's first pixel in the staged rows
 constexpr int MAXR = 6;
 constexpr int DROWS = TS / 2 + 2 * MAXR; // 28: largest D region side above level 0 (level 1)
-constexpr int MTHREADS = 256;            // 8 warps
+constexpr int MTHREADS = 128;            // threads per CTA
 constexpr int ROWS0 = TS / (MTHREADS / 32);  // level-0 tile rows per warp
+static_assert(ROWS0 % 4 == 0, "level-0 rows come in groups of four");
 static_assert(ER % (MTHREADS / 32) == 0, "edge rows split evenly over the warps");
 static_assert(DROWS <= 32, "a D row of a level above 0 fits one word");
 
@@ -129,45 +130,48 @@ __device__ __forceinline__ void store_rows(uint32_t* rows, int k, bool st) {
 // one is given) and the vertical taps from registers.
 template <int R>
 __device__ __forceinline__ void level0_blur(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  constexpr int NH = ROWS0 + 2 * R;
+  constexpr int GR = 4;                  // rows per group: a group's sums stay in registers
+  constexpr int NH = GR + 2 * R;
   constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ty0 = ROWS0 * warp;
   const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
   const int b = EX - R + lane;           // first staged column of the lane's window
   const int k = b >> 5, sh = b & 31;
-  float h[NH];
-  uint32_t any = 0;
-#pragma unroll
-  for (int j = 0; j < NH; ++j) {
-    const uint4 row = sm.E[MG + ty0 - R + j];
-    const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
-    const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
-    any |= win;
-    h[j] = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
-  }
-  const bool blur = __any_sync(0xffffffffu, any != 0u);
   float g[2 * R + 1];
 #pragma unroll
   for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[0][t];
   const int x = x0 + lane;
+#pragma unroll 1
+  for (int ty0 = ROWS0 * warp; ty0 < ROWS0 * (warp + 1); ty0 += GR) {
+    float h[NH];
+    uint32_t any = 0;
 #pragma unroll
-  for (int rr = 0; rr < ROWS0; ++rr) {
-    float s = 0.0f;
-    if (blur) {
+    for (int j = 0; j < NH; ++j) {
+      const uint4 row = sm.E[MG + ty0 - R + j];
+      const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
+      const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
+      any |= win;
+      h[j] = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
+    }
+    const bool blur = __any_sync(0xffffffffu, any != 0u);
 #pragma unroll
-      for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], h[rr + t], s);
+    for (int rr = 0; rr < GR; ++rr) {
+      float s = 0.0f;
+      if (blur) {
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], h[rr + t], s);
+      }
+      const int y = y0 + ty0 + rr;
+      const bool inside = x < m.W && y < m.H;
+      if (m.a0c) {
+        sm.a0t[ty0 + rr][lane] = s;
+      } else if (inside) {
+        m.alpha[0][(size_t)y * m.W + x] = s;
+        m.stencil[0][(size_t)y * m.W + x] = s > 0.0f ? 1 : 0;
+      }
+      const uint32_t bits = __ballot_sync(0xffffffffu, inside && s > 0.0f);
+      if (lane == 0) sm.S[0][ty0 + rr] = bits;
     }
-    const int y = y0 + ty0 + rr;
-    const bool inside = x < m.W && y < m.H;
-    if (m.a0c) {
-      sm.a0t[ty0 + rr][lane] = s;
-    } else if (inside) {
-      m.alpha[0][(size_t)y * m.W + x] = s;
-      m.stencil[0][(size_t)y * m.W + x] = s > 0.0f ? 1 : 0;
-    }
-    const uint32_t bits = __ballot_sync(0xffffffffu, inside && s > 0.0f);
-    if (lane == 0) sm.S[0][ty0 + rr] = bits;
   }
 }
 
@@ -348,19 +352,19 @@ __device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, i
   for (int i = 1; i < MRR_MAX_LEVELS; ++i) {
     if (i >= m.L || m.mode[i] == 2) continue;
     const int Ti = TS >> i;
-    const int k = threadIdx.x;
-    if (k >= Ti * Ti) continue;
-    const int r = k / Ti, c = k - r * Ti;
-    const uint32_t bits = sm.S[i][r];
-    if ((bits >> c) & 1u) {
-      const size_t pos = (size_t)sm.excl[i] + sm.rowpre[i][r] + __popc(bits & ((1u << c) - 1u));
-      if (pos < (size_t)m.Wi[i] * m.Hi[i])
-        m.list[i][pos] = ((uint32_t)((y0 >> i) + r) << 16) | (uint32_t)((x0 >> i) + c);
+    for (int k = threadIdx.x; k < Ti * Ti; k += MTHREADS) {
+      const int r = k / Ti, c = k - r * Ti;
+      const uint32_t bits = sm.S[i][r];
+      if ((bits >> c) & 1u) {
+        const size_t pos = (size_t)sm.excl[i] + sm.rowpre[i][r] + __popc(bits & ((1u << c) - 1u));
+        if (pos < (size_t)m.Wi[i] * m.Hi[i])
+          m.list[i][pos] = ((uint32_t)((y0 >> i) + r) << 16) | (uint32_t)((x0 >> i) + c);
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
+__global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
   __shared__ MaskSmem sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int W = m.W, H = m.H;
@@ -381,28 +385,32 @@ __global__ void __launch_bounds__(MTHREADS, 8) masks_kernel(MaskParams m, const 
     // 16 pixels per 16-byte load (segments lie wholly inside or outside the image);
     // every load of the CTA is issued before the first is used
     constexpr int SEGS = EWORDS * 2, TASKS = ER * SEGS, ROUNDS = (TASKS + MTHREADS - 1) / MTHREADS;
-    uint4 v[ROUNDS];
+    constexpr int BATCH = ROUNDS < 2 ? ROUNDS : 2;  // loads in flight per thread
 #pragma unroll
-    for (int j = 0; j < ROUNDS; ++j) {
-      const int k = threadIdx.x + j * MTHREADS;
-      const int r = k / SEGS, sg = k - r * SEGS;
-      const int y = y0 - MG + r, x = x0 - EX + 16 * sg;
-      v[j] = make_uint4(0u, 0u, 0u, 0u);
-      if (k < TASKS && y >= 0 && y < H && x >= 0 && x < W)
-        v[j] = __ldg(reinterpret_cast<const uint4*>(E + (size_t)y * W + x));
-    }
+    for (int j0 = 0; j0 < ROUNDS; j0 += BATCH) {
+      uint4 v[BATCH];
 #pragma unroll
-    for (int j = 0; j < ROUNDS; ++j) {
-      const int k = threadIdx.x + j * MTHREADS;
-      if (k >= TASKS) break;
-      const int r = k / SEGS, sg = k - r * SEGS;
-      // one bit per nonzero byte: byte flags 0/1 gathered into a nibble by one multiply
-      const uint32_t q0 = (__vcmpne4(v[j].x, 0u) & 0x01010101u) * 0x01020408u;
-      const uint32_t q1 = (__vcmpne4(v[j].y, 0u) & 0x01010101u) * 0x01020408u;
-      const uint32_t q2 = (__vcmpne4(v[j].z, 0u) & 0x01010101u) * 0x01020408u;
-      const uint32_t q3 = (__vcmpne4(v[j].w, 0u) & 0x01010101u) * 0x01020408u;
-      const uint32_t bits = (q0 >> 24) | ((q1 >> 24) << 4) | ((q2 >> 24) << 8) | ((q3 >> 24) << 12);
-      reinterpret_cast<uint16_t*>(Ew + 4 * r)[sg] = (uint16_t)bits;
+      for (int j = 0; j < BATCH; ++j) {
+        const int k = threadIdx.x + (j0 + j) * MTHREADS;
+        const int r = k / SEGS, sg = k - r * SEGS;
+        const int y = y0 - MG + r, x = x0 - EX + 16 * sg;
+        v[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (j0 + j < ROUNDS && k < TASKS && y >= 0 && y < H && x >= 0 && x < W)
+          v[j] = __ldg(reinterpret_cast<const uint4*>(E + (size_t)y * W + x));
+      }
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const int k = threadIdx.x + (j0 + j) * MTHREADS;
+        if (j0 + j >= ROUNDS || k >= TASKS) break;
+        const int r = k / SEGS, sg = k - r * SEGS;
+        // one bit per nonzero byte: byte flags 0/1 gathered into a nibble by one multiply
+        const uint32_t q0 = (__vcmpne4(v[j].x, 0u) & 0x01010101u) * 0x01020408u;
+        const uint32_t q1 = (__vcmpne4(v[j].y, 0u) & 0x01010101u) * 0x01020408u;
+        const uint32_t q2 = (__vcmpne4(v[j].z, 0u) & 0x01010101u) * 0x01020408u;
+        const uint32_t q3 = (__vcmpne4(v[j].w, 0u) & 0x01010101u) * 0x01020408u;
+        const uint32_t bits = (q0 >> 24) | ((q1 >> 24) << 4) | ((q2 >> 24) << 8) | ((q3 >> 24) << 12);
+        reinterpret_cast<uint16_t*>(Ew + 4 * r)[sg] = (uint16_t)bits;
+      }
     }
     if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
   } else {

@@ -101,7 +101,7 @@ struct MaskParams {
   uint32_t* list[MRR_MAX_LEVELS];
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
 };
-constexpr int MASK_LUT_MAX = 2048;
+constexpr int MASK_LUT_MAX = 512;  // level 0's table for R <= 4 (larger R sums the taps)
 
 // Work-list compaction of all levels in one launch: level l owns chunks
 // [chunk_begin[l], chunk_begin[l+1]) of COMPACT_CHUNK texels each.
