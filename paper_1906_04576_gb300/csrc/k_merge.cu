@@ -1,11 +1,11 @@
 // k_merge.cu -- upsampling and blending of the sub-images (Sec. 4.2, Eq. (1)).
 //
-// A CTA owns a 32x32 tile of full-resolution pixels; warp w owns the 4 consecutive rows
-// 4w .. 4w+3 and lane x the column.  Level texel q sits at full-resolution position
+// A CTA owns a 32x16 tile of full-resolution pixels (128 threads, so that many tiles are
+// in flight per SM); warp w owns the 4 consecutive rows 4w .. 4w+3 and lane x the column.  Level texel q sits at full-resolution position
 // 2^i q + o_i, so pixel p reads level coordinate u = (p - o_i) / 2^i, whose floor and
 // fraction are exactly (p - o_i) >> i and ((p - o_i) & (2^i - 1)) * 2^-i; the taps
 // floor(u), floor(u)+1 are clamped to the level.  For every level above 0 the CTA stages
-// the (clamped) taps its tile can touch -- at most (32/2^i + 2)^2 texels -- in shared
+// the (clamped) taps its tile can touch -- (32/2^i + 2) x (16/2^i + 2) texels -- in shared
 // memory once: a_i, the stencil as 0/1 and c_i with unrendered texels replaced by 0, so
 // that w * c and w * s are exactly the terms a rendered tap adds and +0 otherwise.  The
 // 4 rows of a warp touch only 4 / 3 / 2 footprint rows of levels 1 / 2 / 3, which the lane
@@ -21,20 +21,24 @@ namespace mrr {
 
 namespace {
 
-constexpr int MT = 32;                  // tile side (pixels)
-constexpr int RPW = MT / 8;             // consecutive pixel rows per warp
-constexpr int MTHR = 256;
+constexpr int MTHR = 128;               // threads per CTA
+constexpr int RPW = 4;                  // consecutive pixel rows per warp
+constexpr int MTX = 32;                 // tile width (pixels): a warp row
+constexpr int MTY = RPW * (MTHR / 32);  // tile height (pixels)
 
 template <int I> struct Lv {
-  static constexpr int side = (MT >> I) + 2;   // footprint side of the tile at level I
-  static constexpr int off = I <= 1 ? 0 : (I == 2 ? ((MT >> 1) + 2) * ((MT >> 1) + 2)
-                                                  : ((MT >> 1) + 2) * ((MT >> 1) + 2) + ((MT >> 2) + 2) * ((MT >> 2) + 2));
+  static constexpr int side = (MTX >> I) + 2;  // footprint columns of the tile at level I (row stride)
+  static constexpr int rows = (MTY >> I) + 2;  // footprint rows
+  static constexpr int n = side * rows;
   static constexpr int o = I == 0 ? 0 : (1 << (I - 1));
   static constexpr int mask = (1 << I) - 1;
   // footprint rows that the RPW rows of a warp touch (tap rows included)
   static constexpr int nr = I == 1 ? 4 : (I == 2 ? 3 : 2);
 };
-constexpr int NTAP = Lv<3>::off + Lv<3>::side * Lv<3>::side;  // 460
+// staged entries: level 1, then level 2, then level 3
+template <int I> constexpr int lv_off() { return I <= 1 ? 0 : (I == 2 ? Lv<1>::n : Lv<1>::n + Lv<2>::n); }
+constexpr int NTAP = Lv<1>::n + Lv<2>::n + Lv<3>::n;
+static_assert(MTY % 8 == 0 && MTX % 8 == 0, "tiles cover whole level-3 texels");
 
 template <int C> struct MergeSmem {
   float a[NTAP];
@@ -66,7 +70,7 @@ __device__ __forceinline__ void load_entry(const MergeParams& p, int X0, int Y0,
   constexpr int side = Lv<I>::side;
   const int ly = kk / side, lx = kk - ly * side;
   const int Wi = p.Wi[I], Hi = p.Hi[I];
-  // footprint origin: (X0 - o_I) >> I = X0 / 2^I - 1, X0 being a multiple of 32
+  // footprint origin: (X0 - o_I) >> I = X0 / 2^I - 1, X0 and Y0 being multiples of 8
   const int qx = min(max((X0 >> I) - 1 + lx, 0), Wi - 1);
   const int qy = min(max((Y0 >> I) - 1 + ly, 0), Hi - 1);
   const size_t q = (size_t)qy * Wi + qx;
@@ -75,50 +79,46 @@ __device__ __forceinline__ void load_entry(const MergeParams& p, int X0, int Y0,
   cv = load_c<CT>(p.c[I], q, C);  // unrendered texels hold stale values, replaced by 0 below
 }
 
-// Stage the footprints of the enabled levels 1..L-1 (level 1: 324 entries, level 2: 100,
-// level 3: 36, over two rounds of the CTA's threads); every load is issued before the
-// first is used.  Leaves per warp in sm.any bit I when a staged a_I is positive and bit
-// 4 + I when a staged texel of level I is not rendered.
+// Stage the footprints of the enabled levels 1..L-1 (entry k of the concatenation
+// level 1, level 2, level 3 in round k / MTHR); every load is issued before the first is
+// used.  Leaves per warp in sm.any bit I when a staged a_I is positive and bit 4 + I when
+// a staged texel of level I is not rendered.
 template <typename CT, int C, int L>
 __device__ __forceinline__ void stage(const MergeParams& p, MergeSmem<C>& sm, int X0, int Y0) {
-  constexpr int N1 = Lv<1>::side * Lv<1>::side, N2 = Lv<2>::side * Lv<2>::side, N3 = Lv<3>::side * Lv<3>::side;
-  static_assert(N1 >= MTHR && N1 + N2 + N3 <= 2 * MTHR, "two staging rounds");
-  const int t = threadIdx.x;
-  uint8_t st[2] = {0, 0};
-  float av[2] = {0.f, 0.f};
-  float3 cv[2] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f)};
-  int lev[2] = {0, 0}, ent[2] = {0, 0};
-  // round 0: level-1 entry t (level 1 exists when L > 1)
-  if (L > 1 && p.enabled[1]) {
-    load_entry<CT, C, 1>(p, X0, Y0, t, st[0], av[0], cv[0]);
-    lev[0] = 1;
-    ent[0] = t;
-  }
-  // round 1: the rest of level 1, then levels 2 and 3
-  if (t < N1 - MTHR) {
-    if (L > 1 && p.enabled[1]) {
-      load_entry<CT, C, 1>(p, X0, Y0, MTHR + t, st[1], av[1], cv[1]);
-      lev[1] = 1;
-      ent[1] = MTHR + t;
-    }
-  } else if (t < N1 - MTHR + N2) {
-    if (L > 2 && p.enabled[2]) {
-      load_entry<CT, C, (L > 2 ? 2 : 1)>(p, X0, Y0, t - (N1 - MTHR), st[1], av[1], cv[1]);
-      lev[1] = 2;
-      ent[1] = Lv<2>::off + t - (N1 - MTHR);
-    }
-  } else if (t < N1 - MTHR + N2 + N3) {
-    if (L > 3) {
-      load_entry<CT, C, (L > 3 ? 3 : 1)>(p, X0, Y0, t - (N1 - MTHR + N2), st[1], av[1], cv[1]);
-      lev[1] = 3;
-      ent[1] = Lv<3>::off + t - (N1 - MTHR + N2);
+  constexpr int N1 = Lv<1>::n, N2 = Lv<2>::n, ROUNDS = (NTAP + MTHR - 1) / MTHR;
+  uint8_t st[ROUNDS];
+  float av[ROUNDS];
+  float3 cv[ROUNDS];
+  int lev[ROUNDS];
+#pragma unroll
+  for (int j = 0; j < ROUNDS; ++j) {
+    const int k = threadIdx.x + j * MTHR;
+    lev[j] = 0;
+    st[j] = 0;
+    av[j] = 0.0f;
+    cv[j] = make_float3(0.f, 0.f, 0.f);
+    if (k < N1) {
+      if (L > 1 && p.enabled[1]) {
+        load_entry<CT, C, 1>(p, X0, Y0, k, st[j], av[j], cv[j]);
+        lev[j] = 1;
+      }
+    } else if (k < N1 + N2) {
+      if (L > 2 && p.enabled[2]) {
+        load_entry<CT, C, (L > 2 ? 2 : 1)>(p, X0, Y0, k - N1, st[j], av[j], cv[j]);
+        lev[j] = 2;
+      }
+    } else if (k < NTAP) {
+      if (L > 3) {
+        load_entry<CT, C, (L > 3 ? 3 : 1)>(p, X0, Y0, k - N1 - N2, st[j], av[j], cv[j]);
+        lev[j] = 3;
+      }
     }
   }
   int any = 0;
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < ROUNDS; ++j) {
     if (lev[j] == 0) continue;
-    const int k = ent[j];
+    const int k = threadIdx.x + j * MTHR;
     const bool on = st[j] != 0;
     sm.a[k] = av[j];
     sm.s[k] = on ? 1.0f : 0.0f;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void stage(const MergeParams& p, MergeSmem<C>& sm, in
 template <int C, int I, bool FIRST>
 __device__ __forceinline__ void blend_level(const MergeParams& p, const MergeSmem<C>& sm, int lane, int warp,
                                             bool allon, float (&c)[RPW][3]) {
-  constexpr int side = Lv<I>::side, off = Lv<I>::off, o = Lv<I>::o, mask = Lv<I>::mask, NR = Lv<I>::nr;
+  constexpr int side = Lv<I>::side, off = lv_off<I>(), o = Lv<I>::o, mask = Lv<I>::mask, NR = Lv<I>::nr;
   const float inv = __int_as_float((127 - I) << 23);  // 2^-I
   const int lx = ((lane - o) >> I) + 1;
   const float fx = (float)((lane - o) & mask) * inv;
@@ -230,7 +230,7 @@ __device__ __forceinline__ void blend_level(const MergeParams& p, const MergeSme
 // FP32x2 (each half one correctly rounded multiply or add: the scalar form's bits).
 template <int C>
 __device__ __forceinline__ void first_level3(const MergeSmem<C>& sm, int lane, int warp, float (&c)[RPW][3]) {
-  constexpr int I = 3, side = Lv<3>::side, off = Lv<3>::off, o = Lv<3>::o, mask = Lv<3>::mask;
+  constexpr int I = 3, side = Lv<3>::side, off = lv_off<3>(), o = Lv<3>::o, mask = Lv<3>::mask;
   constexpr int NCH = C == 4 ? 3 : 1;
   const float inv = 0.125f;  // 2^-3
   const int lx = ((lane - o) >> I) + 1;
@@ -267,7 +267,7 @@ template <typename CT, int C, int L>
 __global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __restrict__ out) {
   __shared__ MergeSmem<C> sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int X0 = blockIdx.x * MT, Y0 = blockIdx.y * MT;
+  const int X0 = blockIdx.x * MTX, Y0 = blockIdx.y * MTY;
   const int W = p.W, H = p.H;
   const int x = X0 + lane;
   // level 0 taps first: they need no shared memory
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __re
 
 template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
-  dim3 grid((p.W + MT - 1) / MT, (p.H + MT - 1) / MT);
+  dim3 grid((p.W + MTX - 1) / MTX, (p.H + MTY - 1) / MTY);
   switch (p.L) {
     case 1: merge_kernel<CT, C, 1><<<grid, MTHR, 0, s>>>(p, out); break;
     case 2: merge_kernel<CT, C, 2><<<grid, MTHR, 0, s>>>(p, out); break;
