@@ -554,7 +554,10 @@ def mrr_request_info(s: Server, ticket: int) -> dict:
 
 
 def mrr_release(s: Server, ticket: int) -> None:
-    _check(None, _lib.mrr_release(s.handle, ticket)) if False else _lib.mrr_release(s.handle, ticket)
+    """Forget a completed request's record (MrrError for an unknown or unfinished ticket)."""
+    st = _lib.mrr_release(s.handle, ticket)
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_release")
 
 
 def mrr_kernel_launches() -> int:

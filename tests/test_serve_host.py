@@ -47,6 +47,8 @@ def test_every_request_completes_and_effects_share_batches(mrr):
         mrr.mrr_release(srv, t)
     with pytest.raises(mrr.MrrError):
         mrr.mrr_request_info(srv, t0)
+    with pytest.raises(mrr.MrrError):   # a released ticket is unknown
+        mrr.mrr_release(srv, t0)
     mrr.mrr_server_destroy(srv)
 
 
