@@ -192,6 +192,26 @@ def make_frame(sg, wl, seed):
                       shadow_size=wl.get("shadow_size", 0))
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the oracle timing."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
     """The oracle, as it stands, rendering whole frames of the workload on the host cores
     until about budget_s seconds of CPU work have been spent."""
@@ -222,7 +242,7 @@ def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
     t1 = time.perf_counter() - t
     orc.set_threads(cores)
     return {"value": round(n * wl["width"] * wl["height"] / total / 1e6, 4), "unit": "Mpix/s",
-            "cores": cores, "kind": "oracle",
+            "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{n} whole {wl['width']}x{wl['height']} frames of {name} (float oracle, OpenMP over rows)",
             "seconds": round(total, 3),
             "single_thread": {"value": round(wl["width"] * wl["height"] / t1 / 1e6, 4), "unit": "Mpix/s",
@@ -273,7 +293,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": args.workload, "width": W, "height": H,
                                             "effect": eff, "levels": wl["levels"]},
             "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": orc.num_threads(),
-                             "kind": "oracle", "sample": sample},
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -1,13 +1,14 @@
 // k_edges.cu -- the edge image of Sec. 3.1.
 //
-// One thread per pixel, one CTA per 32x8 tile.
+// edges_direct_kernel and edges_kernel: one CTA per 32x8 pixel tile.
 // edges_direct_kernel (SSAO, SSGI): each lane reads its pixel and its 4 neighbours
 //   straight from global memory; the neighbours' lines are the block's own rows, so
 //   they are L1 hits and DRAM sees each G-buffer texel about once.
 // edges_tma_kernel (SSAO, SSGI; rows a multiple of 16 bytes): a persistent CTA walks
 //   32x16 output tiles; the tile's depth and normals plus a one-pixel halo arrive by TMA
-//   into a ring of four shared-memory stages, so three tiles are in flight while one is
-//   tested.  Same tests and arithmetic as edges_direct_kernel, read from shared memory.
+//   into a ring of two shared-memory stages, the next tile's loads in flight while one
+//   is tested (eight such CTAs per SM).  Same tests and arithmetic as
+//   edges_direct_kernel, read from shared memory.
 // edges_kernel (soft shadows): the tile and a one-pixel halo of depth, normals and the
 //   one-sample hard shadow of Sec. 3.1 are staged in shared memory, so each staged
 //   texel's hard shadow (a reconstruction, a light-space projection and a shadow-map
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(TX* TY) edges_direct_kernel(EdgeParams p, cons
 }
 
 // ---- TMA-staged edge detection (SSAO, SSGI)
-constexpr int ETW = 32, ETH = 16, ESTAGES = 4, ETHREADS = 256;
+constexpr int ETW = 32, ETH = 16, ESTAGES = 2, ETHREADS = 256;
 static_assert(ETH % (2 * (ETHREADS / 32)) == 0, "whole pixel pairs per warp");
 constexpr int DOFF = 4, DW = ETW + 2 * DOFF;             // depth staged from x0 - 4 (16-byte start)
 constexpr uint32_t DBYTES = DW * (ETH + 2) * 4;          // 2880
