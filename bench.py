@@ -178,6 +178,10 @@ def effect_config(mrr, sg, spec, W, H, precision):
         kw.update(blocker_taps=sg.disk_taps(spec["blocker_samples"], sg.BLOCKER_SEED),
                   pcf_taps=sg.disk_taps(spec["pcf_samples"], sg.PCF_SEED),
                   blocker_samples=spec["blocker_samples"], pcf_samples=spec["pcf_samples"])
+    if "blur" in spec:
+        kw.update(blur=list(spec["blur"]))
+    if "merge_mode" in spec:
+        kw.update(merge_mode=spec["merge_mode"])
     return mrr.default_config(eff, spec["levels"], W, H, precision=precision, **kw)
 
 
@@ -212,11 +216,8 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
-    """The oracle, as it stands, rendering whole frames of the workload on the host cores
-    until about budget_s seconds of CPU work have been spent."""
-    import oracle as orc
-    fr = make_frame(sg, wl, 0)
+def oracle_config(orc, sg, wl):
+    """The oracle's configuration of a workload (the same parameters the library gets)."""
     eff = wl["effect"]
     kw = {}
     if eff in ("ssao", "ssgi"):
@@ -224,7 +225,19 @@ def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
     else:
         kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
                   pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED))
-    cfg = orc.default_config(eff, wl["levels"], **kw)
+    if "blur" in wl:
+        kw.update(blur=list(wl["blur"]))
+    if "merge_mode" in wl:
+        kw.update(merge_mode=wl["merge_mode"])
+    return orc.default_config(eff, wl["levels"], **kw)
+
+
+def cpu_oracle_sample(sg, wl, name, budget_s=10.0, max_frames=2000):
+    """The oracle, as it stands, rendering whole frames of the workload on the host cores
+    until about budget_s seconds of CPU work have been spent."""
+    import oracle as orc
+    fr = make_frame(sg, wl, 0)
+    cfg = oracle_config(orc, sg, wl)
     orc.render(fr, cfg, "f32")   # warm-up (page-in, thread pool)
     n, t0 = 0, time.perf_counter()
     times = []
@@ -261,13 +274,7 @@ def run_reference(args):
     wl = dict(sg.WORKLOADS[args.workload])
     fr = make_frame(sg, wl, 0)
     eff = wl["effect"]
-    kw = {}
-    if eff in ("ssao", "ssgi"):
-        kw.update(kernel=sg.hemisphere_kernel(wl["samples"]), samples=wl["samples"], radius=wl["radius"])
-    else:
-        kw.update(blocker_taps=sg.disk_taps(wl["blocker_samples"], sg.BLOCKER_SEED),
-                  pcf_taps=sg.disk_taps(wl["pcf_samples"], sg.PCF_SEED))
-    cfg = orc.default_config(eff, wl["levels"], **kw)
+    cfg = oracle_config(orc, sg, wl)
     for _ in range(max(1, min(args.warmup, 3))):
         orc.render(fr, cfg, "f32")
     t = time.perf_counter()
@@ -701,6 +708,8 @@ def main():
             "dtype": "f16-storage/f32" if prec == "fp16" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "width": W, "height": H, "effect": cfg["effect"],
                        "samples": cfg.get("samples"), "levels": cfg["num_levels"], "precision": prec,
+                       "blur": cfg.get("blur", [0, 0, 0, 0]),
+                       "merge": "step-wise (Sec. 3.3)" if cfg.get("merge_mode", 0) == 1 else "direct (Sec. 4.2)",
                        "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
                                 f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",
                        "l2": "flushed (256 MiB write) before every timed step, outside the events",

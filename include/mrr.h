@@ -6,7 +6,7 @@
  * The method (Sec. 3) has three steps, and the entry points follow them:
  *   1. masks   (Sec. 3.1, Sec. 4.1): mrr_edges, mrr_masks
  *   2. render the sub-images at their resolutions where their masks allow
- *              (Sec. 3.2, Sec. 4.1): mrr_shade_level
+ *              (Sec. 3.2, Sec. 4.1): mrr_shade_level, optionally mrr_blur_level
  *   3. blend   (Sec. 3.3, Sec. 4.2, Eq. (1)): mrr_upsample_merge
  * mrr_render runs all three for one frame; mrr_render_full is the naive
  * full-resolution rendering the paper compares against (Sec. 5).
@@ -92,6 +92,12 @@ typedef struct mrr_config {
   int no_graph;                   /* 1: mrr_render launches its kernels one by one instead of replaying a
                                      CUDA graph of them (the graph is re-captured whenever the frame
                                      descriptor or output pointer changes) */
+  /* Sec. 4.1: bilateral blur of rendered sub-images (see mrr_blur_level); off when all 0 */
+  int blur[MRR_MAX_LEVELS];       /* 1: mrr_render blurs level i's sub-image before the blend; only
+                                     enabled levels i >= 1 (level 0 is the full-resolution image) */
+  float blur_depth_rel;           /* the blur's depth test: |d' - d| <= blur_depth_rel * d; >= 0, finite */
+  int merge_mode;                 /* 0: direct upsampling of every level (Sec. 4.2); 1: step-wise
+                                     chain (Sec. 3.3), see mrr_upsample_merge */
 } mrr_config;
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the
@@ -180,17 +186,43 @@ mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const 
 mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv, void* const* c_levels_dev,
                             void* stream);
 
+/* Sec. 4.1: bilateral blur of sub-image `level` (1 <= level < num_levels, enabled).
+ * The paper blurs the SSAO sub-images, above all the coarse ones, against the effect's
+ * variance, without taking values from unrendered texels.  For every texel q with
+ * lv->stencil[level][q] = 1:
+ *   b_level_dev[q] = sum_t w_t c(q + t) / sum_t w_t
+ * over the offsets t = (tx, ty), tx, ty in -2..2, whose texel q + t is inside the level,
+ * has its stencil set, and passes the depth test
+ *   |d(s_i(q + t)) - d(s_i(q))| <= cfg.blur_depth_rel * d(s_i(q))
+ * (d = g->depth at a texel's sample pixel); w_t = B[tx] B[ty], B = (1, 4, 6, 4, 1).
+ * q itself always passes, so the weight sum is at least 36.  Sums in row-major window
+ * order, each operation one IEEE float operation; FP16 sub-images are read as half and
+ * the quotient rounded to half.  Texels whose stencil is 0 are neither read nor written
+ * (lv->worklist and lv->counts are not used).  c_level_dev and b_level_dev are laid out
+ * as in mrr_shade_level and must be distinct buffers (MRR_EINVAL otherwise). */
+mrr_status mrr_blur_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const mrr_levels* lv,
+                          const void* c_level_dev, void* b_level_dev, void* stream);
+
 /* Sec. 4.2 and Eq. (1): upsample every enabled sub-image to full resolution and blend
  * them from the coarsest to the finest: a_i is interpolated bilinearly, c_i bilinearly
  * over rendered taps only (weights renormalised), alpha = min(w_i a_i, 1) and
  * c' = c_i alpha + c' (1 - alpha), starting from c' = the coarsest sub-image.
+ * With cfg.merge_mode = 1, the step-wise reading of Sec. 3.3 instead: starting from the
+ * coarsest sub-image, each finer enabled level i is blended at its own resolution with
+ * the previous composite scaled up to it (plain bilinear; texel q of level i sits at
+ * (2^i q + o_i - o_j) / 2^j in texels of the previous level j, taps clamped):
+ * comp_i(q) = c_i(q) alpha + up (1 - alpha), alpha = min(w_i a_i(q), 1), where
+ * S_i(q) = 1 and alpha > 0, else up; the output is the composite at level 0.  That mode
+ * keeps the intermediate composites in the context's pools, so the frame must fit the
+ * context's max size (MRR_EINVAL otherwise).
  * c_levels_dev[i] as in mrr_shade_level (NULL for disabled levels).  out_dev is
  * [H][W] float, or [H][W] float4 (rgb + 0) for MRR_SSGI. */
 mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,
                               void* stream);
 
 /* The whole method for one frame on one stream: edges, masks, work lists, all
- * sub-images, blend -- using the context's pools for every intermediate.  Frames up to
+ * sub-images, the blur of the levels cfg.blur names, blend -- using the context's pools
+ * for every intermediate.  Frames up to
  * the context's max size.  out_dev as in mrr_upsample_merge. */
 mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream);
 

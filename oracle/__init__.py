@@ -56,6 +56,7 @@ class Params(ctypes.Structure):
         ("blocker_taps", ctypes.POINTER(ctypes.c_float)), ("pcf_taps", ctypes.POINTER(ctypes.c_float)),
         ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float), ("store_half", ctypes.c_int),
         ("cam", ctypes.c_float * 15), ("light", ctypes.c_float * 15), ("shadow_size", ctypes.c_int),
+        ("blur", ctypes.c_int * 4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
     ]
 
 
@@ -76,6 +77,8 @@ def _L():
             getattr(lib, f"orc_shade_pixel_{suf}").argtypes = [P, vp, vp, vp, vp, ci, ci, vp]
             getattr(lib, f"orc_view_pos_{suf}").argtypes = [P, ci, ci, ctypes.c_double, vp]
             getattr(lib, f"orc_merge_{suf}").argtypes = [P, vp, vp, vp, vp]
+            getattr(lib, f"orc_blur_level_{suf}").argtypes = [P, vp, ci, vp, vp, vp]
+            getattr(lib, f"orc_merge_stepwise_{suf}").argtypes = [P, vp, vp, vp, vp]
         lib.orc_gauss_weights_f32.argtypes = [ctypes.c_double, vp]
         lib.orc_gauss_weights_f64.argtypes = [ctypes.c_double, vp]
         lib.orc_compact.argtypes = [ci, ci, vp, vp]
@@ -139,7 +142,8 @@ def default_config(effect: str, num_levels: int = 4, **kw) -> dict:
     cfg = dict(effect=effect, num_levels=num_levels, sigma2=sigma2, weight=weight, enabled=enabled,
                depth_rel=0.05, normal_cos=0.9, force_level0=0, samples=16, radius=0.5,
                ao_bias=0.0125, gi_min_dist2=0.01, kernel=None, blocker_samples=32, pcf_samples=64,
-               blocker_taps=None, pcf_taps=None, light_size=0.5, shadow_bias=0.03, store_half=0)
+               blocker_taps=None, pcf_taps=None, light_size=0.5, shadow_bias=0.03, store_half=0,
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0)
     cfg.update(kw)
     return cfg
 
@@ -170,6 +174,11 @@ class _Bound:
         p.pcf_taps = ctypes.cast(_ptr(self.ptaps), ctypes.POINTER(ctypes.c_float))
         p.light_size, p.shadow_bias = cfg["light_size"], cfg["shadow_bias"]
         p.store_half = int(cfg.get("store_half", 0))
+        blur = cfg.get("blur", [0, 0, 0, 0])
+        for i in range(4):
+            p.blur[i] = int(blur[i])
+        p.blur_depth_rel = cfg.get("blur_depth_rel", 0.05)
+        p.merge_mode = int(cfg.get("merge_mode", 0))
         cam = frame.cam.as_array()
         for k in range(15):
             p.cam[k] = cam[k]
@@ -275,24 +284,44 @@ def view_pos(frame, cfg, x, y, d, precision="f64"):
 
 
 def merge(frame, cfg, a, S, c, precision="f32"):
+    """Eq. (1): direct upsampling of every level (Sec. 4.2), or with cfg["merge_mode"] = 1
+    the step-wise chain of Sec. 3.3."""
     b = _Bound(frame, cfg)
     dt = _dtype(precision)
     a = [np.ascontiguousarray(x, dt) for x in a]
     S = [np.ascontiguousarray(x, np.uint8) for x in S]
     c = [np.ascontiguousarray(x, dt) for x in c]
     out = np.zeros((frame.height, frame.width, channels(cfg)), dt)
-    getattr(_L(), f"orc_merge_{_suffix(precision)}")(b.ref, _ptr_array(a), _ptr_array(S), _ptr_array(c), _ptr(out))
+    fn = "orc_merge_stepwise" if cfg.get("merge_mode", 0) == 1 else "orc_merge"
+    getattr(_L(), f"{fn}_{_suffix(precision)}")(b.ref, _ptr_array(a), _ptr_array(S), _ptr_array(c), _ptr(out))
+    return out
+
+
+def blur_level(frame, cfg, level, S, c, precision="f32"):
+    """Bilateral blur of sub-image `level` (Sec. 4.1) over its rendered texels S."""
+    b = _Bound(frame, cfg)
+    dt = _dtype(precision)
+    S = np.ascontiguousarray(S, np.uint8)
+    c = np.ascontiguousarray(c, dt)
+    out = np.empty_like(c)
+    getattr(_L(), f"orc_blur_level_{_suffix(precision)}")(b.ref, _ptr(b.depth), int(level), _ptr(S), _ptr(c),
+                                                           _ptr(out))
     return out
 
 
 def render(frame, cfg, precision="f32") -> dict:
-    """The whole method (Sec. 3): edges -> masks -> work lists -> sub-images -> Eq. (1)."""
+    """The whole method (Sec. 3): edges -> masks -> work lists -> sub-images (blurred
+    where cfg["blur"] asks, Sec. 4.1) -> Eq. (1)."""
     E = edges(frame, cfg, precision)
     a, S, label = masks(frame, cfg, E, precision)
     lists, c = [], []
+    blur = cfg.get("blur", [0, 0, 0, 0])
     for i in range(cfg["num_levels"]):
         wl = compact(S[i])
         lists.append(wl)
-        c.append(shade_level(frame, cfg, i, wl, precision))
+        ci = shade_level(frame, cfg, i, wl, precision)
+        if blur[i]:
+            ci = blur_level(frame, cfg, i, S[i], ci, precision)
+        c.append(ci)
     out = merge(frame, cfg, a, S, c, precision)
     return dict(E=E, a=a, S=S, label=label, lists=lists, c=c, out=out)

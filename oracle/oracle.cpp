@@ -13,10 +13,12 @@
 //             downsample to each level, Gaussian blur with variance sigma_i^2
 //             (Table 1), inclusive nesting of the levels (Sec. 3.1, Fig. 2/3);
 //   Sec. 4.1  stencil = [mask > 0]; each sub-image shaded only where its stencil is set;
+//             optionally a bilateral blur of the rendered sub-images;
 //   Sec. 2.4  the effects (SSAO, PCSS soft shadows, SSGI) -- the paper gives no
 //             formulas, so the readings below are fixed in the design notes;
 //   Sec. 4.2  bilinear upsampling of every sub-image to full size and the sequential
-//             blend of Eq. (1), from the coarsest level to the finest.
+//             blend of Eq. (1), from the coarsest level to the finest; optionally the
+//             step-wise chain of Sec. 3.3 instead.
 // T = float is the parity oracle (discrete decisions in the kernels' precision, FP32);
 // T = double is the FP64 reference for error statements.  The build uses
 // -ffp-contract=off: a multiply-add is fused only where the source writes std::fma
@@ -58,6 +60,9 @@ struct orc_params {
   float cam[15];         // eye, right, up, forward, tan(fov/2), near, far
   float light[15];       // the light camera, same layout
   int shadow_size;       // S, shadow map is S x S
+  int blur[4];           // 1: level i's sub-image gets the bilateral blur of Sec. 4.1
+  float blur_depth_rel;  // that blur's depth test: |d' - d| <= blur_depth_rel * d
+  int merge_mode;        // 0: direct upsampling (Sec. 4.2); 1: step-wise chain (Sec. 3.3)
 };
 
 }  // extern "C"
@@ -587,6 +592,58 @@ void shade_level(const orc_params& p, const Inputs& in, int level, const uint32_
   }
 }
 
+// ---------------------------------------------------------------- Sec. 4.1 sub-image blur
+
+// Bilateral blur of sub-image i (Sec. 4.1: the SSAO sub-images, above all the coarse
+// ones, are blurred against sampling variance, and the blur must not take values from
+// texels that were never rendered).  For every rendered texel q (S_i(q) = 1):
+//   b_i(q) = sum_t w_t c_i(q + t) / sum_t w_t,
+// the sums taken over the offsets t = (tx, ty) of the 5 x 5 window, tx, ty in -2..2, whose
+// texel q + t is inside the level, rendered, and on q's surface:
+//   |d(s_i(q + t)) - d(s_i(q))| <= blur_depth_rel * d(s_i(q)),
+// d being the full-resolution depth at a texel's sample pixel s_i.  The spatial weight is
+// w_t = B[tx] B[ty] with the binomial row B = (1, 4, 6, 4, 1) (Pascal's triangle, the
+// discrete Gaussian of variance 1).  Both sums run over the window in row-major order;
+// q itself always takes part, so the denominator is at least 36.  Texels outside the
+// stencil are copied unchanged.
+template <typename T>
+void blur_level(const orc_params& p, const float* depth, int level, const uint8_t* S, const T* c, T* b) {
+  const int W = p.width, H = p.height, C = channels(p);
+  const int Wi = level_dim(W, level), Hi = level_dim(H, level);
+  const T B[5] = {T(1), T(4), T(6), T(4), T(1)};
+  const T rel = (T)p.blur_depth_rel;
+#pragma omp parallel for schedule(static)
+  for (int qy = 0; qy < Hi; ++qy) {
+    for (int qx = 0; qx < Wi; ++qx) {
+      const size_t q = (size_t)qy * Wi + qx;
+      if (!S[q]) {
+        for (int ch = 0; ch < C; ++ch) b[q * C + ch] = c[q * C + ch];
+        continue;
+      }
+      const T d = (T)depth[(size_t)level_sample(qy, level, H) * W + level_sample(qx, level, W)];
+      T num[3] = {T(0), T(0), T(0)}, den = T(0);
+      for (int ty = -2; ty <= 2; ++ty) {
+        for (int tx = -2; tx <= 2; ++tx) {
+          const int ux = qx + tx, uy = qy + ty;
+          if (ux < 0 || ux >= Wi || uy < 0 || uy >= Hi) continue;
+          const size_t u = (size_t)uy * Wi + ux;
+          if (!S[u]) continue;
+          const T du = (T)depth[(size_t)level_sample(uy, level, H) * W + level_sample(ux, level, W)];
+          if (!(std::fabs(du - d) <= rel * d)) continue;
+          const T w = B[ty + 2] * B[tx + 2];
+          for (int ch = 0; ch < C; ++ch) num[ch] = num[ch] + w * c[u * C + ch];
+          den = den + w;
+        }
+      }
+      for (int ch = 0; ch < C; ++ch) {
+        T out = num[ch] / den;
+        if (p.store_half) out = (T)round_to_half((float)out);
+        b[q * C + ch] = out;
+      }
+    }
+  }
+}
+
 // Naive full-resolution rendering (the comparison of Sec. 5): the effect at every pixel.
 template <typename T> void shade_full(const orc_params& p, const Inputs& in, T* out) {
   const int W = p.width, H = p.height, C = channels(p);
@@ -655,6 +712,57 @@ void merge(const orc_params& p, T* const* a, uint8_t* const* S, T* const* c, T* 
       for (int ch = 0; ch < C; ++ch) out[((size_t)y * W + x) * C + ch] = cp[ch];
     }
   }
+}
+
+// Step-wise blending (Sec. 3.3), the alternative to the direct upsampling above: the
+// sub-images are merged from the coarsest upwards, each finer enabled level i blended,
+// at its own resolution, with the composite of the levels below it scaled up to level
+// i's grid; the full-resolution image is the composite at level 0.  Starting from
+// comp = c_{L-1} (the coarsest level is rendered everywhere), for every finer level i
+// (descending; disabled levels above 0 are skipped, so a step may span several
+// octaves) and every texel q of level i:
+//   u = (2^i q + o_i - o_j) / 2^j   (q's position in texels of the previous level j)
+//   up = bilinear interpolation of comp at u (taps floor(u), floor(u) + 1 clamped; comp
+//        is defined everywhere, so no renormalisation)
+//   comp_i(q) = c_i(q) * alpha + up * (1 - alpha),  alpha = min(w_i a_i(q), 1),
+//               where S_i(q) = 1 and alpha > 0;  comp_i(q) = up elsewhere.
+// Level 0 takes part as any other level when enabled, and is the last step either way.
+template <typename T>
+void merge_stepwise(const orc_params& p, T* const* a, uint8_t* const* S, T* const* c, T* out) {
+  const int W = p.width, H = p.height, L = p.num_levels, C = channels(p);
+  int j = L - 1;
+  std::vector<T> comp(c[j], c[j] + (size_t)level_dim(W, j) * level_dim(H, j) * C);
+  for (int i = L - 2; i >= 0; --i) {
+    if (i > 0 && !p.enabled[i]) continue;
+    const int Wi = level_dim(W, i), Hi = level_dim(H, i), Wj = level_dim(W, j), Hj = level_dim(H, j);
+    const T scale = (T)(1 << j);
+    std::vector<T> next((size_t)Wi * Hi * C);
+#pragma omp parallel for schedule(static)
+    for (int qy = 0; qy < Hi; ++qy) {
+      for (int qx = 0; qx < Wi; ++qx) {
+        T ux = (T)((qx << i) + level_origin(i) - level_origin(j)) / scale;
+        T uy = (T)((qy << i) + level_origin(i) - level_origin(j)) / scale;
+        int x0 = (int)std::floor(ux), y0 = (int)std::floor(uy);
+        T fx = ux - (T)x0, fy = uy - (T)y0;
+        int xs[2] = {std::min(std::max(x0, 0), Wj - 1), std::min(std::max(x0 + 1, 0), Wj - 1)};
+        int ys[2] = {std::min(std::max(y0, 0), Hj - 1), std::min(std::max(y0 + 1, 0), Hj - 1)};
+        T w[4] = {(T(1) - fx) * (T(1) - fy), fx * (T(1) - fy), (T(1) - fx) * fy, fx * fy};
+        size_t idx[4] = {(size_t)ys[0] * Wj + xs[0], (size_t)ys[0] * Wj + xs[1], (size_t)ys[1] * Wj + xs[0],
+                         (size_t)ys[1] * Wj + xs[1]};
+        const size_t q = (size_t)qy * Wi + qx;
+        T up[3] = {T(0), T(0), T(0)};
+        for (int k = 0; k < 4; ++k)
+          for (int ch = 0; ch < C; ++ch) up[ch] = up[ch] + w[k] * comp[idx[k] * C + ch];
+        T alpha = T(0);
+        if (p.enabled[i] && S[i][q]) alpha = std::min((T)p.weight[i] * a[i][q], T(1));
+        for (int ch = 0; ch < C; ++ch)
+          next[q * C + ch] = alpha > T(0) ? c[i][q * C + ch] * alpha + up[ch] * (T(1) - alpha) : up[ch];
+      }
+    }
+    comp.swap(next);
+    j = i;
+  }
+  std::copy(comp.begin(), comp.end(), out);
 }
 
 Inputs make_inputs(const float* depth, const float* normal, const float* color, const float* smap) {
@@ -735,6 +843,13 @@ int orc_gauss_weights_f64(double sigma2, double* g) { return gauss_weights<doubl
   }                                                                                                          \
   void orc_merge_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) {          \
     merge<T>(*p, a, S, c, out);                                                                              \
+  }                                                                                                          \
+  void orc_merge_stepwise_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) { \
+    merge_stepwise<T>(*p, a, S, c, out);                                                                     \
+  }                                                                                                          \
+  void orc_blur_level_##SUF(const orc_params* p, const float* depth, int level, const uint8_t* S,           \
+                            const T* c, T* b) {                                                              \
+    blur_level<T>(*p, depth, level, S, c, b);                                                                \
   }
 
 ORC_STAGES(f32, float)

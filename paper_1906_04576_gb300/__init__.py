@@ -60,6 +60,7 @@ class mrr_config(ctypes.Structure):
         ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float),
         ("max_width", ctypes.c_int), ("max_height", ctypes.c_int),
         ("lanes_per_texel", ctypes.c_int), ("lanes_per_pixel", ctypes.c_int), ("no_graph", ctypes.c_int),
+        ("blur", I4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
     ]
 
 
@@ -148,6 +149,8 @@ _lib.mrr_edges.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_masks.argtypes = [_vp, _vp, ctypes.POINTER(mrr_levels), _vp]
 _lib.mrr_shade_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp]
 _lib.mrr_upsample_merge.argtypes = [_vp, ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp, _vp]
+_lib.mrr_blur_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp,
+                                _vp]
 _lib.mrr_shade_levels.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp]
 _lib.mrr_masks_static.argtypes = [ctypes.POINTER(mrr_config), _vp, ctypes.POINTER(mrr_levels), _vp]
 _lib.mrr_masks_static.restype = ctypes.c_int
@@ -159,7 +162,7 @@ _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 for _fn in ("mrr_level_dims", "mrr_create", "mrr_edges", "mrr_masks", "mrr_shade_level", "mrr_shade_levels",
-            "mrr_upsample_merge",
+            "mrr_upsample_merge", "mrr_blur_level",
             "mrr_render", "mrr_render_full", "mrr_render_host"):
     getattr(_lib, _fn).restype = ctypes.c_int
 
@@ -262,6 +265,11 @@ def make_config(cfg: dict) -> tuple[mrr_config, list]:
     c.lanes_per_texel = int(cfg.get("lanes_per_texel", 0))
     c.lanes_per_pixel = int(cfg.get("lanes_per_pixel", 0))
     c.no_graph = int(cfg.get("no_graph", 0))
+    blur = cfg.get("blur", [0, 0, 0, 0])
+    for i in range(4):
+        c.blur[i] = int(blur[i])
+    c.blur_depth_rel = cfg.get("blur_depth_rel", 0.05)
+    c.merge_mode = int(cfg.get("merge_mode", 0))
     return c, keep
 
 
@@ -395,6 +403,13 @@ def mrr_shade_level(ctx: Context, level: int, frame: DeviceFrame, levels: Levels
     g, lv = frame.struct(), levels.struct()
     _check(ctx, _lib.mrr_shade_level(ctx.handle, level, ctypes.byref(g), ctypes.byref(lv), _ptr(c),
                                      _stream(stream)))
+
+
+def mrr_blur_level(ctx: Context, level: int, frame: DeviceFrame, levels: Levels, c: torch.Tensor, b: torch.Tensor,
+                   stream=None) -> None:
+    g, lv = frame.struct(), levels.struct()
+    _check(ctx, _lib.mrr_blur_level(ctx.handle, level, ctypes.byref(g), ctypes.byref(lv), _ptr(c), _ptr(b),
+                                    _stream(stream)))
 
 
 def mrr_shade_levels(ctx: Context, frame: DeviceFrame, levels: Levels, c_list: list, stream=None) -> None:
@@ -655,6 +670,7 @@ def default_config(effect: str, num_levels: int, max_width: int, max_height: int
             enabled[i] = 1
     cfg = dict(effect=effect, precision="fp32", num_levels=num_levels, sigma2=sigma2, weight=weight,
                enabled=enabled, depth_rel=0.05, normal_cos=0.9, force_level0=0, radius=0.5, ao_bias=0.0125,
-               gi_min_dist2=0.01, light_size=0.5, shadow_bias=0.03, max_width=max_width, max_height=max_height)
+               gi_min_dist2=0.01, light_size=0.5, shadow_bias=0.03, max_width=max_width, max_height=max_height,
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0)
     cfg.update(kw)
     return cfg

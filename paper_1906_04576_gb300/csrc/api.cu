@@ -2,6 +2,7 @@
 // constants of each stage and the launches.  No exception crosses the ABI; every
 // failure is a status code plus a message kept on the context.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -30,6 +31,8 @@ struct mrr_ctx {
   uint8_t* stencil[MRR_MAX_LEVELS] = {};
   uint32_t* worklist[MRR_MAX_LEVELS] = {};
   void* cbuf[MRR_MAX_LEVELS] = {};
+  void* bbuf[MRR_MAX_LEVELS] = {};  // blurred sub-images of the levels cfg.blur names
+  float* comp[MRR_MAX_LEVELS] = {};  // step-wise blending's composites of levels 1 .. L-2
   uint32_t* counts = nullptr;
   uint32_t* chunk_counts = nullptr;
   size_t chunk_cap = 0;
@@ -324,34 +327,76 @@ mrr_levels pool_levels(mrr_ctx* ctx, int W, int H) {
   return lv;
 }
 
+// The step-wise blending of Sec. 3.3: one chain launch per finer enabled level (and a
+// last one at level 0), intermediate composites in the context's pools.  With
+// compact_level0, level 0's blend is left to the caller (level 0's list).
+mrr_status chain_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
+                      bool compact_level0) {
+  const mrr_config& cf = ctx->cfg;
+  int j = cf.num_levels - 1;
+  const void* src = c[j];
+  bool src_sub = true;
+  for (int i = cf.num_levels - 2; i >= 0; --i) {
+    if (i > 0 && !cf.enabled[i]) continue;
+    ChainParams cp;
+    std::memset(&cp, 0, sizeof cp);
+    cp.C = channels(cf);
+    cp.half_store = cf.precision == MRR_FP16;
+    cp.i = i;
+    cp.j = j;
+    cp.Wi = lv->width[i];
+    cp.Hi = lv->height[i];
+    cp.Wj = lv->width[j];
+    cp.Hj = lv->height[j];
+    cp.weight = cf.weight[i];
+    cp.blend = cf.enabled[i] && !(i == 0 && compact_level0);
+    cp.alpha = lv->alpha[i];
+    cp.stencil = lv->stencil[i];
+    cp.c = c[i];
+    cp.src = src;
+    cp.src_sub = src_sub;
+    cp.dst = i == 0 ? out : ctx->comp[i];
+    MRR_CUDA(ctx, launch_chain(cp, s));
+    src = cp.dst;
+    src_sub = false;
+    j = i;
+  }
+  return MRR_OK;
+}
+
 mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
                       bool compact_level0 = false) {
   const mrr_config& cf = ctx->cfg;
-  MergeParams mp;
-  std::memset(&mp, 0, sizeof mp);
-  mp.W = lv->width[0];
-  mp.H = lv->height[0];
-  mp.L = cf.num_levels;
-  mp.C = channels(cf);
-  mp.half_store = cf.precision == MRR_FP16;
-  for (int i = 0; i < cf.num_levels; ++i) {
-    mp.enabled[i] = cf.enabled[i];
-    mp.Wi[i] = lv->width[i];
-    mp.Hi[i] = lv->height[i];
-    mp.weight[i] = cf.weight[i];
-    mp.alpha[i] = lv->alpha[i];
-    mp.stencil[i] = lv->stencil[i];
-    mp.c[i] = c[i];
+  if (cf.merge_mode == 1 && cf.num_levels > 1) {
+    mrr_status st = chain_impl(ctx, lv, c, out, s, compact_level0);
+    if (st != MRR_OK) return st;
+  } else {
+    MergeParams mp;
+    std::memset(&mp, 0, sizeof mp);
+    mp.W = lv->width[0];
+    mp.H = lv->height[0];
+    mp.L = cf.num_levels;
+    mp.C = channels(cf);
+    mp.half_store = cf.precision == MRR_FP16;
+    for (int i = 0; i < cf.num_levels; ++i) {
+      mp.enabled[i] = cf.enabled[i];
+      mp.Wi[i] = lv->width[i];
+      mp.Hi[i] = lv->height[i];
+      mp.weight[i] = cf.weight[i];
+      mp.alpha[i] = lv->alpha[i];
+      mp.stencil[i] = lv->stencil[i];
+      mp.c[i] = c[i];
+    }
+    if (compact_level0) mp.enabled[0] = 0;  // blended afterwards from level 0's list
+    MRR_CUDA(ctx, launch_merge(mp, out, s));
   }
-  if (compact_level0) mp.enabled[0] = 0;  // blended afterwards from level 0's list
-  MRR_CUDA(ctx, launch_merge(mp, out, s));
   if (compact_level0 && cf.enabled[0]) {
     Blend0Params bp;
     std::memset(&bp, 0, sizeof bp);
-    bp.W = mp.W;
-    bp.H = mp.H;
-    bp.C = mp.C;
-    bp.half_store = mp.half_store;
+    bp.W = lv->width[0];
+    bp.H = lv->height[0];
+    bp.C = channels(cf);
+    bp.half_store = cf.precision == MRR_FP16;
     bp.weight = cf.weight[0];
     bp.list = ctx->worklist[0];
     bp.count = ctx->counts;
@@ -359,6 +404,44 @@ mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
     bp.c0c = ctx->cbuf[0];
     MRR_CUDA(ctx, launch_blend0(bp, out, s));
   }
+  return MRR_OK;
+}
+
+// Blur parameters for frame g with levels lv; slots are added by the caller.
+BlurParams blur_params(const mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv) {
+  BlurParams bp;
+  std::memset(&bp, 0, sizeof bp);
+  bp.W = g->width;
+  bp.H = g->height;
+  bp.C = channels(ctx->cfg);
+  bp.half_store = ctx->cfg.precision == MRR_FP16;
+  bp.rel = ctx->cfg.blur_depth_rel;
+  bp.depth = g->depth;
+  return bp;
+}
+
+void add_blur_slot(BlurParams& bp, const mrr_levels* lv, int level, const void* c, void* b) {
+  const int k = bp.nlev++;
+  bp.level[k] = level;
+  bp.Wi[k] = lv->width[level];
+  bp.Hi[k] = lv->height[level];
+  bp.tile_begin[k + 1] = bp.tile_begin[k] + blur_tiles(bp.Wi[k], bp.Hi[k]);
+  bp.stencil[k] = lv->stencil[level];
+  bp.c[k] = c;
+  bp.b[k] = b;
+}
+
+// Sec. 4.1: blur the pool sub-images of the levels cfg.blur names (one launch); c_merge[i]
+// receives the sub-image the blend reads for level i (blurred or not).
+mrr_status blur_pools(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv, void** c_merge, cudaStream_t s) {
+  BlurParams bp = blur_params(ctx, g, lv);
+  for (int i = 0; i < MRR_MAX_LEVELS; ++i) c_merge[i] = ctx->cbuf[i];
+  for (int i = 1; i < ctx->cfg.num_levels; ++i) {
+    if (!ctx->cfg.blur[i]) continue;
+    add_blur_slot(bp, lv, i, ctx->cbuf[i], ctx->bbuf[i]);
+    c_merge[i] = ctx->bbuf[i];
+  }
+  if (bp.nlev) MRR_CUDA(ctx, launch_blur(bp, s));
   return MRR_OK;
 }
 
@@ -453,8 +536,9 @@ mrr_status frame_masks(mrr_ctx* ctx, const mrr_gbuffer* g, mrr_levels* lv, cudaS
 
 // With at least two levels: edges (also clearing the per-level counts; the edge image
 // bit-packed), masks that also write the work lists and level 0's a_0 list-aligned, one
-// shading launch over every level (level 0's c_0 list-aligned too), the merge of the
-// levels above 0, and level 0 blended in over its list.  Level 0's full-resolution a_0,
+// shading launch over every level (level 0's c_0 list-aligned too), the blur of the
+// levels cfg.blur names (if any), the merge of the levels above 0, and level 0 blended
+// in over its list.  Level 0's full-resolution a_0,
 // S_0 and c_0 never reach memory, and no compaction launch is needed.
 mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const mrr_config& c = ctx->cfg;
@@ -479,7 +563,10 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   }
   sl.counts = ctx->counts;
   MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
-  return merge_impl(ctx, &lv, ctx->cbuf, out, s, true);
+  void* cm[MRR_MAX_LEVELS];
+  st = blur_pools(ctx, g, &lv, cm, s);
+  if (st != MRR_OK) return st;
+  return merge_impl(ctx, &lv, cm, out, s, true);
 }
 
 // One level only (level 0 is the coarsest): edges, masks, compaction, shading, merge.
@@ -520,6 +607,8 @@ void free_pools(mrr_ctx* ctx) {
     cudaFree(ctx->stencil[i]);
     cudaFree(ctx->worklist[i]);
     cudaFree(ctx->cbuf[i]);
+    cudaFree(ctx->bbuf[i]);
+    cudaFree(ctx->comp[i]);
   }
   cudaFree(ctx->counts);
   cudaFree(ctx->chunk_counts);
@@ -549,6 +638,9 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
       MRR_CUDA(ctx, cudaMalloc(&ctx->worklist[i], n * sizeof(uint32_t)));
       MRR_CUDA(ctx, cudaMalloc(&ctx->cbuf[i], n * cbytes(c)));
     }
+    if (c.blur[i]) MRR_CUDA(ctx, cudaMalloc(&ctx->bbuf[i], n * cbytes(c)));
+    if (c.merge_mode == 1 && i >= 1 && i < c.num_levels - 1 && c.enabled[i])
+      MRR_CUDA(ctx, cudaMalloc(&ctx->comp[i], n * (c.effect == MRR_SSGI ? 16 : 4)));
     chunks += (n + COMPACT_CHUNK - 1) / COMPACT_CHUNK;
   }
   // level 0's horizontal blur for every (2R+1)-bit window, summed exactly as the
@@ -603,6 +695,12 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
     if (!(c.weight[i] >= 0.f)) return MRR_EINVAL;
   }
   if (c.max_width < 1 || c.max_height < 1 || c.max_width > MAX_DIM || c.max_height > MAX_DIM) return MRR_EINVAL;
+  for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
+    if (c.blur[i] != 0 && c.blur[i] != 1) return MRR_EINVAL;
+    if (c.blur[i] && (i == 0 || i >= c.num_levels || !c.enabled[i])) return MRR_EINVAL;
+  }
+  if (!(c.blur_depth_rel >= 0.f) || !(c.blur_depth_rel <= FLT_MAX)) return MRR_EINVAL;
+  if (c.merge_mode != 0 && c.merge_mode != 1) return MRR_EINVAL;
   for (int v : {c.lanes_per_texel, c.lanes_per_pixel})
     if (v != 0 && v != 1 && v != 2 && v != 4) return MRR_EINVAL;
   if (c.effect != MRR_SSM) {
@@ -759,6 +857,28 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
   return MRR_OK;
 }
 
+mrr_status mrr_blur_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const mrr_levels* lv,
+                          const void* c_level_dev, void* b_level_dev, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  st = check_levels(ctx, lv, false);
+  if (st != MRR_OK) return st;
+  if (level < 1 || level >= ctx->cfg.num_levels || !ctx->cfg.enabled[level])
+    return fail(ctx, MRR_EINVAL, "level %d is not an enabled level above 0", level);
+  if (lv->width[0] != g->width || lv->height[0] != g->height)
+    return fail(ctx, MRR_EINVAL, "levels are for %dx%d, frame is %dx%d", lv->width[0], lv->height[0], g->width,
+                g->height);
+  if (!c_level_dev || !b_level_dev || !aligned(c_level_dev, cbytes(ctx->cfg)) ||
+      !aligned(b_level_dev, cbytes(ctx->cfg)))
+    return fail(ctx, MRR_EINVAL, "c_level_dev / b_level_dev is NULL or misaligned");
+  if (c_level_dev == b_level_dev) return fail(ctx, MRR_EINVAL, "the blur cannot run in place");
+  BlurParams bp = blur_params(ctx, g, lv);
+  add_blur_slot(bp, lv, level, c_level_dev, b_level_dev);
+  MRR_CUDA(ctx, launch_blur(bp, (cudaStream_t)stream));
+  return MRR_OK;
+}
+
 uint64_t mrr_kernel_launches(void) { return mrr::launch_counter().load(); }
 
 mrr_status mrr_batch_create(mrr_batch** out) {
@@ -860,7 +980,9 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     return batch_fail(b, MRR_ECUDA, "batched shading launch");
   if (outs) {
     for (int k = 0; k < n; ++k) {
-      mrr_status st = merge_impl(ctxs[k], &lv[k], ctxs[k]->cbuf, outs[k], s, framed[k]);
+      void* cm[MRR_MAX_LEVELS];
+      mrr_status st = blur_pools(ctxs[k], &frames[k], &lv[k], cm, s);
+      if (st == MRR_OK) st = merge_impl(ctxs[k], &lv[k], cm, outs[k], s, framed[k]);
       if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
     }
   }
@@ -1132,6 +1254,9 @@ mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c
     if (ctx->cfg.enabled[i] && (!c_levels_dev[i] || !aligned(c_levels_dev[i], cbytes(ctx->cfg))))
       return fail(ctx, MRR_EINVAL, "sub-image %d is NULL or misaligned", i);
   if (!aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4)) return fail(ctx, MRR_EINVAL, "out_dev misaligned");
+  if (ctx->cfg.merge_mode == 1 && !fits_pools(ctx, lv->width[0], lv->height[0]))
+    return fail(ctx, MRR_EINVAL, "step-wise blending: frame %dx%d exceeds the context's max size", lv->width[0],
+                lv->height[0]);
   return merge_impl(ctx, lv, c_levels_dev, out_dev, (cudaStream_t)stream);
 }
 

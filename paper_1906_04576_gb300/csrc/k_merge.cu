@@ -15,6 +15,9 @@
 // plainly, c_i over rendered taps with renormalised weights, alpha = min(w_i a_i, 1) and
 // c' = c_i alpha + c' (1 - alpha); the coarsest level is taken as is.  The renormalising
 // division is skipped when the weight sum is exactly 1 (x / 1 = x).
+//
+// chain_kernel: the step-wise reading of Sec. 3.3 instead -- one launch per step, each
+// level's composite computed at its own resolution from the previous one.
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -374,6 +377,104 @@ __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __re
   }
 }
 
+// One step of the step-wise blending (Sec. 3.3): level i's composite from the previous
+// composite (level j > i).  Texel q of level i sits at u = (2^i q + o_i - o_j) / 2^j in
+// level-j texels, whose floor and fraction are exactly n >> j and (n & (2^j - 1)) 2^-j for
+// the integer n = 2^i q + o_i - o_j (arithmetic shift: the floor of negative n too); the
+// four taps are clamped to level j.  The previous composite is defined at every texel,
+// so the interpolation is plain.  Then, where the level blends (BLEND) and S_i(q) = 1,
+// alpha = min(w_i a_i(q), 1) and, if alpha > 0, comp = c_i alpha + up (1 - alpha).
+// SRC_SUB: the previous composite is the coarsest sub-image itself (storage type CT);
+// otherwise float / float4 as written here.
+constexpr int CH_TX = 32, CH_TY = 8, CH_R = 4;  // chain CTA: 32 x 8 threads, 4 rows per thread
+
+template <typename CT, int C, bool SRC_SUB>
+__global__ void __launch_bounds__(CH_TX* CH_TY) chain_kernel(ChainParams p) {
+  const int qx = blockIdx.x * CH_TX + threadIdx.x;
+  if (qx >= p.Wi) return;
+  const int oi = p.i == 0 ? 0 : 1 << (p.i - 1), oj = 1 << (p.j - 1);
+  const int mask = (1 << p.j) - 1;
+  const float inv = __int_as_float((127 - p.j) << 23);  // 2^-j
+  // the column's horizontal taps and weights, shared by its rows
+  const int nx = qx * (1 << p.i) + oi - oj;
+  const int x0 = nx >> p.j;
+  const float fx = (float)(nx & mask) * inv;
+  const int xa = min(max(x0, 0), p.Wj - 1), xb = min(max(x0 + 1, 0), p.Wj - 1);
+  const float gx = 1.0f - fx;
+  const int qy0 = blockIdx.y * CH_TY * CH_R + threadIdx.y;
+  // every load of the thread's rows first (rows past the level read its last row)
+  float3 t[CH_R][4];
+  float av[CH_R];
+  uint8_t sv[CH_R];
+#pragma unroll
+  for (int r = 0; r < CH_R; ++r) {
+    const int qy = min(qy0 + r * CH_TY, p.Hi - 1);
+    const int ny = qy * (1 << p.i) + oi - oj;
+    const int y0 = ny >> p.j;
+    const int ya = min(max(y0, 0), p.Hj - 1), yb = min(max(y0 + 1, 0), p.Hj - 1);
+    const uint32_t idx[4] = {(uint32_t)(ya * p.Wj + xa), (uint32_t)(ya * p.Wj + xb), (uint32_t)(yb * p.Wj + xa),
+                             (uint32_t)(yb * p.Wj + xb)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[r][k] = SRC_SUB ? load_c<CT>(p.src, idx[k], C) : load_c<float>(p.src, idx[k], C);
+    const uint32_t q = (uint32_t)(qy * p.Wi + qx);
+    sv[r] = p.blend ? __ldg(p.stencil + q) : (uint8_t)0;
+    av[r] = p.blend ? __ldg(p.alpha + q) : 0.0f;
+  }
+  // level i's own values where it is blended in (issued together)
+  float alpha[CH_R];
+  float3 v[CH_R];
+#pragma unroll
+  for (int r = 0; r < CH_R; ++r) {
+    const float wa = p.weight * av[r];
+    alpha[r] = sv[r] ? ((1.0f < wa) ? 1.0f : wa) : 0.0f;
+    v[r] = make_float3(0.0f, 0.0f, 0.0f);
+    if (alpha[r] > 0.0f) {
+      const int qy = min(qy0 + r * CH_TY, p.Hi - 1);
+      v[r] = load_c<CT>(p.c, (uint32_t)(qy * p.Wi + qx), C);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < CH_R; ++r) {
+    const int qy = qy0 + r * CH_TY;
+    if (qy >= p.Hi) break;
+    const int ny = qy * (1 << p.i) + oi - oj;
+    const float fy = (float)(ny & mask) * inv;
+    const float gy = 1.0f - fy;
+    const float w[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u0 = u0 + w[k] * t[r][k].x;
+      if (C == 4) {
+        u1 = u1 + w[k] * t[r][k].y;
+        u2 = u2 + w[k] * t[r][k].z;
+      }
+    }
+    if (alpha[r] > 0.0f) {
+      const float om = 1.0f - alpha[r];
+      u0 = v[r].x * alpha[r] + u0 * om;
+      if (C == 4) {
+        u1 = v[r].y * alpha[r] + u1 * om;
+        u2 = v[r].z * alpha[r] + u2 * om;
+      }
+    }
+    const uint32_t q = (uint32_t)(qy * p.Wi + qx);
+    if (C == 4)
+      reinterpret_cast<float4*>(p.dst)[q] = make_float4(u0, u1, u2, 0.0f);
+    else
+      p.dst[q] = u0;
+  }
+}
+
+template <typename CT, int C>
+void launch_chain_t(const ChainParams& p, cudaStream_t s) {
+  dim3 grid((p.Wi + CH_TX - 1) / CH_TX, (p.Hi + CH_TY * CH_R - 1) / (CH_TY * CH_R)), block(CH_TX, CH_TY);
+  if (p.src_sub)
+    chain_kernel<CT, C, true><<<grid, block, 0, s>>>(p);
+  else
+    chain_kernel<CT, C, false><<<grid, block, 0, s>>>(p);
+}
+
 template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
   dim3 grid((p.W + MTX - 1) / MTX, (p.H + MTY - 1) / MTY);
@@ -406,6 +507,18 @@ cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s) {
   } else {
     if (p.half_store) blend0_kernel<__half, 1><<<grid, 256, 0, s>>>(p, out);
     else blend0_kernel<float, 1><<<grid, 256, 0, s>>>(p, out);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain(const ChainParams& p, cudaStream_t s) {
+  if (p.C == 4) {
+    if (p.half_store) launch_chain_t<__half, 4>(p, s);
+    else launch_chain_t<float, 4>(p, s);
+  } else {
+    if (p.half_store) launch_chain_t<__half, 1>(p, s);
+    else launch_chain_t<float, 1>(p, s);
   }
   count_launches(1);
   return cudaGetLastError();

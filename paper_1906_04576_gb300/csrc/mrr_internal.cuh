@@ -152,6 +152,22 @@ struct MergeParams {
   const void* c[MRR_MAX_LEVELS];
 };
 
+// One step of the step-wise blending (Sec. 3.3, k_merge.cu): level i's composite dst
+// ([H_i][W_i] float, float4 when C == 4) from the composite src of level j > i.
+struct ChainParams {
+  int C, half_store;
+  int i, j;
+  int Wi, Hi, Wj, Hj;
+  float weight;            // w_i
+  int blend;               // blend c_i in (level i enabled and its planes given)
+  const float* alpha;      // a_i
+  const uint8_t* stencil;  // S_i
+  const void* c;           // c_i (sub-image storage type)
+  const void* src;         // composite of level j, or the coarsest sub-image when src_sub
+  int src_sub;
+  float* dst;
+};
+
 // Level 0's part of Eq. (1) over level 0's work list, after the coarser levels are merged
 // into `out`: entry k (pixel list[k]) has a_0 = a0c[k] and c_0 at position k of c0c.
 struct Blend0Params {
@@ -161,6 +177,22 @@ struct Blend0Params {
   const uint32_t* count;  // device: entries in the list
   const float* a0c;
   const void* c0c;
+};
+
+// Bilateral blur of one or more levels' sub-images (k_blur.cu): slot k blurs every
+// stencil texel of level `level[k]` from c[k] into b[k] (dense [H_i][W_i] sub-images);
+// its tiles are blocks tile_begin[k] .. tile_begin[k + 1] - 1 of the launch.
+struct BlurParams {
+  int W, H, C, half_store;
+  float rel;               // depth test: |d' - d| <= rel * d
+  const float* depth;      // full-resolution depth
+  int nlev;
+  int level[MRR_MAX_LEVELS];
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  int tile_begin[MRR_MAX_LEVELS + 1];
+  const uint8_t* stencil[MRR_MAX_LEVELS];
+  const void* c[MRR_MAX_LEVELS];
+  void* b[MRR_MAX_LEVELS];
 };
 
 // ---- launchers (return cudaGetLastError() of the launch)
@@ -177,10 +209,13 @@ cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 // reciprocal of x or of -x differs from IEEE division
 cudaError_t launch_check_reciprocal(uint32_t first, uint32_t last, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s);
+cudaError_t launch_chain(const ChainParams& p, cudaStream_t s);
+cudaError_t launch_blur(const BlurParams& p, cudaStream_t s);
 
 void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)
 int shade_grid_blocks();  // grid multiplier base of the work-list kernel (grid = multiple of its resident CTAs)
 int batch_grid_blocks();  // resident CTAs of the batched shading kernel
+int blur_tiles(int Wi, int Hi);  // blur tiles of a W_i x H_i level
 cudaError_t launch_shade_batch(const BatchItem* items_dev, int nitems, uint32_t* queue_head, int chunk, int grid,
                                cudaStream_t s);
 

@@ -206,6 +206,16 @@ WORKLOADS = {
                          samples=64, radius=0.5, levels=4),
     "ssao64_4k": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
                       samples=64, radius=0.5, levels=4),
+    # the same two with the bilateral blur of levels 1-3 (Sec. 4.1)
+    "ssao64_1080p_blur": dict(effect="ssao", width=1920, height=1080, n_boxes=64, n_spheres=16,
+                              samples=64, radius=0.5, levels=4, blur=(0, 1, 1, 1)),
+    "ssao64_4k_blur": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
+                           samples=64, radius=0.5, levels=4, blur=(0, 1, 1, 1)),
+    # the same two with the step-wise blending of Sec. 3.3
+    "ssao64_1080p_step": dict(effect="ssao", width=1920, height=1080, n_boxes=64, n_spheres=16,
+                              samples=64, radius=0.5, levels=4, merge_mode=1),
+    "ssao64_4k_step": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
+                           samples=64, radius=0.5, levels=4, merge_mode=1),
     # soft shadows, 32 blocker + 64 PCF taps, 2048^2 shadow map, 4 levels, 2560x1440
     "ssm_1440p": dict(effect="ssm", width=2560, height=1440, n_boxes=64, n_spheres=16,
                       blocker_samples=32, pcf_samples=64, shadow_size=2048, levels=4),

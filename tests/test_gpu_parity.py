@@ -68,6 +68,12 @@ def run_staged(mrr, ctx, dev, W, H, L):
     for i in range(L):
         if ctx.config["enabled"][i]:
             mrr.mrr_shade_level(ctx, i, dev, levels, subs[i])
+    blur = ctx.config.get("blur", [0, 0, 0, 0])
+    for i in range(L):
+        if blur[i]:                       # Sec. 4.1 blur into a fresh sub-image
+            b = torch.full_like(subs[i], float("nan"))
+            mrr.mrr_blur_level(ctx, i, dev, levels, subs[i], b)
+            subs[i] = b
     mrr.mrr_upsample_merge(ctx, levels, subs, out)
     torch.cuda.synchronize()
     return edges, levels, subs, out

@@ -518,6 +518,229 @@ def test_masked_bilinear_ignores_unrendered_taps():
     assert np.all(out[:, 8:] == 0.75)
 
 
+# ----------------------------------------------------------------- step-wise blending (Sec. 3.3)
+
+def _stepwise_cfg(levels, **kw):
+    return cfg_for("ssao", levels, merge_mode=1, **kw)
+
+
+def test_stepwise_constant_subimages_survive():
+    rng = np.random.default_rng(8)
+    H, W, L = 45, 67, 4
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    cfg = _stepwise_cfg(L)
+    E = (rng.random((H, W)) < 0.02).astype(np.uint8)
+    a, S, _ = orc.masks(fr, cfg, E)
+    for K in (0.3, 0.7779, 1.0):
+        c = _levels_like(H, W, L, K)
+        for i in range(L):
+            c[i][S[i] == 0] = np.nan          # unrendered texels are never read
+        for prec in ("f32", "f64"):
+            out = orc.merge(fr, cfg, a, S, c, prec)
+            assert np.all(np.isfinite(out))
+            assert np.allclose(out, K, rtol=4e-7, atol=0)
+
+
+@pytest.mark.parametrize("enabled", [[1, 1, 1, 0], [1, 0, 1, 1]])
+def test_stepwise_chain_reproduces_linear_ramps(enabled):
+    """Only the coarsest level visible (every other alpha 0): c(Q) = x of Q's sample pixel
+    at the coarsest level is carried through each step (2x, or 4x over a disabled level)
+    to c'(p) = p_x away from the clamped borders -- pins every step's origin and scale."""
+    L = 3 if enabled[3] == 0 else 4
+    H, W = 64, 96
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    cfg = _stepwise_cfg(L, enabled=enabled)
+    a = [np.zeros((orc.level_dim(H, i), orc.level_dim(W, i)), np.float64) for i in range(L)]
+    S = [np.zeros_like(x, dtype=np.uint8) for x in a]
+    c = [np.full(x.shape + (1,), np.nan) for x in a]
+    top = L - 1
+    S[top][:] = 1
+    qx = np.arange(orc.level_dim(W, top))
+    c[top][:] = ((qx << top) + (1 << (top - 1))).astype(np.float64)[None, :, None]
+    out = orc.merge(fr, cfg, a, S, c, "f64")[..., 0]
+    m = 1 << (top + 1)
+    assert np.array_equal(out[:, m:W - m], np.broadcast_to(np.arange(m, W - m, dtype=np.float64), (H, W - 2 * m)))
+
+
+def test_stepwise_alpha_saturates_at_level_resolution():
+    """Three levels; level 1 (w = 50) holds one rendered texel Q with a_1 = 0.04 and c = 1,
+    the coarsest level is 0, level 0 is empty.  The chain saturates alpha at Q itself
+    (min(50 * 0.04, 1) = 1, so c'_1(Q) = 1) and then interpolates: the pixel half-way to
+    the next texel reads 1/2.  The direct merge interpolates a first (0.02, saturating
+    to alpha = 1) and reads 1 there."""
+    H, W = 32, 32
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    Q = (6, 5)                                  # (row, column) of level 1
+    a = [np.zeros((H, W)), np.zeros((16, 16)), np.zeros((8, 8))]
+    S = [np.zeros((H, W), np.uint8), np.zeros((16, 16), np.uint8), np.ones((8, 8), np.uint8)]
+    c = [np.full((H, W, 1), np.nan), np.full((16, 16, 1), np.nan), np.zeros((8, 8, 1))]
+    a[1][Q] = 0.04
+    S[1][Q] = 1
+    c[1][Q] = 1.0
+    y, x = 2 * Q[0] + 1, 2 * Q[1] + 2           # level-1 coordinate (Q_row, Q_col + 1/2)
+    step = orc.merge(fr, _stepwise_cfg(3), a, S, c, "f64")[..., 0]
+    direct = orc.merge(fr, cfg_for("ssao", 3), a, S, c, "f64")[..., 0]
+    assert step[y, x - 1] == 1.0 and step[y, x] == 0.5
+    assert direct[y, x - 1] == 1.0 and direct[y, x] == 1.0
+    # in the linear regime (no saturation) the two readings agree
+    a[1][Q] = 0.01
+    step = orc.merge(fr, _stepwise_cfg(3), a, S, c, "f64")[..., 0]
+    direct = orc.merge(fr, cfg_for("ssao", 3), a, S, c, "f64")[..., 0]
+    assert step[y, x] == 0.25 and direct[y, x] == 0.25
+
+
+def test_stepwise_two_levels_is_eq1():
+    H, W = 16, 16
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    cfg = _stepwise_cfg(2, enabled=[1, 1, 0, 0], weight=[4.0, 1.0, 0, 0])
+    A, B = 0.25, 0.75
+    for a0 in (0.0, 0.05, 0.2, 0.3, 1.0):
+        a = [np.full((H, W), a0), np.ones((8, 8))]
+        S = [np.ones((H, W), np.uint8), np.ones((8, 8), np.uint8)]
+        c = [np.full((H, W, 1), A), np.full((8, 8, 1), B)]
+        out = orc.merge(fr, cfg, a, S, c, "f64")
+        alpha = min(4.0 * a0, 1.0)
+        assert np.allclose(out, A * alpha + B * (1 - alpha), rtol=1e-12, atol=1e-12)
+
+
+def test_stepwise_render_error_against_full_resolution_is_small():
+    fr = sg.gbuffer(0, 256, 256, 8, 0)
+    cfg = cfg_for("ssao", 3, samples=16, merge_mode=1)
+    res = orc.render(fr, cfg)
+    full = orc.shade_full(fr, cfg)
+    assert float(np.sqrt(np.mean((res["out"] - full) ** 2))) <= 1e-2
+
+
+# ----------------------------------------------------------------- sub-image blur (Sec. 4.1)
+
+BINOMIAL = np.array([1.0, 4.0, 6.0, 4.0, 1.0])
+
+
+def _blur_frame(depth):
+    H, W = depth.shape
+    return synthetic_frame(depth, flat_normals(H, W))
+
+
+def test_blur_flat_depth_is_normalised_binomial_convolution():
+    """One depth everywhere: the bilateral blur reduces to the normalised convolution
+    conv(c S) / conv(S) with the 5x5 binomial kernel (scipy.ndimage), zero outside."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(11)
+    H, W, level = 38, 54, 1
+    fr = _blur_frame(np.full((H, W), 2.0))
+    cfg = cfg_for("ssao", 4)
+    Hi, Wi = orc.level_dim(H, level), orc.level_dim(W, level)
+    K = np.outer(BINOMIAL, BINOMIAL)
+    for density in (1.0, 0.6):
+        S = (rng.random((Hi, Wi)) < density).astype(np.uint8)
+        c = rng.random((Hi, Wi, 1))
+        c[S == 0] = np.nan
+        b = orc.blur_level(fr, cfg, level, S, c, "f64")
+        cs = np.where(S == 1, c[..., 0], 0.0)
+        want = (ndimage.convolve(cs, K, mode="constant", cval=0.0)
+                / ndimage.convolve(S.astype(np.float64), K, mode="constant", cval=0.0))
+        on = S == 1
+        assert np.allclose(b[..., 0][on], want[on], rtol=1e-13, atol=1e-15)
+        assert np.all(np.isnan(b[..., 0][~on]))          # unrendered texels are left alone
+
+
+def test_blur_reproduces_linear_ramps_and_constants():
+    """The binomial kernel is symmetric with unit-normalised weights: a constant stays
+    exact everywhere and a linear ramp is reproduced two texels from the borders."""
+    H, W, level = 40, 48, 2
+    fr = _blur_frame(np.full((H, W), 4.0))
+    cfg = cfg_for("ssao", 4)
+    Hi, Wi = orc.level_dim(H, level), orc.level_dim(W, level)
+    S = np.ones((Hi, Wi), np.uint8)
+    for prec in ("f32", "f64"):
+        b = orc.blur_level(fr, cfg, level, S, np.full((Hi, Wi, 1), 0.625), prec)
+        assert np.all(b == 0.625)
+    qy, qx = np.mgrid[0:Hi, 0:Wi]
+    ramp = (0.125 * qx - 0.0625 * qy + 1.0)[..., None]
+    b = orc.blur_level(fr, cfg, level, S, ramp, "f64")
+    assert np.array_equal(b[2:-2, 2:-2], ramp[2:-2, 2:-2])
+
+
+def test_blur_depth_test_is_relative_to_the_centre_texel():
+    """Depth 1 left of column k and 0.952 from k on, blur_depth_rel = 0.05: a texel on the
+    left takes its right neighbours (|0.048| <= 0.05), one on the right refuses its left
+    neighbours (0.048 > 0.0476).  With c = 0 left and 1 right, the texel just left of
+    the step reads (B[3] + B[4]) / 16 = 5/16 and every right texel stays 1."""
+    level, k = 1, 8
+    Hi, Wi = 12, 16
+    H, W = 2 * Hi, 2 * Wi
+    depth = np.ones((H, W))
+    depth[:, 2 * k:] = 0.952
+    fr = _blur_frame(depth)
+    cfg = cfg_for("ssao", 4, blur_depth_rel=0.05)
+    S = np.ones((Hi, Wi), np.uint8)
+    c = np.zeros((Hi, Wi, 1))
+    c[:, k:] = 1.0
+    b = orc.blur_level(fr, cfg, level, S, c, "f64")[..., 0]
+    assert np.all(b[:, k:] == 1.0)
+    assert np.all(b[2:-2, k - 1] == 5.0 / 16.0)
+    assert np.all(b[2:-2, k - 2] == 1.0 / 16.0)
+    assert np.all(b[:, : k - 2] == 0.0)
+    # a tighter test keeps the two sides apart in both directions
+    b = orc.blur_level(fr, cfg_for("ssao", 4, blur_depth_rel=0.04), level, S, c, "f64")[..., 0]
+    assert np.all(b[:, :k] == 0.0) and np.all(b[:, k:] == 1.0)
+
+
+def test_blur_reads_depth_at_the_level_sample_pixels():
+    """Level 2 samples pixel 4q + 2.  Depth is 9 at every other pixel; at the sample
+    pixels it is 1, and 3 from texel column k on.  Read at the sample pixels, the step
+    keeps the two sides apart (c stays 0 | 1); read anywhere else, the depth is flat and
+    the texels beside the step would mix to 5/16 and 11/16."""
+    level, k = 2, 6
+    Hi, Wi = 10, 14
+    H, W = 4 * Hi, 4 * Wi
+    depth = np.full((H, W), 9.0)
+    ys = np.arange(Hi) * 4 + 2
+    xs = np.arange(Wi) * 4 + 2
+    depth[np.ix_(ys, xs)] = np.where(np.arange(Wi)[None, :] < k, 1.0, 3.0)
+    fr = _blur_frame(depth)
+    cfg = cfg_for("ssao", 4, blur_depth_rel=0.05)
+    c = np.zeros((Hi, Wi, 1))
+    c[:, k:] = 1.0
+    b = orc.blur_level(fr, cfg, level, np.ones((Hi, Wi), np.uint8), c, "f64")[..., 0]
+    assert np.all(b[:, :k] == 0.0) and np.all(b[:, k:] == 1.0)
+    flat = orc.blur_level(_blur_frame(np.full((H, W), 9.0)), cfg, level, np.ones((Hi, Wi), np.uint8), c,
+                          "f64")[..., 0]
+    assert np.all(flat[2:-2, k - 1] == 5.0 / 16.0) and np.all(flat[2:-2, k] == 11.0 / 16.0)
+
+
+def test_blur_border_window_is_renormalised():
+    """At the level's corner only the 3 x 3 quarter of the window lies inside: its
+    weights (6 4 1) x (6 4 1) sum to 121, and a unit impulse at the corner reads
+    36 / 121 there.  One texel in, a row or column keeps 4 + 6 + 4 + 1 = 15 of its 16."""
+    level = 1
+    Hi, Wi = 9, 11
+    fr = _blur_frame(np.full((2 * Hi, 2 * Wi), 3.0))
+    cfg = cfg_for("ssao", 4)
+    c = np.zeros((Hi, Wi, 1))
+    c[0, 0] = 1.0
+    b = orc.blur_level(fr, cfg, level, np.ones((Hi, Wi), np.uint8), c, "f64")[..., 0]
+    assert b[0, 0] == 36.0 / 121.0
+    # texel (0, 1): rows 0..2 inside (6 + 4 + 1 = 11), columns -1..3 inside (4+6+4+1 = 15)
+    assert b[0, 1] == 4.0 * 6.0 / (11.0 * 15.0)
+    # texel (1, 1): rows and columns -1..3 inside (15 each); the impulse is at (-1, -1)
+    assert b[1, 1] == 16.0 / 225.0
+
+
+def test_blur_in_render_changes_only_blurred_levels():
+    fr = sg.gbuffer(4, 120, 72, 10, 3)
+    base = cfg_for("ssao", 4, samples=16)
+    res0 = orc.render(fr, base)
+    res1 = orc.render(fr, dict(base, blur=[0, 1, 1, 1]))
+    assert np.array_equal(res0["c"][0], res1["c"][0], equal_nan=True)
+    for i in (1, 2, 3):
+        on = res0["S"][i] == 1
+        assert not np.array_equal(res0["c"][i][on], res1["c"][i][on])
+        assert np.all(np.isfinite(res1["c"][i][on]))
+        assert np.all((res1["c"][i][on] >= 0) & (res1["c"][i][on] <= 1))
+    assert np.all(np.isfinite(res1["out"]))
+
+
 # ----------------------------------------------------------------- whole method
 
 def test_cross_level_point_sample_invariant():
