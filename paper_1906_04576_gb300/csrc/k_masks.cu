@@ -299,6 +299,38 @@ __device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, in
   fill_level<3>(m, sm, x0, y0, m.mode[3]);  // level 3 can only be the coarsest
 }
 
+// Level patterns compiled on their own, so that the kernel holds only the code they run
+// (the generic kernel carries every radius of every level, and its instruction footprint
+// stalls warps on instruction fetch):
+//   MASK_SIG_T1_4: four levels, levels 0-2 blurred with radii 3, 5, 6 (Table 1's SSAO and
+//                  soft-shadow rows, sigma^2 = 0.924, 1.848, 3.696);
+//   MASK_SIG_T1_GI: four levels, level 1 disabled, levels 0 and 2 blurred with radius 3
+//                  (Table 1's SSGI rows);
+//   MASK_SIG_T1_3: three levels, levels 0 and 1 blurred with radii 3 and 5.
+// The steps and their order are those of all_levels for the same configuration.
+enum { MASK_SIG_ANY = 0, MASK_SIG_T1_4 = 1, MASK_SIG_T1_GI = 2, MASK_SIG_T1_3 = 3 };
+
+template <int SIG>
+__device__ __forceinline__ void all_levels_sig(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  if constexpr (SIG == MASK_SIG_T1_4) {
+    level0_blur<3>(m, sm, x0, y0);
+    blur_level<1, 5, 0>(m, sm, x0, y0);
+    blur_level<2, 6, 1>(m, sm, x0, y0);
+    fill_level<3>(m, sm, x0, y0, m.mode[3]);
+  } else if constexpr (SIG == MASK_SIG_T1_GI) {
+    level0_blur<3>(m, sm, x0, y0);
+    fill_level<1>(m, sm, x0, y0, 2);
+    blur_level<2, 3, 0>(m, sm, x0, y0);
+    fill_level<3>(m, sm, x0, y0, m.mode[3]);
+  } else if constexpr (SIG == MASK_SIG_T1_3) {
+    level0_blur<3>(m, sm, x0, y0);
+    blur_level<1, 5, 0>(m, sm, x0, y0);
+    fill_level<2>(m, sm, x0, y0, m.mode[2]);
+  } else {
+    all_levels(m, sm, x0, y0);
+  }
+}
+
 // ---- frame mode: the work lists of every enabled level, written by the mask kernel
 //
 // Each tile reserves room for its set texels of each level with one atomicAdd on the
@@ -364,6 +396,7 @@ __device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, i
   }
 }
 
+template <int SIG>
 __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
   __shared__ MaskSmem sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -436,7 +469,7 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
     for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   __syncthreads();
-  all_levels(m, sm, x0, y0);
+  all_levels_sig<SIG>(m, sm, x0, y0);
   if (m.a0c) frame_lists(m, sm, x0, y0);
   if (m.label) {
     __syncthreads();
@@ -547,9 +580,23 @@ __global__ void __launch_bounds__(COMPACT_THREADS) compact_scatter_kernel(Compac
 
 }  // namespace
 
+// The level pattern of m when it is one of the specialised ones.
+int mask_signature(const MaskParams& m) {
+  const bool b0 = m.mode[0] == 0 && m.R[0] == 3;
+  if (m.L == 4 && b0 && m.mode[1] == 0 && m.R[1] == 5 && m.mode[2] == 0 && m.R[2] == 6) return MASK_SIG_T1_4;
+  if (m.L == 4 && b0 && m.mode[1] == 2 && m.mode[2] == 0 && m.R[2] == 3) return MASK_SIG_T1_GI;
+  if (m.L == 3 && b0 && m.mode[1] == 0 && m.R[1] == 5) return MASK_SIG_T1_3;
+  return MASK_SIG_ANY;
+}
+
 cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s) {
   dim3 grid((m.W + TS - 1) / TS, (m.H + TS - 1) / TS);
-  masks_kernel<<<grid, MTHREADS, 0, s>>>(m, E);
+  switch (mask_signature(m)) {
+    case MASK_SIG_T1_4: masks_kernel<MASK_SIG_T1_4><<<grid, MTHREADS, 0, s>>>(m, E); break;
+    case MASK_SIG_T1_GI: masks_kernel<MASK_SIG_T1_GI><<<grid, MTHREADS, 0, s>>>(m, E); break;
+    case MASK_SIG_T1_3: masks_kernel<MASK_SIG_T1_3><<<grid, MTHREADS, 0, s>>>(m, E); break;
+    default: masks_kernel<MASK_SIG_ANY><<<grid, MTHREADS, 0, s>>>(m, E); break;
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -144,6 +144,15 @@ def test_ssao_ragged_sizes(mrr, W, H, seed):
     check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=64))
 
 
+@pytest.mark.parametrize("sigma2", [[0.5, 1.0, 2.5, 0.0], [0.3, 0.924, 3.696, 0.0], [1.848, 3.696, 0.924, 0.0]])
+def test_masks_other_radii(mrr, sigma2):
+    """Radii other than Table 1's (3, 5, 6) take the mask kernel that carries every radius;
+    Table 1's patterns take kernels compiled for them.  Both match the oracle bit for bit."""
+    W, H = 203, 141
+    fr = sg.gbuffer(12, W, H, 16, 6)
+    check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=16, sigma2=sigma2), check_full=False)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("W,H", [(100, 37), (36, 18), (4, 1), (1924, 33), (64, 300)])
 def test_edges_tile_staged_sizes(mrr, W, H, precision):
