@@ -14,7 +14,6 @@ namespace mrr {
 // Fault bits a kernel records in the context's device fault word.
 enum : uint32_t {
   FAULT_EDGES_WAIT = 1u << 0,  // an edge-detection tile load did not complete in time
-  FAULT_MERGE_WAIT = 1u << 1,  // a merge tile load did not complete in time
 };
 
 constexpr long long WAIT_CYCLES = 2000000000LL;
