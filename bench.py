@@ -183,6 +183,8 @@ def effect_config(mrr, sg, spec, W, H, precision):
         kw.update(blur=list(spec["blur"]))
     if "merge_mode" in spec:
         kw.update(merge_mode=spec["merge_mode"])
+    if "sample_levels" in spec:
+        kw.update(sample_levels=spec["sample_levels"])
     return mrr.default_config(eff, spec["levels"], W, H, precision=precision, **kw)
 
 
@@ -230,6 +232,8 @@ def oracle_config(orc, sg, wl):
         kw.update(blur=list(wl["blur"]))
     if "merge_mode" in wl:
         kw.update(merge_mode=wl["merge_mode"])
+    if "sample_levels" in wl:
+        kw.update(sample_levels=wl["sample_levels"])
     return orc.default_config(eff, wl["levels"], **kw)
 
 
@@ -676,22 +680,42 @@ def main():
     mrr.mrr_masks(ctx, edges, levels, stream)
     torch.cuda.synchronize()
 
+    import numpy as np
     counts = levels.counts.cpu().tolist()
     depth_host = fr.depth
     n_sky = n_all = 0
+    alg = 0
+    sample_levels = bool(cfg.get("sample_levels", 0))
     for i in range(cfg["num_levels"]):
         if not cfg["enabled"][i] or counts[i] == 0:
             continue
         wlst = levels.worklist[i][: counts[i]].cpu().numpy().view("uint32")
         qy, qx = wlst >> 16, wlst & 0xFFFF
+        if sample_levels and i > 0:
+            # every pixel of each listed block, with every 2^i-th sample
+            dy, dx = np.meshgrid(np.arange(1 << i), np.arange(1 << i), indexing="ij")
+            py = ((qy.astype("int64") << i)[:, None] + dy.reshape(1, -1)).reshape(-1)
+            px = ((qx.astype("int64") << i)[:, None] + dx.reshape(1, -1)).reshape(-1)
+            keep = (py < H) & (px < W)
+            sky = int((depth_host[py[keep], px[keep]] >= fr.cam.far).sum())
+            npx = int(keep.sum())
+            thin = dict(cfg)
+            for key in ("samples", "blocker_samples", "pcf_samples"):
+                if cfg.get(key):
+                    thin[key] = -(-cfg[key] // (1 << i))
+            alg += algorithmic_bytes(thin, npx - sky, sky)
+            n_sky += sky
+            n_all += npx
+            continue
         o = 0 if i == 0 else (1 << (i - 1))
         sy = (qy.astype("int64") << i) + o
         sx = (qx.astype("int64") << i) + o
         sy[sy > H - 1] = H - 1
         sx[sx > W - 1] = W - 1
-        n_sky += int((depth_host[sy, sx] >= fr.cam.far).sum())
+        sky = int((depth_host[sy, sx] >= fr.cam.far).sum())
+        alg += algorithmic_bytes(cfg, counts[i] - sky, sky)
+        n_sky += sky
         n_all += counts[i]
-    alg = algorithmic_bytes(cfg, n_all - n_sky, n_sky)
     peak, peak_kind = measured_peaks()
     achieved = alg / (k_ms * 1e-3) / 1e9
     l2_gbs = l2_copy_gbs(torch)
@@ -711,6 +735,7 @@ def main():
                        "samples": cfg.get("samples"), "levels": cfg["num_levels"], "precision": prec,
                        "blur": cfg.get("blur", [0, 0, 0, 0]),
                        "merge": "step-wise (Sec. 3.3)" if cfg.get("merge_mode", 0) == 1 else "direct (Sec. 4.2)",
+                       "levels_kind": "sample-count (Sec. 6)" if cfg.get("sample_levels", 0) else "resolution",
                        "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
                                 f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",
                        "l2": "flushed (256 MiB write) before every timed step, outside the events",
@@ -724,7 +749,8 @@ def main():
             "shaded_texels": n_all, "shaded_fraction": round(n_all / (W * H), 5),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": measured_traffic(args.workload),
-                         "kernel": "shade_levels_kernel", "kernel_ms": round(k_ms, 5),
+                         "kernel": "shade_levels_kernel" + (" + shade_blocks_kernel" if sample_levels else ""),
+                         "kernel_ms": round(k_ms, 5),
                          "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs",
                          "l2": {"achieved": round(achieved, 2), "peak": round(l2_gbs, 1), "unit": "GB/s",
                                 "frac": round(achieved / l2_gbs, 4),

@@ -98,6 +98,9 @@ typedef struct mrr_config {
   float blur_depth_rel;           /* the blur's depth test: |d' - d| <= blur_depth_rel * d; >= 0, finite */
   int merge_mode;                 /* 0: direct upsampling of every level (Sec. 4.2); 1: step-wise
                                      chain (Sec. 3.3), see mrr_upsample_merge */
+  int sample_levels;              /* 1: sample-count levels (Sec. 6): levels above 0 are rendered at full
+                                     resolution with fewer samples instead of at a lower resolution (see
+                                     mrr_shade_level); requires blur all 0 and merge_mode 0 */
 } mrr_config;
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the
@@ -175,7 +178,11 @@ mrr_status mrr_masks(mrr_ctx* ctx, const uint8_t* edges_dev, const mrr_levels* l
  * texel q in lv->worklist[level] (count lv->counts[level], read on the device),
  * c_level_dev[q] = the context's effect evaluated at full-resolution pixel s_i(q)
  * from the full-resolution G-buffer.  Other texels are not written.  c_level_dev is
- * [H_i][W_i] of float (FP32) / half (FP16), 4 per texel (rgb + 0) for MRR_SSGI. */
+ * [H_i][W_i] of float (FP32) / half (FP16), 4 per texel (rgb + 0) for MRR_SSGI.
+ * With cfg.sample_levels = 1 and level > 0 (Sec. 6), c_level_dev is [H][W] instead: every
+ * full-resolution pixel p of each listed texel's block [2^i q, 2^i q + 2^i) gets the
+ * effect at p computed with every 2^i-th entry of each sample table (entries 0, 2^i,
+ * 2 2^i, ...: ceil(n / 2^i) of n hemisphere samples, blocker taps and filter taps). */
 mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const mrr_levels* lv,
                            void* c_level_dev, void* stream);
 
@@ -215,6 +222,10 @@ mrr_status mrr_blur_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const m
  * S_i(q) = 1 and alpha > 0, else up; the output is the composite at level 0.  That mode
  * keeps the intermediate composites in the context's pools, so the frame must fit the
  * context's max size (MRR_EINVAL otherwise).
+ * With cfg.sample_levels = 1 every c_levels_dev[i] is [H][W] and only the masks are
+ * interpolated: per pixel, from c' = c_{L-1}(p), each finer enabled level i whose texel
+ * (p_x >> i, p_y >> i) is rendered blends in c_i(p) with alpha = min(w_i a_i(p), 1), a_i
+ * interpolated as above.
  * c_levels_dev[i] as in mrr_shade_level (NULL for disabled levels).  out_dev is
  * [H][W] float, or [H][W] float4 (rgb + 0) for MRR_SSGI. */
 mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,

@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float), ("store_half", ctypes.c_int),
         ("cam", ctypes.c_float * 15), ("light", ctypes.c_float * 15), ("shadow_size", ctypes.c_int),
         ("blur", ctypes.c_int * 4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
+        ("sample_levels", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,8 @@ def _L():
             getattr(lib, f"orc_merge_{suf}").argtypes = [P, vp, vp, vp, vp]
             getattr(lib, f"orc_blur_level_{suf}").argtypes = [P, vp, ci, vp, vp, vp]
             getattr(lib, f"orc_merge_stepwise_{suf}").argtypes = [P, vp, vp, vp, vp]
+            getattr(lib, f"orc_merge_samples_{suf}").argtypes = [P, vp, vp, vp, vp]
+            getattr(lib, f"orc_shade_blocks_{suf}").argtypes = [P, vp, vp, vp, vp, ci, vp, ci, vp]
         lib.orc_gauss_weights_f32.argtypes = [ctypes.c_double, vp]
         lib.orc_gauss_weights_f64.argtypes = [ctypes.c_double, vp]
         lib.orc_compact.argtypes = [ci, ci, vp, vp]
@@ -143,7 +146,7 @@ def default_config(effect: str, num_levels: int = 4, **kw) -> dict:
                depth_rel=0.05, normal_cos=0.9, force_level0=0, samples=16, radius=0.5,
                ao_bias=0.0125, gi_min_dist2=0.01, kernel=None, blocker_samples=32, pcf_samples=64,
                blocker_taps=None, pcf_taps=None, light_size=0.5, shadow_bias=0.03, store_half=0,
-               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0)
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0)
     cfg.update(kw)
     return cfg
 
@@ -179,6 +182,7 @@ class _Bound:
             p.blur[i] = int(blur[i])
         p.blur_depth_rel = cfg.get("blur_depth_rel", 0.05)
         p.merge_mode = int(cfg.get("merge_mode", 0))
+        p.sample_levels = int(cfg.get("sample_levels", 0))
         cam = frame.cam.as_array()
         for k in range(15):
             p.cam[k] = cam[k]
@@ -283,16 +287,48 @@ def view_pos(frame, cfg, x, y, d, precision="f64"):
     return out
 
 
+def level_config(cfg, level):
+    """Sample-count levels (Sec. 6): level i keeps every 2^i-th entry of each sample table
+    (entries 0, 2^i, 2 2^i, ...: ceil(n / 2^i) of n), so the thinned set spans the same
+    range of sample lengths or disk radii as the full one."""
+    out = dict(cfg)
+    step = 1 << level
+    if cfg.get("kernel") is not None:
+        k = np.asarray(cfg["kernel"], np.float32).reshape(-1, 4)[::step]
+        out.update(kernel=k, samples=len(k))
+    for taps, count in (("blocker_taps", "blocker_samples"), ("pcf_taps", "pcf_samples")):
+        if cfg.get(taps) is not None:
+            t = np.asarray(cfg[taps], np.float32).reshape(-1, 2)[::step]
+            out.update({taps: t, count: len(t)})
+    return out
+
+
+def shade_blocks(frame, cfg, level, worklist, precision="f32"):
+    """Sample-count level `level`: every pixel of each listed texel's block at full
+    resolution, with the level's thinned sample tables; [H][W][C], NaN elsewhere."""
+    b = _Bound(frame, level_config(cfg, level))
+    dt = _dtype(precision)
+    c = np.full((frame.height, frame.width, channels(cfg)), np.nan, dt)
+    wl = np.ascontiguousarray(worklist, np.uint32)
+    getattr(_L(), f"orc_shade_blocks_{_suffix(precision)}")(
+        b.ref, _ptr(b.depth), _ptr(b.normal), _ptr(b.color), _ptr(b.smap), level, _ptr(wl), len(wl), _ptr(c))
+    return c
+
+
 def merge(frame, cfg, a, S, c, precision="f32"):
     """Eq. (1): direct upsampling of every level (Sec. 4.2), or with cfg["merge_mode"] = 1
-    the step-wise chain of Sec. 3.3."""
+    the step-wise chain of Sec. 3.3; with cfg["sample_levels"] = 1 the full-resolution
+    sub-images of sample-count levels (Sec. 6)."""
     b = _Bound(frame, cfg)
     dt = _dtype(precision)
     a = [np.ascontiguousarray(x, dt) for x in a]
     S = [np.ascontiguousarray(x, np.uint8) for x in S]
     c = [np.ascontiguousarray(x, dt) for x in c]
     out = np.zeros((frame.height, frame.width, channels(cfg)), dt)
-    fn = "orc_merge_stepwise" if cfg.get("merge_mode", 0) == 1 else "orc_merge"
+    if cfg.get("sample_levels", 0):
+        fn = "orc_merge_samples"
+    else:
+        fn = "orc_merge_stepwise" if cfg.get("merge_mode", 0) == 1 else "orc_merge"
     getattr(_L(), f"{fn}_{_suffix(precision)}")(b.ref, _ptr_array(a), _ptr_array(S), _ptr_array(c), _ptr(out))
     return out
 
@@ -311,15 +347,21 @@ def blur_level(frame, cfg, level, S, c, precision="f32"):
 
 def render(frame, cfg, precision="f32") -> dict:
     """The whole method (Sec. 3): edges -> masks -> work lists -> sub-images (blurred
-    where cfg["blur"] asks, Sec. 4.1) -> Eq. (1)."""
+    where cfg["blur"] asks, Sec. 4.1; full resolution with thinned samples above level 0
+    when cfg["sample_levels"] is set, Sec. 6) -> Eq. (1)."""
+    blur = cfg.get("blur", [0, 0, 0, 0])
+    if cfg.get("sample_levels", 0) and (any(blur) or cfg.get("merge_mode", 0)):
+        raise ValueError("sample-count levels take neither the sub-image blur nor step-wise blending")
     E = edges(frame, cfg, precision)
     a, S, label = masks(frame, cfg, E, precision)
     lists, c = [], []
-    blur = cfg.get("blur", [0, 0, 0, 0])
     for i in range(cfg["num_levels"]):
         wl = compact(S[i])
         lists.append(wl)
-        ci = shade_level(frame, cfg, i, wl, precision)
+        if cfg.get("sample_levels", 0) and i > 0:
+            ci = shade_blocks(frame, cfg, i, wl, precision)
+        else:
+            ci = shade_level(frame, cfg, i, wl, precision)
         if blur[i]:
             ci = blur_level(frame, cfg, i, S[i], ci, precision)
         c.append(ci)

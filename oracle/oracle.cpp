@@ -18,7 +18,9 @@
 //             formulas, so the readings below are fixed in the design notes;
 //   Sec. 4.2  bilinear upsampling of every sub-image to full size and the sequential
 //             blend of Eq. (1), from the coarsest level to the finest; optionally the
-//             step-wise chain of Sec. 3.3 instead.
+//             step-wise chain of Sec. 3.3 instead;
+//   Sec. 6    optionally sample-count levels: levels above 0 rendered at full
+//             resolution with fewer samples, blended without upsampling.
 // T = float is the parity oracle (discrete decisions in the kernels' precision, FP32);
 // T = double is the FP64 reference for error statements.  The build uses
 // -ffp-contract=off: a multiply-add is fused only where the source writes std::fma
@@ -63,6 +65,7 @@ struct orc_params {
   int blur[4];           // 1: level i's sub-image gets the bilateral blur of Sec. 4.1
   float blur_depth_rel;  // that blur's depth test: |d' - d| <= blur_depth_rel * d
   int merge_mode;        // 0: direct upsampling (Sec. 4.2); 1: step-wise chain (Sec. 3.3)
+  int sample_levels;     // 1: levels above 0 at full resolution with fewer samples (Sec. 6)
 };
 
 }  // extern "C"
@@ -644,6 +647,36 @@ void blur_level(const orc_params& p, const float* depth, int level, const uint8_
   }
 }
 
+// Sample-count levels (Sec. 6 proposes them for effects that must not be sub-sampled:
+// a sub-image rendered at full resolution with fewer samples instead of at a lower
+// resolution).  Level i >= 1 keeps its mask and work list, but every full-resolution
+// pixel of each listed texel's block [2^i q, 2^i q + 2^i) (inside the image) is shaded;
+// p carries the level's sample tables (the caller thins them).  c is [H][W] x C; pixels
+// outside the listed blocks are left untouched.
+template <typename T>
+void shade_blocks(const orc_params& p, const Inputs& in, int level, const uint32_t* list, int n, T* c) {
+  const int W = p.width, H = p.height, C = channels(p), B = 1 << level;
+  View<T> v = make_view<T>(W, H, p.cam[12], p.cam[13], p.cam[14]);
+  LightView<T> L = make_light<T>(p);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int k = 0; k < n; ++k) {
+    const int qx = (int)(list[k] & 0xFFFFu), qy = (int)(list[k] >> 16);
+    for (int dy = 0; dy < B; ++dy) {
+      for (int dx = 0; dx < B; ++dx) {
+        const int x = qx * B + dx, y = qy * B + dy;
+        if (x >= W || y >= H) continue;
+        T val[3];
+        shade_at(p, v, L, in, x, y, val);
+        for (int ch = 0; ch < C; ++ch) {
+          T out = val[ch];
+          if (p.store_half) out = (T)round_to_half((float)out);
+          c[((size_t)y * W + x) * C + ch] = out;
+        }
+      }
+    }
+  }
+}
+
 // Naive full-resolution rendering (the comparison of Sec. 5): the effect at every pixel.
 template <typename T> void shade_full(const orc_params& p, const Inputs& in, T* out) {
   const int W = p.width, H = p.height, C = channels(p);
@@ -765,6 +798,46 @@ void merge_stepwise(const orc_params& p, T* const* a, uint8_t* const* S, T* cons
   std::copy(comp.begin(), comp.end(), out);
 }
 
+// Blending of sample-count levels: every sub-image is full resolution, so nothing is
+// upsampled but the masks.  Per pixel p, from c' = c_{L-1}(p) (the coarsest level is
+// rendered everywhere) over every finer enabled level i: if p's texel at level i,
+// (p_x >> i, p_y >> i), is rendered, alpha = min(w_i a_i(p), 1) with a_i(p) interpolated
+// bilinearly exactly as in the direct merge above, and c' = c_i(p) alpha + c' (1 - alpha)
+// where alpha > 0; a pixel whose texel is not rendered keeps c' (its value does not exist).
+template <typename T>
+void merge_samples(const orc_params& p, T* const* a, uint8_t* const* S, T* const* c, T* out) {
+  const int W = p.width, H = p.height, L = p.num_levels, C = channels(p);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      const size_t pix = (size_t)y * W + x;
+      T cp[3] = {T(0), T(0), T(0)};
+      for (int ch = 0; ch < C; ++ch) cp[ch] = c[L - 1][pix * C + ch];
+      for (int i = L - 2; i >= 0; --i) {
+        if (!p.enabled[i]) continue;
+        const int Wi = level_dim(W, i), Hi = level_dim(H, i);
+        if (!S[i][(size_t)(y >> i) * Wi + (x >> i)]) continue;
+        const T scale = (T)(1 << i);
+        T ux = (T)(x - level_origin(i)) / scale;
+        T uy = (T)(y - level_origin(i)) / scale;
+        int x0 = (int)std::floor(ux), y0 = (int)std::floor(uy);
+        T fx = ux - (T)x0, fy = uy - (T)y0;
+        int xs[2] = {std::min(std::max(x0, 0), Wi - 1), std::min(std::max(x0 + 1, 0), Wi - 1)};
+        int ys[2] = {std::min(std::max(y0, 0), Hi - 1), std::min(std::max(y0 + 1, 0), Hi - 1)};
+        T w[4] = {(T(1) - fx) * (T(1) - fy), fx * (T(1) - fy), (T(1) - fx) * fy, fx * fy};
+        size_t idx[4] = {(size_t)ys[0] * Wi + xs[0], (size_t)ys[0] * Wi + xs[1], (size_t)ys[1] * Wi + xs[0],
+                         (size_t)ys[1] * Wi + xs[1]};
+        T ahat = T(0);
+        for (int k = 0; k < 4; ++k) ahat = ahat + w[k] * a[i][idx[k]];
+        T alpha = std::min((T)p.weight[i] * ahat, T(1));
+        if (!(alpha > T(0))) continue;
+        for (int ch = 0; ch < C; ++ch) cp[ch] = c[i][pix * C + ch] * alpha + cp[ch] * (T(1) - alpha);
+      }
+      for (int ch = 0; ch < C; ++ch) out[pix * C + ch] = cp[ch];
+    }
+  }
+}
+
 Inputs make_inputs(const float* depth, const float* normal, const float* color, const float* smap) {
   Inputs in;
   in.depth = depth;
@@ -843,6 +916,14 @@ int orc_gauss_weights_f64(double sigma2, double* g) { return gauss_weights<doubl
   }                                                                                                          \
   void orc_merge_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) {          \
     merge<T>(*p, a, S, c, out);                                                                              \
+  }                                                                                                          \
+  void orc_shade_blocks_##SUF(const orc_params* p, const float* depth, const float* normal,                  \
+                              const float* color, const float* smap, int level, const uint32_t* list, int n,\
+                              T* c) {                                                                        \
+    shade_blocks<T>(*p, make_inputs(depth, normal, color, smap), level, list, n, c);                        \
+  }                                                                                                          \
+  void orc_merge_samples_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) {  \
+    merge_samples<T>(*p, a, S, c, out);                                                                      \
   }                                                                                                          \
   void orc_merge_stepwise_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) { \
     merge_stepwise<T>(*p, a, S, c, out);                                                                     \

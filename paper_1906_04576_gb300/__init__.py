@@ -61,6 +61,7 @@ class mrr_config(ctypes.Structure):
         ("max_width", ctypes.c_int), ("max_height", ctypes.c_int),
         ("lanes_per_texel", ctypes.c_int), ("lanes_per_pixel", ctypes.c_int), ("no_graph", ctypes.c_int),
         ("blur", I4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
+        ("sample_levels", ctypes.c_int),
     ]
 
 
@@ -270,6 +271,7 @@ def make_config(cfg: dict) -> tuple[mrr_config, list]:
         c.blur[i] = int(blur[i])
     c.blur_depth_rel = cfg.get("blur_depth_rel", 0.05)
     c.merge_mode = int(cfg.get("merge_mode", 0))
+    c.sample_levels = int(cfg.get("sample_levels", 0))
     return c, keep
 
 
@@ -376,8 +378,9 @@ def alloc_levels(width: int, height: int, num_levels: int, with_label: bool = Tr
 def alloc_subimages(ctx: Context, width: int, height: int, device="cuda") -> list:
     dt = torch.float16 if ctx.config.get("precision", "fp32") == "fp16" else torch.float32
     out = []
+    full_res = bool(ctx.config.get("sample_levels", 0))   # sample-count levels: [H][W] above level 0
     for i in range(ctx.config["num_levels"]):
-        w, h = mrr_level_dims(width, height, i)
+        w, h = (width, height) if full_res else mrr_level_dims(width, height, i)
         shape = (h, w, 4) if ctx.channels == 4 else (h, w)
         out.append(torch.full(shape, float("nan"), dtype=dt, device=device) if ctx.config["enabled"][i] else None)
     return out
@@ -671,6 +674,6 @@ def default_config(effect: str, num_levels: int, max_width: int, max_height: int
     cfg = dict(effect=effect, precision="fp32", num_levels=num_levels, sigma2=sigma2, weight=weight,
                enabled=enabled, depth_rel=0.05, normal_cos=0.9, force_level0=0, radius=0.5, ao_bias=0.0125,
                gi_min_dist2=0.01, light_size=0.5, shadow_bias=0.03, max_width=max_width, max_height=max_height,
-               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0)
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0)
     cfg.update(kw)
     return cfg

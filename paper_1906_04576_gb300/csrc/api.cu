@@ -208,6 +208,47 @@ ShadeParams make_shade_params(const mrr_ctx* ctx, const mrr_gbuffer& g) {
   return p;
 }
 
+FrameIn make_frame_in(const mrr_gbuffer& g);
+
+// The shading parameters of level `level`: for sample-count levels above 0 (Sec. 6) every
+// sample table keeps its entries 0, 2^level, 2 * 2^level, ... (ceil(n / 2^level) of n).
+ShadeParams level_shade_params(const mrr_ctx* ctx, const mrr_gbuffer& g, int level) {
+  ShadeParams p = make_shade_params(ctx, g);
+  if (!ctx->cfg.sample_levels || level == 0) return p;
+  const int step = 1 << level;
+  auto thin = [&](int n) { return (n + step - 1) / step; };
+  p.samples = thin(ctx->cfg.samples);
+  for (int j = 0; j < MRR_MAX_SAMPLES; ++j) {
+    const float4 k = j < p.samples ? ctx->kernel[j * step] : make_float4(0.f, 0.f, 0.f, 0.f);
+    p.kernel[j] = k;
+    p.kx[j] = k.x;
+    p.ky[j] = k.y;
+    p.kz[j] = k.z;
+  }
+  p.nb = thin(ctx->cfg.blocker_samples);
+  p.np = thin(ctx->cfg.pcf_samples);
+  for (int j = 0; j < MRR_MAX_TAPS; ++j) {
+    p.btaps[j] = j < p.nb ? ctx->btaps[j * step] : make_float2(0.f, 0.f);
+    p.ptaps[j] = j < p.np ? ctx->ptaps[j * step] : make_float2(0.f, 0.f);
+  }
+  return p;
+}
+
+// Sample-count level `level` of frame g into c ([H][W]).
+mrr_status shade_blocks_impl(mrr_ctx* ctx, const mrr_gbuffer& g, const mrr_levels* lv, int level, void* c,
+                             cudaStream_t s) {
+  BlockLevel b;
+  b.level = level;
+  b.Wi = lv->width[level];
+  b.Hi = lv->height[level];
+  b.list = lv->worklist[level];
+  b.count = lv->counts + level;
+  b.c = c;
+  MRR_CUDA(ctx, launch_shade_blocks(level_shade_params(ctx, g, level), make_frame_in(g), ctx->cfg.precision, b,
+                                    ctx->shade_grid, s));
+  return MRR_OK;
+}
+
 FrameIn make_frame_in(const mrr_gbuffer& g) {
   FrameIn in;
   in.depth = g.depth;
@@ -370,6 +411,25 @@ mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
   if (cf.merge_mode == 1 && cf.num_levels > 1) {
     mrr_status st = chain_impl(ctx, lv, c, out, s, compact_level0);
     if (st != MRR_OK) return st;
+  } else if (cf.sample_levels && cf.num_levels > 1) {
+    MergeParams mp;
+    std::memset(&mp, 0, sizeof mp);
+    mp.W = lv->width[0];
+    mp.H = lv->height[0];
+    mp.L = cf.num_levels;
+    mp.C = channels(cf);
+    mp.half_store = cf.precision == MRR_FP16;
+    for (int i = 0; i < cf.num_levels; ++i) {
+      mp.enabled[i] = cf.enabled[i];
+      mp.Wi[i] = lv->width[i];
+      mp.Hi[i] = lv->height[i];
+      mp.weight[i] = cf.weight[i];
+      mp.alpha[i] = lv->alpha[i];
+      mp.stencil[i] = lv->stencil[i];
+      mp.c[i] = c[i];
+    }
+    if (compact_level0) mp.enabled[0] = 0;  // blended afterwards from level 0's list
+    MRR_CUDA(ctx, launch_merge_samples(mp, out, s));
   } else {
     MergeParams mp;
     std::memset(&mp, 0, sizeof mp);
@@ -552,7 +612,7 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   ShadeLevels sl;
   std::memset(&sl, 0, sizeof sl);
   for (int i = 0; i < c.num_levels; ++i) {
-    if (!c.enabled[i]) continue;
+    if (!c.enabled[i] || (c.sample_levels && i > 0)) continue;
     const int k = sl.nlev++;
     sl.level[k] = i;
     sl.list[k] = ctx->worklist[i];
@@ -562,7 +622,14 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
     if (i == 0) sl.compact |= 1 << k;
   }
   sl.counts = ctx->counts;
-  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
+  if (sl.nlev)
+    MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
+  if (c.sample_levels)
+    for (int i = 1; i < c.num_levels; ++i) {
+      if (!c.enabled[i]) continue;
+      st = shade_blocks_impl(ctx, *g, &lv, i, ctx->cbuf[i], s);
+      if (st != MRR_OK) return st;
+    }
   void* cm[MRR_MAX_LEVELS];
   st = blur_pools(ctx, g, &lv, cm, s);
   if (st != MRR_OK) return st;
@@ -636,7 +703,8 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
     MRR_CUDA(ctx, cudaMalloc(&ctx->stencil[i], n));
     if (c.enabled[i]) {
       MRR_CUDA(ctx, cudaMalloc(&ctx->worklist[i], n * sizeof(uint32_t)));
-      MRR_CUDA(ctx, cudaMalloc(&ctx->cbuf[i], n * cbytes(c)));
+      // sample-count levels keep every level's sub-image at full resolution
+      MRR_CUDA(ctx, cudaMalloc(&ctx->cbuf[i], (c.sample_levels && i > 0 ? npx : n) * cbytes(c)));
     }
     if (c.blur[i]) MRR_CUDA(ctx, cudaMalloc(&ctx->bbuf[i], n * cbytes(c)));
     if (c.merge_mode == 1 && i >= 1 && i < c.num_levels - 1 && c.enabled[i])
@@ -701,6 +769,12 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
   }
   if (!(c.blur_depth_rel >= 0.f) || !(c.blur_depth_rel <= FLT_MAX)) return MRR_EINVAL;
   if (c.merge_mode != 0 && c.merge_mode != 1) return MRR_EINVAL;
+  if (c.sample_levels != 0 && c.sample_levels != 1) return MRR_EINVAL;
+  if (c.sample_levels) {  // full-resolution sub-images: no level blur, direct blend only
+    if (c.merge_mode != 0) return MRR_EINVAL;
+    for (int i = 0; i < MRR_MAX_LEVELS; ++i)
+      if (c.blur[i]) return MRR_EINVAL;
+  }
   for (int v : {c.lanes_per_texel, c.lanes_per_pixel})
     if (v != 0 && v != 1 && v != 2 && v != 4) return MRR_EINVAL;
   if (c.effect != MRR_SSM) {
@@ -811,6 +885,7 @@ mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const 
                 g->height);
   if (!c_level_dev || !aligned(c_level_dev, cbytes(ctx->cfg)))
     return fail(ctx, MRR_EINVAL, "c_level_dev is NULL or misaligned");
+  if (ctx->cfg.sample_levels && level > 0) return shade_blocks_impl(ctx, *g, lv, level, c_level_dev, (cudaStream_t)stream);
   ShadeParams p = make_shade_params(ctx, *g);
   ShadeLevels sl;
   std::memset(&sl, 0, sizeof sl);
@@ -843,6 +918,7 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
     if (!ctx->cfg.enabled[i]) continue;
     if (!c_levels_dev[i] || !aligned(c_levels_dev[i], cbytes(ctx->cfg)))
       return fail(ctx, MRR_EINVAL, "sub-image %d is NULL or misaligned", i);
+    if (ctx->cfg.sample_levels && i > 0) continue;  // shaded below, at full resolution
     const int k = sl.nlev++;
     sl.level[k] = i;
     sl.list[k] = lv->worklist[i];
@@ -852,8 +928,15 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
   }
   sl.counts = lv->counts;
   ShadeParams p = make_shade_params(ctx, *g);
-  MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
-                                    ctx->split_texel, (cudaStream_t)stream));
+  if (sl.nlev)
+    MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
+                                      ctx->split_texel, (cudaStream_t)stream));
+  if (ctx->cfg.sample_levels)
+    for (int i = 1; i < ctx->cfg.num_levels; ++i) {
+      if (!ctx->cfg.enabled[i]) continue;
+      st = shade_blocks_impl(ctx, *g, lv, i, c_levels_dev[i], (cudaStream_t)stream);
+      if (st != MRR_OK) return st;
+    }
   return MRR_OK;
 }
 
@@ -963,7 +1046,7 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     it.in = make_frame_in(frames[k]);
     it.precision = ctx->cfg.precision;
     for (int i = 0; i < ctx->cfg.num_levels; ++i) {
-      if (!ctx->cfg.enabled[i]) continue;
+      if (!ctx->cfg.enabled[i] || (ctx->cfg.sample_levels && i > 0)) continue;
       const int q = it.lv.nlev++;
       it.lv.level[q] = i;
       it.lv.list[q] = ctx->worklist[i];
@@ -978,6 +1061,16 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     return batch_fail(b, MRR_ECUDA, "item upload");
   if (launch_shade_batch(b->items_dev, n, b->queue_head, chunk, grid, s) != cudaSuccess)
     return batch_fail(b, MRR_ECUDA, "batched shading launch");
+  // sample-count levels above 0 are shaded per frame at full resolution
+  for (int k = 0; k < n; ++k) {
+    mrr_ctx* ctx = ctxs[k];
+    if (!ctx->cfg.sample_levels) continue;
+    for (int i = 1; i < ctx->cfg.num_levels; ++i) {
+      if (!ctx->cfg.enabled[i]) continue;
+      mrr_status st = shade_blocks_impl(ctx, frames[k], &lv[k], i, ctx->cbuf[i], s);
+      if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());
+    }
+  }
   if (outs) {
     for (int k = 0; k < n; ++k) {
       void* cm[MRR_MAX_LEVELS];

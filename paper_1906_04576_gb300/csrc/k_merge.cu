@@ -18,6 +18,7 @@
 //
 // chain_kernel: the step-wise reading of Sec. 3.3 instead -- one launch per step, each
 // level's composite computed at its own resolution from the previous one.
+// merge_samples_kernel: the blend of sample-count levels (full-resolution sub-images).
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -475,6 +476,53 @@ void launch_chain_t(const ChainParams& p, cudaStream_t s) {
     chain_kernel<CT, C, false><<<grid, block, 0, s>>>(p);
 }
 
+// Blend of sample-count levels (Sec. 6): every sub-image is [H][W], so only the masks
+// are interpolated.  Per pixel, from c' = c_{L-1}(p), over every finer enabled level i
+// whose texel (x >> i, y >> i) is rendered: a_i interpolated at p exactly as merge_kernel
+// does (taps (p - o_i) >> i, +1, clamped; fraction ((p - o_i) & (2^i - 1)) 2^-i),
+// alpha = min(w_i a_i, 1) and, where alpha > 0, c' = c_i(p) alpha + c' (1 - alpha).
+template <typename CT, int C>
+__global__ void __launch_bounds__(256) merge_samples_kernel(MergeParams p, float* __restrict__ out) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= p.W || y >= p.H) return;
+  const size_t pix = (size_t)y * p.W + x;
+  const float3 top = load_c<CT>(p.c[p.L - 1], pix, C);
+  float c0 = top.x, c1 = top.y, c2 = top.z;
+  for (int i = p.L - 2; i >= 0; --i) {
+    if (!p.enabled[i]) continue;
+    const int Wi = p.Wi[i], Hi = p.Hi[i];
+    if (!__ldg(p.stencil[i] + (size_t)(y >> i) * Wi + (x >> i))) continue;
+    const int o = i == 0 ? 0 : 1 << (i - 1), mask = (1 << i) - 1;
+    const float inv = __int_as_float((127 - i) << 23);  // 2^-i
+    const int nx = x - o, ny = y - o;
+    const int x0 = nx >> i, y0 = ny >> i;
+    const float fx = (float)(nx & mask) * inv, fy = (float)(ny & mask) * inv;
+    const int xa = min(max(x0, 0), Wi - 1), xb = min(max(x0 + 1, 0), Wi - 1);
+    const int ya = min(max(y0, 0), Hi - 1), yb = min(max(y0 + 1, 0), Hi - 1);
+    const float* a = p.alpha[i];
+    const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy), w2 = (1.0f - fx) * fy, w3 = fx * fy;
+    float ahat = 0.0f;
+    ahat = ahat + w0 * __ldg(a + (size_t)ya * Wi + xa);
+    ahat = ahat + w1 * __ldg(a + (size_t)ya * Wi + xb);
+    ahat = ahat + w2 * __ldg(a + (size_t)yb * Wi + xa);
+    ahat = ahat + w3 * __ldg(a + (size_t)yb * Wi + xb);
+    const float wa = p.weight[i] * ahat;
+    const float alpha = (1.0f < wa) ? 1.0f : wa;
+    if (!(alpha > 0.0f)) continue;
+    const float3 v = load_c<CT>(p.c[i], pix, C);
+    const float om = 1.0f - alpha;
+    c0 = v.x * alpha + c0 * om;
+    if (C == 4) {
+      c1 = v.y * alpha + c1 * om;
+      c2 = v.z * alpha + c2 * om;
+    }
+  }
+  if (C == 4)
+    reinterpret_cast<float4*>(out)[pix] = make_float4(c0, c1, c2, 0.0f);
+  else
+    out[pix] = c0;
+}
+
 template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
   dim3 grid((p.W + MTX - 1) / MTX, (p.H + MTY - 1) / MTY);
@@ -519,6 +567,19 @@ cudaError_t launch_chain(const ChainParams& p, cudaStream_t s) {
   } else {
     if (p.half_store) launch_chain_t<__half, 1>(p, s);
     else launch_chain_t<float, 1>(p, s);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_samples(const MergeParams& p, float* out, cudaStream_t s) {
+  dim3 grid((p.W + 31) / 32, (p.H + 7) / 8), block(32, 8);
+  if (p.C == 4) {
+    if (p.half_store) merge_samples_kernel<__half, 4><<<grid, block, 0, s>>>(p, out);
+    else merge_samples_kernel<float, 4><<<grid, block, 0, s>>>(p, out);
+  } else {
+    if (p.half_store) merge_samples_kernel<__half, 1><<<grid, block, 0, s>>>(p, out);
+    else merge_samples_kernel<float, 1><<<grid, block, 0, s>>>(p, out);
   }
   count_launches(1);
   return cudaGetLastError();

@@ -10,6 +10,8 @@
 //   is an integer, so the split is exact); SSM and SSGI accumulate floats in sample order
 //   and use one lane per texel.
 // shade_full_kernel: one lane group per pixel over 2-D tiles of 8 rows.
+// shade_blocks_kernel: sample-count levels -- every pixel of a listed texel's block at
+//   full resolution, with the level's thinned sample tables.
 // Both evaluate the same effect function at the same full-resolution pixel, so a level
 // texel's value equals full-resolution shading at its sample pixel bit for bit.
 #include "mrr_internal.cuh"
@@ -116,6 +118,35 @@ __global__ void __launch_bounds__(256, 2) shade_full_kernel(ShadeParams p, Frame
   if (valid && (threadIdx.x & (SPLIT - 1)) == 0) store_value<EFFECT>(out, (size_t)y * p.v.W + x, v, false);
 }
 
+// Sample-count levels (Sec. 6): one lane per full-resolution pixel of each listed texel's
+// block, with the level's thinned sample tables in p; lanes past the end (or on an entry
+// that is not a texel of the level, or a pixel past the image) shade nothing.
+template <int EFFECT, typename NT, typename SMT>
+__global__ void __launch_bounds__(SHADE_THREADS, 2) shade_blocks_kernel(ShadeParams p, FrameIn in, BlockLevel b,
+                                                                     int half_store) {
+  const int W = p.v.W, H = p.v.H, i = b.level, B = 1 << b.level;
+  const uint32_t n = min(__ldg(b.count), (uint32_t)b.Wi * (uint32_t)b.Hi);
+  const uint32_t total = n << (2 * i);
+  for (uint32_t base = blockIdx.x * SHADE_THREADS; base < total; base += gridDim.x * SHADE_THREADS) {
+    const uint32_t g = base + threadIdx.x;
+    bool valid = g < total;
+    int x = 0, y = 0;
+    if (valid) {
+      const uint32_t e = __ldg(b.list + (g >> (2 * i)));
+      const int qx = (int)(e & 0xFFFFu), qy = (int)(e >> 16);
+      const uint32_t sub = g & ((1u << (2 * i)) - 1u);
+      const int px = qx * B + (int)(sub & (uint32_t)(B - 1)), py = qy * B + (int)(sub >> i);
+      valid = qx < b.Wi && qy < b.Hi && px < W && py < H;
+      if (valid) {
+        x = px;
+        y = py;
+      }
+    }
+    const float3 v = effect_at<EFFECT, NT, SMT, 1>(p, in, x, y, valid);
+    if (valid) store_value<EFFECT>(b.c, (size_t)y * W + x, v, half_store != 0);
+  }
+}
+
 // Resident CTAs of one instantiation (SMs x CTAs per SM), computed once per instantiation.
 template <typename K> int resident_blocks(K kernel) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -138,6 +169,23 @@ template <int EFFECT, typename NT, typename SMT, int SPLIT>
 void launch_full_t(const ShadeParams& p, const FrameIn& in, float* out, cudaStream_t s) {
   dim3 block(32, 8), grid((p.v.W + 32 / SPLIT - 1) / (32 / SPLIT), (p.v.H + 7) / 8);
   shade_full_kernel<EFFECT, NT, SMT, SPLIT><<<grid, block, 0, s>>>(p, in, out);
+}
+
+template <int EFFECT, typename NT, typename SMT>
+void launch_blocks_t(const ShadeParams& p, const FrameIn& in, const BlockLevel& b, int half_store, int grid_mult,
+                     cudaStream_t s) {
+  static const int resident = resident_blocks(shade_blocks_kernel<EFFECT, NT, SMT>);
+  shade_blocks_kernel<EFFECT, NT, SMT><<<resident * grid_mult, SHADE_THREADS, 0, s>>>(p, in, b, half_store);
+}
+
+template <typename NT, typename SMT>
+void blocks_dispatch(const ShadeParams& p, const FrameIn& in, const BlockLevel& b, int half_store, int grid,
+                     cudaStream_t s) {
+  switch (p.effect) {
+    case MRR_SSAO: launch_blocks_t<MRR_SSAO, NT, SMT>(p, in, b, half_store, grid, s); break;
+    case MRR_SSM: launch_blocks_t<MRR_SSM, NT, SMT>(p, in, b, half_store, grid, s); break;
+    default: launch_blocks_t<MRR_SSGI, NT, SMT>(p, in, b, half_store, grid, s); break;
+  }
 }
 
 template <typename NT, typename SMT>
@@ -207,6 +255,14 @@ cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int pre
                                 int grid, int split, cudaStream_t s) {
   if (precision == MRR_FP16) levels_dispatch<half4, __half>(p, in, lv, 1, grid, split, s);
   else levels_dispatch<float4, float>(p, in, lv, 0, grid, split, s);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade_blocks(const ShadeParams& p, const FrameIn& in, int precision, const BlockLevel& b,
+                                int grid_mult, cudaStream_t s) {
+  if (precision == MRR_FP16) blocks_dispatch<half4, __half>(p, in, b, 1, grid_mult, s);
+  else blocks_dispatch<float4, float>(p, in, b, 0, grid_mult, s);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -132,6 +132,15 @@ struct ShadeLevels {
   int compact;
 };
 
+// One sample-count level (Sec. 6): every full-resolution pixel of each listed texel's
+// block [2^level q, 2^level q + 2^level) is shaded into the [H][W] sub-image c.
+struct BlockLevel {
+  int level, Wi, Hi;
+  const uint32_t* list;
+  const uint32_t* count;  // device: entries in the list (clamped to W_i * H_i when read)
+  void* c;
+};
+
 // One frame of a batched shading launch (k_batch.cu); an array of these lives in
 // device memory.
 constexpr int MAX_BATCH = 8;
@@ -204,12 +213,17 @@ cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int pre
                                 int grid, int split, cudaStream_t s);
 cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
                               cudaStream_t s);
+cudaError_t launch_shade_blocks(const ShadeParams& p, const FrameIn& in, int precision, const BlockLevel& b,
+                                int grid_mult, cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 // bit patterns [first, last] as floats x: counts into *bad every x where the kernels'
 // reciprocal of x or of -x differs from IEEE division
 cudaError_t launch_check_reciprocal(uint32_t first, uint32_t last, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_blend0(const Blend0Params& p, float* out, cudaStream_t s);
 cudaError_t launch_chain(const ChainParams& p, cudaStream_t s);
+// Blend of sample-count levels (every c[i] is [H][W]): the levels above 0, and level 0
+// too where enabled[0] is set (full-resolution a_0, S_0, c_0).
+cudaError_t launch_merge_samples(const MergeParams& p, float* out, cudaStream_t s);
 cudaError_t launch_blur(const BlurParams& p, cudaStream_t s);
 
 void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)

@@ -611,6 +611,84 @@ def test_stepwise_render_error_against_full_resolution_is_small():
     assert float(np.sqrt(np.mean((res["out"] - full) ** 2))) <= 1e-2
 
 
+# ----------------------------------------------------------------- sample-count levels (Sec. 6)
+
+def test_sample_levels_shade_blocks_of_listed_texels_with_thinned_tables():
+    """Level i >= 1 shades every pixel of each listed texel's 2^i x 2^i block at full
+    resolution: each equals full-resolution shading with every 2^i-th sample (a separate
+    code path), its AO is a multiple of 1 / ceil(N / 2^i), and no other pixel is written."""
+    fr = sg.gbuffer(5, 96, 72, 10, 3)
+    N = 48
+    cfg = cfg_for("ssao", 4, samples=N, sample_levels=1)
+    res = orc.render(fr, cfg)
+    for i in (1, 2, 3):
+        ci = res["c"][i][..., 0]
+        wl = res["lists"][i]
+        want = np.zeros(ci.shape, bool)
+        for e in wl:
+            qy, qx = int(e >> 16), int(e & 0xFFFF)
+            want[qy << i:(qy + 1) << i, qx << i:(qx + 1) << i] = True
+        assert np.array_equal(np.isfinite(ci), want), i
+        thin = orc.level_config(cfg, i)
+        assert thin["samples"] == -(-N // (1 << i))
+        full = orc.shade_full(fr, dict(thin, sample_levels=0))[..., 0]
+        assert np.array_equal(ci[want], full[want]), i
+        n_i = thin["samples"]
+        occ = (1.0 - ci[want].astype(np.float64)) * n_i
+        assert np.allclose(occ, np.round(occ), atol=1e-4), i
+
+
+def test_sample_levels_merge_gates_on_the_pixels_own_texel():
+    """Three levels, the coarsest 0.5; level 1 rendered (c = 1, a = 1, w = 1) on texel
+    columns 0..3 only.  Pixel x = 7 (texel 3) reads a_1 = 1 and becomes 1; pixel x = 8 sits
+    in texel 4, which was not rendered, so it keeps 0.5 although a_1 interpolates to 1/2
+    there.  The direct merge of level-resolution sub-images gives 0.75 at x = 8 (its c_1
+    is renormalised over the rendered tap)."""
+    H, W = 16, 24
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    w = [0.0, 1.0, 1.0, 0.0]
+    cfg_s = cfg_for("ssao", 3, weight=w, enabled=[0, 1, 1, 0], sample_levels=1)
+    a = [np.zeros((H, W)), np.zeros((8, 12)), np.ones((4, 6))]
+    S = [np.zeros((H, W), np.uint8), np.zeros((8, 12), np.uint8), np.ones((4, 6), np.uint8)]
+    a[1][:, :4] = 1.0
+    S[1][:, :4] = 1
+    full1 = np.full((H, W, 1), np.nan)
+    full1[:, :8] = 1.0
+    c_s = [np.full((H, W, 1), np.nan), full1, np.full((H, W, 1), 0.5)]
+    out = orc.merge(fr, cfg_s, a, S, c_s, "f64")[..., 0]
+    assert np.all(out[2:-2, 7] == 1.0) and np.all(out[2:-2, 8] == 0.5)
+    c1 = np.full((8, 12, 1), np.nan)
+    c1[:, :4] = 1.0
+    direct = orc.merge(fr, cfg_for("ssao", 3, weight=w, enabled=[0, 1, 1, 0]), a, S,
+                       [np.full((H, W, 1), np.nan), c1, np.full((4, 6, 1), 0.5)], "f64")[..., 0]
+    assert np.all(direct[2:-2, 8] == 0.75)
+
+
+def test_sample_levels_merge_constants_and_eq1():
+    H, W = 16, 16
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    cfg = cfg_for("ssao", 2, enabled=[1, 1, 0, 0], weight=[4.0, 1.0, 0, 0], sample_levels=1)
+    A, B = 0.25, 0.75
+    for a0 in (0.0, 0.05, 0.2, 0.3, 1.0):
+        a = [np.full((H, W), a0), np.ones((8, 8))]
+        S = [np.ones((H, W), np.uint8), np.ones((8, 8), np.uint8)]
+        out = orc.merge(fr, cfg, a, S, [np.full((H, W, 1), A), np.full((H, W, 1), B)], "f64")
+        alpha = min(4.0 * a0, 1.0)
+        assert np.allclose(out, A * alpha + B * (1 - alpha), rtol=1e-12, atol=1e-12)
+
+
+def test_sample_levels_with_one_sample_equal_full_resolution():
+    """With N = 1 every level keeps the same single sample, so every sub-image equals
+    full-resolution shading and the blend returns it (up to the rounding of Eq. (1))."""
+    fr = sg.gbuffer(7, 80, 60, 10, 3)
+    cfg = cfg_for("ssao", 4, samples=1, sample_levels=1)
+    res = orc.render(fr, cfg, "f64")
+    full = orc.shade_full(fr, cfg, "f64")
+    assert np.allclose(res["out"], full, rtol=0, atol=1e-12)
+    with pytest.raises(ValueError):
+        orc.render(fr, dict(cfg, blur=[0, 1, 1, 1]))
+
+
 # ----------------------------------------------------------------- sub-image blur (Sec. 4.1)
 
 BINOMIAL = np.array([1.0, 4.0, 6.0, 4.0, 1.0])
