@@ -440,6 +440,49 @@ def test_ssm_box_casts_umbra_and_penumbra():
     assert np.mean(hs[ground & (vis == 1)] == 1) > 0.99
 
 
+def test_ssm_penumbra_width_follows_similar_triangles():
+    """A half-plane occluder at light depth z_b over the ground (the left half of the
+    shadow map; its edge is the map's middle column, tangent coordinate 0).  PCSS must
+    leave a ground point fully dark or fully lit outside a band around the edge whose
+    half-width, in the light's tangent units at receiver depth z_r, is
+    R = (l/2)(z_r - z_b)/(z_b z_r) -- Fernando's similar triangles: a penumbra of world
+    width l (z_r - z_b)/z_b on the receiver -- and partly lit in the inner third of the
+    band.  Receiver positions come from the pinhole definitions here, not from the oracle."""
+    W, H, S = 160, 120, 512
+    fr = sg.gbuffer(0, W, H, 0, 0, shadow_size=S)        # ground plane only
+    zb, l = 6.0, 0.5
+    sm = np.full((S, S), sg.LIGHT_FAR, np.float32)
+    sm[:, : S // 2] = zb
+    fr.shadow_map = sm
+    cfg = _ssm_cfg()
+    assert cfg["light_size"] == l
+    vis = orc.shade_full(fr, cfg, "f64")[..., 0]
+    cam, L = fr.cam, fr.light
+    d = fr.depth.astype(np.float64)
+    th = float(cam.tan_half_fov)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    sx = ((x + 0.5) / W * 2.0 - 1.0) * th * (W / H)
+    sy = (1.0 - (y + 0.5) / H * 2.0) * th
+    e, r, u, f = (np.asarray(v, np.float64) for v in (cam.eye, cam.right, cam.up, cam.forward))
+    world = e + (sx * d)[..., None] * r + (sy * d)[..., None] * u + d[..., None] * f
+    rel = world - np.asarray(L.eye, np.float64)
+    zr = rel @ np.asarray(L.forward, np.float64)
+    ut = (rel @ np.asarray(L.right, np.float64)) / zr
+    vt = (rel @ np.asarray(L.up, np.float64)) / zr
+    R = (l / 2) * (zr - zb) / (zb * zr)
+    tl = float(L.tan_half_fov)
+    ground = (fr.depth < cam.far) & (np.abs(ut) < 0.8 * tl) & (np.abs(vt) < 0.8 * tl)
+    dark = ground & (ut < -R * (1 + 1e-3))
+    lit = ground & (ut > R * (1 + 1e-3))
+    inner = ground & (np.abs(ut) < R / 3)
+    assert dark.sum() > 100 and lit.sum() > 100 and inner.sum() > 10
+    assert np.all(vis[dark] == 0.0)
+    assert np.all(vis[lit] == 1.0)
+    assert np.all((vis[inner] > 0.0) & (vis[inner] < 1.0))
+    # the band is really as wide as the formula: halving it would misclassify pixels
+    assert np.any((vis > 0) & (vis < 1) & ground & (np.abs(ut) > R / 2))
+
+
 # ----------------------------------------------------------------- blending (Sec. 4.2, Eq. 1)
 
 def _levels_like(H, W, L, fill):
