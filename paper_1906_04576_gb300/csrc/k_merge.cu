@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __re
 // alpha = min(w_i a_i(q), 1) and, if alpha > 0, comp = c_i alpha + up (1 - alpha).
 // SRC_SUB: the previous composite is the coarsest sub-image itself (storage type CT);
 // otherwise float / float4 as written here.
-constexpr int CH_TX = 32, CH_TY = 8, CH_R = 4;  // chain CTA: 32 x 8 threads, 4 rows per thread
+constexpr int CH_TX = 32, CH_TY = 8;  // chain CTA: 32 x 8 threads, CH_R rows per thread
 
-template <typename CT, int C, bool SRC_SUB>
+template <typename CT, int C, bool SRC_SUB, int CH_R>
 __global__ void __launch_bounds__(CH_TX* CH_TY) chain_kernel(ChainParams p) {
   const int qx = blockIdx.x * CH_TX + threadIdx.x;
   if (qx >= p.Wi) return;
@@ -467,13 +467,35 @@ __global__ void __launch_bounds__(CH_TX* CH_TY) chain_kernel(ChainParams p) {
   }
 }
 
+template <typename CT, int C, int R>
+void launch_chain_r(const ChainParams& p, cudaStream_t s) {
+  dim3 grid((p.Wi + CH_TX - 1) / CH_TX, (p.Hi + CH_TY * R - 1) / (CH_TY * R)), block(CH_TX, CH_TY);
+  if (p.src_sub)
+    chain_kernel<CT, C, true, R><<<grid, block, 0, s>>>(p);
+  else
+    chain_kernel<CT, C, false, R><<<grid, block, 0, s>>>(p);
+}
+
+// Four rows per thread where the level fills the GPU with CTAs to spare; one row per
+// thread for the small levels, which would otherwise run a fraction of a wave.
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
 template <typename CT, int C>
 void launch_chain_t(const ChainParams& p, cudaStream_t s) {
-  dim3 grid((p.Wi + CH_TX - 1) / CH_TX, (p.Hi + CH_TY * CH_R - 1) / (CH_TY * CH_R)), block(CH_TX, CH_TY);
-  if (p.src_sub)
-    chain_kernel<CT, C, true><<<grid, block, 0, s>>>(p);
+  const long blocks4 = (long)((p.Wi + CH_TX - 1) / CH_TX) * ((p.Hi + CH_TY * 4 - 1) / (CH_TY * 4));
+  if (blocks4 >= 4L * sm_count())
+    launch_chain_r<CT, C, 4>(p, s);
   else
-    chain_kernel<CT, C, false><<<grid, block, 0, s>>>(p);
+    launch_chain_r<CT, C, 1>(p, s);
 }
 
 // Blend of sample-count levels (Sec. 6): every sub-image is [H][W], so only the masks
