@@ -388,10 +388,19 @@ const char* mrr_last_error(mrr_ctx* ctx);
 
 /* Device-side fault bits of the context: kernels that wait on asynchronous tile loads
  * give up after about a second and record a bit here instead of waiting for ever (bit 0:
- * edge detection, bit 1: upsample/merge); their output for that frame is then invalid.
- * Synchronises the device, copies the word to *flags and, if `clear` is nonzero, resets
- * it.  Not part of the paper's method; it makes a stalled load visible to the host. */
+ * edge detection; bit 30: mrr_check_wait_timeout); the output of a frame whose edge
+ * loads gave up is invalid.  Synchronises the device, copies the word to *flags and, if
+ * `clear` is nonzero, resets it.  Not part of the paper's method; it makes a stalled load
+ * visible to the host. */
 mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear);
+
+/* Self-check of that failure path: runs one CTA that waits, with the edge kernel's
+ * bounded wait, on an mbarrier phase that expects 16 bytes of transactions no copy will
+ * ever bring.  The wait gives up after about a second of SM clocks, the kernel records
+ * bit 30 in the context's fault word and returns -- no fault, no hang, the context stays
+ * usable.  Synchronises the device before and after; copies the fault word (not cleared)
+ * to *flags.  Takes about one second. */
+mrr_status mrr_check_wait_timeout(mrr_ctx* ctx, uint32_t* flags);
 
 /* Diagnostic: the effect kernels project sample points with their own correctly rounded
  * reciprocal (Newton-Raphson refinement of the hardware estimate) instead of IEEE

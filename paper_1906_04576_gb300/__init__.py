@@ -158,6 +158,7 @@ _lib.mrr_masks_static.restype = ctypes.c_int
 _lib.mrr_kernel_launches.argtypes = []
 _lib.mrr_kernel_launches.restype = ctypes.c_uint64
 _lib.mrr_fault_flags.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+_lib.mrr_check_wait_timeout.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32)]
 _lib.mrr_check_reciprocal.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
@@ -587,6 +588,12 @@ def mrr_check_reciprocal(first_bits: int, last_bits: int) -> int:
     n = ctypes.c_uint64(0)
     _check(None, _lib.mrr_check_reciprocal(first_bits, last_bits, ctypes.byref(n)))
     return int(n.value)
+
+
+def mrr_check_wait_timeout(ctx: Context) -> int:
+    f = ctypes.c_uint32(0)
+    _check(ctx, _lib.mrr_check_wait_timeout(ctx.handle, ctypes.byref(f)))
+    return int(f.value)
 
 
 def mrr_fault_flags(ctx: Context, clear: bool = False) -> int:

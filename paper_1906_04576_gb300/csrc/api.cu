@@ -848,6 +848,15 @@ mrr_status mrr_fault_flags(mrr_ctx* ctx, uint32_t* flags, int clear) {
   return MRR_OK;
 }
 
+mrr_status mrr_check_wait_timeout(mrr_ctx* ctx, uint32_t* flags) {
+  if (!ctx || !flags) return MRR_EINVAL;
+  MRR_CUDA(ctx, cudaDeviceSynchronize());
+  MRR_CUDA(ctx, launch_check_wait(ctx->fault, nullptr));
+  MRR_CUDA(ctx, cudaDeviceSynchronize());
+  MRR_CUDA(ctx, cudaMemcpy(flags, ctx->fault, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  return MRR_OK;
+}
+
 mrr_status mrr_edges(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* edges_dev, void* stream) {
   if (!ctx) return MRR_EINVAL;
   mrr_status st = check_gbuffer(ctx, g);

@@ -361,6 +361,26 @@ bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* norma
 
 }  // namespace
 
+// The bounded-wait self-check: one thread arms an mbarrier phase that expects 16 bytes of
+// transactions which no copy will ever bring, then waits for it exactly as the edge
+// kernel waits for its tiles.  The wait gives up after WAIT_CYCLES (about a second) and
+// the kernel records FAULT_CHECK_WAIT and returns; nothing faults and nothing hangs.
+__global__ void check_wait_kernel(uint32_t* fault) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_arrive_expect_tx(&bar, 16u);
+    if (!mbar_wait(&bar, 0u)) atomicOr(fault, FAULT_CHECK_WAIT);
+  }
+}
+
+cudaError_t launch_check_wait(uint32_t* fault, cudaStream_t s) {
+  check_wait_kernel<<<1, 32, 0, s>>>(fault);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 void edges_prepare() {
   edges_tma_grid<float4>();
   edges_tma_grid<half4>();

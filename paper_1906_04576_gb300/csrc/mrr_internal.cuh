@@ -225,6 +225,9 @@ cudaError_t launch_chain(const ChainParams& p, cudaStream_t s);
 // too where enabled[0] is set (full-resolution a_0, S_0, c_0).
 cudaError_t launch_merge_samples(const MergeParams& p, float* out, cudaStream_t s);
 cudaError_t launch_blur(const BlurParams& p, cudaStream_t s);
+// One CTA that waits, as the TMA edge kernel does, on an mbarrier phase nothing will
+// complete, and records the timeout in *fault (tma.cuh's FAULT_CHECK_WAIT).
+cudaError_t launch_check_wait(uint32_t* fault, cudaStream_t s);
 
 void edges_prepare();     // one-time launch set-up of the edge kernels (before any stream capture)
 int shade_grid_blocks();  // grid multiplier base of the work-list kernel (grid = multiple of its resident CTAs)

@@ -13,7 +13,8 @@ namespace mrr {
 
 // Fault bits a kernel records in the context's device fault word.
 enum : uint32_t {
-  FAULT_EDGES_WAIT = 1u << 0,  // an edge-detection tile load did not complete in time
+  FAULT_EDGES_WAIT = 1u << 0,   // an edge-detection tile load did not complete in time
+  FAULT_CHECK_WAIT = 1u << 30,  // the self-check's deliberately unanswered wait gave up
 };
 
 constexpr long long WAIT_CYCLES = 2000000000LL;

@@ -144,6 +144,21 @@ def test_ssao_ragged_sizes(mrr, W, H, seed):
     check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=64))
 
 
+@pytest.mark.parametrize("W,H", [(16384, 40), (40, 16384), (16383, 9)])
+def test_maximum_dimension_frames(mrr, W, H):
+    """Frames at the largest supported width or height (16384): work-list coordinates use
+    all 14 bits of their 16-bit fields, the TMA edge kernel walks 512 tiles along a row,
+    and a width one below the limit takes the edge kernel without TMA."""
+    fr = sg.gbuffer(W % 97 + H, W, H, 24, 8)
+    check_frame(mrr, fr, make_cfg("ssao", 4, W, H, samples=16), check_full=False)
+
+
+def test_dimension_limit_is_enforced(mrr):
+    with pytest.raises(mrr.MrrError) as ei:
+        mrr.mrr_create(make_cfg("ssao", 4, 16385, 8))
+    assert ei.value.status == mrr.MRR_EINVAL
+
+
 @pytest.mark.parametrize("sigma2", [[0.5, 1.0, 2.5, 0.0], [0.3, 0.924, 3.696, 0.0], [1.848, 3.696, 0.924, 0.0]])
 def test_masks_other_radii(mrr, sigma2):
     """Radii other than Table 1's (3, 5, 6) take the mask kernel that carries every radius;
