@@ -734,7 +734,8 @@ def main():
             "config": {"workload": args.workload, "width": W, "height": H, "effect": cfg["effect"],
                        "samples": cfg.get("samples"), "levels": cfg["num_levels"], "precision": prec,
                        "blur": cfg.get("blur", [0, 0, 0, 0]),
-                       "merge": "step-wise (Sec. 3.3)" if cfg.get("merge_mode", 0) == 1 else "direct (Sec. 4.2)",
+                       "merge": {0: "direct (Sec. 4.2)", 1: "step-wise (Sec. 3.3)",
+                                 2: "direct, bilateral taps (Sec. 3.3)"}[cfg.get("merge_mode", 0)],
                        "levels_kind": "sample-count (Sec. 6)" if cfg.get("sample_levels", 0) else "resolution",
                        "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
                                 f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",

@@ -97,7 +97,8 @@ typedef struct mrr_config {
                                      enabled levels i >= 1 (level 0 is the full-resolution image) */
   float blur_depth_rel;           /* the blur's depth test: |d' - d| <= blur_depth_rel * d; >= 0, finite */
   int merge_mode;                 /* 0: direct upsampling of every level (Sec. 4.2); 1: step-wise
-                                     chain (Sec. 3.3), see mrr_upsample_merge */
+                                     chain (Sec. 3.3), see mrr_upsample_merge; 2: direct upsampling
+                                     with bilateral taps (Sec. 3.3), see mrr_upsample_merge_bilateral */
   int sample_levels;              /* 1: sample-count levels (Sec. 6): levels above 0 are rendered at full
                                      resolution with fewer samples instead of at a lower resolution (see
                                      mrr_shade_level); requires blur all 0 and merge_mode 0 */
@@ -230,6 +231,16 @@ mrr_status mrr_blur_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const m
  * [H][W] float, or [H][W] float4 (rgb + 0) for MRR_SSGI. */
 mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c_levels_dev, float* out_dev,
                               void* stream);
+
+/* Sec. 3.3 (bilateral upsampling, after Tomasi and Manduchi): mrr_upsample_merge for a
+ * context with cfg.merge_mode = 2, which needs the frame's depth (g->depth; the other
+ * planes of g are not read).  As the direct merge, except that c_i is interpolated over
+ * the rendered taps Q whose sample depth lies on the pixel's surface,
+ *   |d(s_i(Q)) - d(p)| <= cfg.blur_depth_rel * d(p),
+ * and over every rendered tap when none does; a_i stays plain bilinear.  mrr_upsample_merge
+ * itself returns MRR_EINVAL for such a context; mrr_render passes the depth itself. */
+mrr_status mrr_upsample_merge_bilateral(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv,
+                                        void* const* c_levels_dev, float* out_dev, void* stream);
 
 /* The whole method for one frame on one stream: edges, masks, work lists, all
  * sub-images, the blur of the levels cfg.blur names, blend -- using the context's pools

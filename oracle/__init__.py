@@ -81,6 +81,7 @@ def _L():
             getattr(lib, f"orc_blur_level_{suf}").argtypes = [P, vp, ci, vp, vp, vp]
             getattr(lib, f"orc_merge_stepwise_{suf}").argtypes = [P, vp, vp, vp, vp]
             getattr(lib, f"orc_merge_samples_{suf}").argtypes = [P, vp, vp, vp, vp]
+            getattr(lib, f"orc_merge_bilateral_{suf}").argtypes = [P, vp, vp, vp, vp, vp]
             getattr(lib, f"orc_shade_blocks_{suf}").argtypes = [P, vp, vp, vp, vp, ci, vp, ci, vp]
         lib.orc_gauss_weights_f32.argtypes = [ctypes.c_double, vp]
         lib.orc_gauss_weights_f64.argtypes = [ctypes.c_double, vp]
@@ -316,15 +317,20 @@ def shade_blocks(frame, cfg, level, worklist, precision="f32"):
 
 
 def merge(frame, cfg, a, S, c, precision="f32"):
-    """Eq. (1): direct upsampling of every level (Sec. 4.2), or with cfg["merge_mode"] = 1
-    the step-wise chain of Sec. 3.3; with cfg["sample_levels"] = 1 the full-resolution
-    sub-images of sample-count levels (Sec. 6)."""
+    """Eq. (1): direct upsampling of every level (Sec. 4.2); with cfg["merge_mode"] = 1 the
+    step-wise chain of Sec. 3.3, with 2 the direct upsampling with bilateral (depth-aware)
+    taps; with cfg["sample_levels"] = 1 the full-resolution sub-images of sample-count
+    levels (Sec. 6)."""
     b = _Bound(frame, cfg)
     dt = _dtype(precision)
     a = [np.ascontiguousarray(x, dt) for x in a]
     S = [np.ascontiguousarray(x, np.uint8) for x in S]
     c = [np.ascontiguousarray(x, dt) for x in c]
     out = np.zeros((frame.height, frame.width, channels(cfg)), dt)
+    if cfg.get("merge_mode", 0) == 2 and not cfg.get("sample_levels", 0):
+        getattr(_L(), f"orc_merge_bilateral_{_suffix(precision)}")(b.ref, _ptr(b.depth), _ptr_array(a),
+                                                                   _ptr_array(S), _ptr_array(c), _ptr(out))
+        return out
     if cfg.get("sample_levels", 0):
         fn = "orc_merge_samples"
     else:

@@ -64,7 +64,8 @@ struct orc_params {
   int shadow_size;       // S, shadow map is S x S
   int blur[4];           // 1: level i's sub-image gets the bilateral blur of Sec. 4.1
   float blur_depth_rel;  // that blur's depth test: |d' - d| <= blur_depth_rel * d
-  int merge_mode;        // 0: direct upsampling (Sec. 4.2); 1: step-wise chain (Sec. 3.3)
+  int merge_mode;        // 0: direct upsampling (Sec. 4.2); 1: step-wise chain (Sec. 3.3);
+                         // 2: direct upsampling with depth-aware (bilateral) taps (Sec. 3.3)
   int sample_levels;     // 1: levels above 0 at full resolution with fewer samples (Sec. 6)
 };
 
@@ -747,6 +748,71 @@ void merge(const orc_params& p, T* const* a, uint8_t* const* S, T* const* c, T* 
   }
 }
 
+// Direct upsampling with bilateral taps (Sec. 3.3 cites Tomasi and Manduchi's bilateral
+// filter for upsampling without mixing in unrelated pixels).  As merge above, except that
+// c_i is interpolated over the rendered taps that also lie on the pixel's surface:
+// tap k (texel Q_k) takes weight w_k when S_i(Q_k) = 1 and
+//   |d(s_i(Q_k)) - d(p)| <= blur_depth_rel * d(p),
+// d the full-resolution depth (the blur's depth test); when no tap passes, the rendered
+// taps are used as in merge.  a_i stays plain bilinear.  depth is [H][W].
+template <typename T>
+void merge_bilateral(const orc_params& p, const float* depth, T* const* a, uint8_t* const* S, T* const* c,
+                     T* out) {
+  const int W = p.width, H = p.height, L = p.num_levels, C = channels(p);
+  const T rel = (T)p.blur_depth_rel;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      const T dp = (T)depth[(size_t)y * W + x];
+      T cp[3] = {T(0), T(0), T(0)};
+      bool first = true;
+      for (int i = L - 1; i >= 0; --i) {
+        if (!p.enabled[i]) continue;
+        const int Wi = level_dim(W, i), Hi = level_dim(H, i);
+        const T scale = (T)(1 << i);
+        T ux = (T)(x - level_origin(i)) / scale;
+        T uy = (T)(y - level_origin(i)) / scale;
+        int x0 = (int)std::floor(ux), y0 = (int)std::floor(uy);
+        T fx = ux - (T)x0, fy = uy - (T)y0;
+        int xs[2] = {std::min(std::max(x0, 0), Wi - 1), std::min(std::max(x0 + 1, 0), Wi - 1)};
+        int ys[2] = {std::min(std::max(y0, 0), Hi - 1), std::min(std::max(y0 + 1, 0), Hi - 1)};
+        T w[4] = {(T(1) - fx) * (T(1) - fy), fx * (T(1) - fy), (T(1) - fx) * fy, fx * fy};
+        int tx[4] = {xs[0], xs[1], xs[0], xs[1]}, ty[4] = {ys[0], ys[0], ys[1], ys[1]};
+        T ahat = T(0);
+        for (int k = 0; k < 4; ++k) ahat = ahat + w[k] * a[i][(size_t)ty[k] * Wi + tx[k]];
+        T alpha = std::min((T)p.weight[i] * ahat, T(1));
+        if (!first && !(alpha > T(0))) continue;
+        T num[3] = {T(0), T(0), T(0)}, den = T(0);
+        T numb[3] = {T(0), T(0), T(0)}, denb = T(0);
+        for (int k = 0; k < 4; ++k) {
+          const size_t q = (size_t)ty[k] * Wi + tx[k];
+          if (!S[i][q]) continue;
+          for (int ch = 0; ch < C; ++ch) num[ch] = num[ch] + w[k] * c[i][q * C + ch];
+          den = den + w[k];
+          const T dq = (T)depth[(size_t)level_sample(ty[k], i, H) * W + level_sample(tx[k], i, W)];
+          if (!(std::fabs(dq - dp) <= rel * dp)) continue;
+          for (int ch = 0; ch < C; ++ch) numb[ch] = numb[ch] + w[k] * c[i][q * C + ch];
+          denb = denb + w[k];
+        }
+        if (denb > T(0)) {
+          for (int ch = 0; ch < C; ++ch) num[ch] = numb[ch];
+          den = denb;
+        }
+        if (first) {
+          for (int ch = 0; ch < C; ++ch) cp[ch] = num[ch] / den;
+          first = false;
+          continue;
+        }
+        for (int ch = 0; ch < C; ++ch) {
+          T chat = num[ch] / den;
+          cp[ch] = chat * alpha + cp[ch] * (T(1) - alpha);
+        }
+      }
+      for (int ch = 0; ch < C; ++ch) out[((size_t)y * W + x) * C + ch] = cp[ch];
+    }
+  }
+}
+
 // Step-wise blending (Sec. 3.3), the alternative to the direct upsampling above: the
 // sub-images are merged from the coarsest upwards, each finer enabled level i blended,
 // at its own resolution, with the composite of the levels below it scaled up to level
@@ -916,6 +982,10 @@ int orc_gauss_weights_f64(double sigma2, double* g) { return gauss_weights<doubl
   }                                                                                                          \
   void orc_merge_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) {          \
     merge<T>(*p, a, S, c, out);                                                                              \
+  }                                                                                                          \
+  void orc_merge_bilateral_##SUF(const orc_params* p, const float* depth, T* const* a, uint8_t* const* S,   \
+                                 T* const* c, T* out) {                                                       \
+    merge_bilateral<T>(*p, depth, a, S, c, out);                                                             \
   }                                                                                                          \
   void orc_shade_blocks_##SUF(const orc_params* p, const float* depth, const float* normal,                  \
                               const float* color, const float* smap, int level, const uint32_t* list, int n,\

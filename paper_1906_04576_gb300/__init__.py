@@ -150,6 +150,8 @@ _lib.mrr_edges.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_masks.argtypes = [_vp, _vp, ctypes.POINTER(mrr_levels), _vp]
 _lib.mrr_shade_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp]
 _lib.mrr_upsample_merge.argtypes = [_vp, ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp, _vp]
+_lib.mrr_upsample_merge_bilateral.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels),
+                                              ctypes.POINTER(_vp), _vp, _vp]
 _lib.mrr_blur_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), _vp, _vp,
                                 _vp]
 _lib.mrr_shade_levels.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), ctypes.POINTER(mrr_levels), ctypes.POINTER(_vp), _vp]
@@ -164,7 +166,7 @@ _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 for _fn in ("mrr_level_dims", "mrr_create", "mrr_edges", "mrr_masks", "mrr_shade_level", "mrr_shade_levels",
-            "mrr_upsample_merge", "mrr_blur_level",
+            "mrr_upsample_merge", "mrr_upsample_merge_bilateral", "mrr_blur_level",
             "mrr_render", "mrr_render_full", "mrr_render_host"):
     getattr(_lib, _fn).restype = ctypes.c_int
 
@@ -607,6 +609,14 @@ def mrr_upsample_merge(ctx: Context, levels: Levels, c_list: list, out: torch.Te
     lv = levels.struct()
     arr = (_vp * MAX_LEVELS)(*[(_ptr(c) if c is not None else None) for c in c_list])
     _check(ctx, _lib.mrr_upsample_merge(ctx.handle, ctypes.byref(lv), arr, _ptr(out), _stream(stream)))
+
+
+def mrr_upsample_merge_bilateral(ctx: Context, frame: DeviceFrame, levels: Levels, c_list: list,
+                                 out: torch.Tensor, stream=None) -> None:
+    g, lv = frame.struct(), levels.struct()
+    arr = (_vp * MAX_LEVELS)(*[(_ptr(c) if c is not None else None) for c in c_list])
+    _check(ctx, _lib.mrr_upsample_merge_bilateral(ctx.handle, ctypes.byref(g), ctypes.byref(lv), arr, _ptr(out),
+                                                  _stream(stream)))
 
 
 def mrr_render(ctx: Context, frame: DeviceFrame, out: torch.Tensor, stream=None) -> None:

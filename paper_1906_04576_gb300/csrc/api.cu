@@ -406,9 +406,29 @@ mrr_status chain_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
 }
 
 mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
-                      bool compact_level0 = false) {
+                      bool compact_level0 = false, const float* depth = nullptr) {
   const mrr_config& cf = ctx->cfg;
-  if (cf.merge_mode == 1 && cf.num_levels > 1) {
+  if (cf.merge_mode == 2 && !cf.sample_levels) {
+    if (!depth) return fail(ctx, MRR_EINVAL, "the bilateral merge needs the frame's depth");
+    MergeParams mp;
+    std::memset(&mp, 0, sizeof mp);
+    mp.W = lv->width[0];
+    mp.H = lv->height[0];
+    mp.L = cf.num_levels;
+    mp.C = channels(cf);
+    mp.half_store = cf.precision == MRR_FP16;
+    for (int i = 0; i < cf.num_levels; ++i) {
+      mp.enabled[i] = cf.enabled[i];
+      mp.Wi[i] = lv->width[i];
+      mp.Hi[i] = lv->height[i];
+      mp.weight[i] = cf.weight[i];
+      mp.alpha[i] = lv->alpha[i];
+      mp.stencil[i] = lv->stencil[i];
+      mp.c[i] = c[i];
+    }
+    if (compact_level0) mp.enabled[0] = 0;  // blended afterwards from level 0's list
+    MRR_CUDA(ctx, launch_merge_bilateral(mp, depth, cf.blur_depth_rel, out, s));
+  } else if (cf.merge_mode == 1 && cf.num_levels > 1) {
     mrr_status st = chain_impl(ctx, lv, c, out, s, compact_level0);
     if (st != MRR_OK) return st;
   } else if (cf.sample_levels && cf.num_levels > 1) {
@@ -633,7 +653,7 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   void* cm[MRR_MAX_LEVELS];
   st = blur_pools(ctx, g, &lv, cm, s);
   if (st != MRR_OK) return st;
-  return merge_impl(ctx, &lv, cm, out, s, true);
+  return merge_impl(ctx, &lv, cm, out, s, true, g->depth);
 }
 
 // One level only (level 0 is the coarsest): edges, masks, compaction, shading, merge.
@@ -659,7 +679,7 @@ mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out
   sl.counts = ctx->counts;
   MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
                                     ctx->split_texel, s));
-  return merge_impl(ctx, &lv, ctx->cbuf, out, s);
+  return merge_impl(ctx, &lv, ctx->cbuf, out, s, false, g->depth);
 }
 
 void free_pools(mrr_ctx* ctx) {
@@ -768,7 +788,7 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
     if (c.blur[i] && (i == 0 || i >= c.num_levels || !c.enabled[i])) return MRR_EINVAL;
   }
   if (!(c.blur_depth_rel >= 0.f) || !(c.blur_depth_rel <= FLT_MAX)) return MRR_EINVAL;
-  if (c.merge_mode != 0 && c.merge_mode != 1) return MRR_EINVAL;
+  if (c.merge_mode < 0 || c.merge_mode > 2) return MRR_EINVAL;
   if (c.sample_levels != 0 && c.sample_levels != 1) return MRR_EINVAL;
   if (c.sample_levels) {  // full-resolution sub-images: no level blur, direct blend only
     if (c.merge_mode != 0) return MRR_EINVAL;
@@ -1084,7 +1104,7 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     for (int k = 0; k < n; ++k) {
       void* cm[MRR_MAX_LEVELS];
       mrr_status st = blur_pools(ctxs[k], &frames[k], &lv[k], cm, s);
-      if (st == MRR_OK) st = merge_impl(ctxs[k], &lv[k], cm, outs[k], s, framed[k]);
+      if (st == MRR_OK) st = merge_impl(ctxs[k], &lv[k], cm, outs[k], s, framed[k], frames[k].depth);
       if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
     }
   }
@@ -1359,7 +1379,29 @@ mrr_status mrr_upsample_merge(mrr_ctx* ctx, const mrr_levels* lv, void* const* c
   if (ctx->cfg.merge_mode == 1 && !fits_pools(ctx, lv->width[0], lv->height[0]))
     return fail(ctx, MRR_EINVAL, "step-wise blending: frame %dx%d exceeds the context's max size", lv->width[0],
                 lv->height[0]);
+  if (ctx->cfg.merge_mode == 2 && !ctx->cfg.sample_levels)
+    return fail(ctx, MRR_EINVAL, "the bilateral merge needs the frame's depth: mrr_upsample_merge_bilateral");
   return merge_impl(ctx, lv, c_levels_dev, out_dev, (cudaStream_t)stream);
+}
+
+mrr_status mrr_upsample_merge_bilateral(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels* lv,
+                                        void* const* c_levels_dev, float* out_dev, void* stream) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, g);
+  if (st != MRR_OK) return st;
+  st = check_levels(ctx, lv, false);
+  if (st != MRR_OK) return st;
+  if (ctx->cfg.merge_mode != 2 || ctx->cfg.sample_levels)
+    return fail(ctx, MRR_EINVAL, "mrr_upsample_merge_bilateral needs merge_mode 2");
+  if (lv->width[0] != g->width || lv->height[0] != g->height)
+    return fail(ctx, MRR_EINVAL, "levels are for %dx%d, frame is %dx%d", lv->width[0], lv->height[0], g->width,
+                g->height);
+  if (!c_levels_dev || !out_dev) return fail(ctx, MRR_EINVAL, "c_levels_dev / out_dev is NULL");
+  for (int i = 0; i < ctx->cfg.num_levels; ++i)
+    if (ctx->cfg.enabled[i] && (!c_levels_dev[i] || !aligned(c_levels_dev[i], cbytes(ctx->cfg))))
+      return fail(ctx, MRR_EINVAL, "sub-image %d is NULL or misaligned", i);
+  if (!aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4)) return fail(ctx, MRR_EINVAL, "out_dev misaligned");
+  return merge_impl(ctx, lv, c_levels_dev, out_dev, (cudaStream_t)stream, false, g->depth);
 }
 
 mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream) {

@@ -19,6 +19,7 @@
 // chain_kernel: the step-wise reading of Sec. 3.3 instead -- one launch per step, each
 // level's composite computed at its own resolution from the previous one.
 // merge_samples_kernel: the blend of sample-count levels (full-resolution sub-images).
+// merge_bilateral_kernel: the direct merge with depth-aware (bilateral) taps.
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -545,6 +546,88 @@ __global__ void __launch_bounds__(256) merge_samples_kernel(MergeParams p, float
     out[pix] = c0;
 }
 
+// Direct upsampling with bilateral taps (merge_mode 2): merge_kernel's arithmetic per
+// pixel, except that c_i is interpolated over the rendered taps that lie on the pixel's
+// surface, |d(s_i(Q)) - d(p)| <= rel * d(p), falling back to every rendered tap when none
+// does.  One pixel per thread; the taps are read from global memory (L1 / L2).
+template <typename CT, int C>
+__global__ void __launch_bounds__(256) merge_bilateral_kernel(MergeParams p, const float* __restrict__ depth,
+                                                               float rel, float* __restrict__ out) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= p.W || y >= p.H) return;
+  const size_t pix = (size_t)y * p.W + x;
+  const float dp = __ldg(depth + pix);
+  const float thr = rel * dp;
+  float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  bool first = true;
+  for (int i = p.L - 1; i >= 0; --i) {
+    if (!p.enabled[i]) continue;
+    const int Wi = p.Wi[i], Hi = p.Hi[i];
+    const int o = i == 0 ? 0 : 1 << (i - 1), mask = (1 << i) - 1;
+    const float inv = __int_as_float((127 - i) << 23);  // 2^-i
+    const int nx = x - o, ny = y - o;
+    const int x0 = nx >> i, y0 = ny >> i;
+    const float fx = (float)(nx & mask) * inv, fy = (float)(ny & mask) * inv;
+    const int xs[2] = {min(max(x0, 0), Wi - 1), min(max(x0 + 1, 0), Wi - 1)};
+    const int ys[2] = {min(max(y0, 0), Hi - 1), min(max(y0 + 1, 0), Hi - 1)};
+    const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
+    const int tx[4] = {xs[0], xs[1], xs[0], xs[1]}, ty[4] = {ys[0], ys[0], ys[1], ys[1]};
+    float ahat = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ahat = ahat + w[k] * __ldg(p.alpha[i] + (size_t)ty[k] * Wi + tx[k]);
+    const float wa = p.weight[i] * ahat;
+    const float alpha = (1.0f < wa) ? 1.0f : wa;
+    if (!first && !(alpha > 0.0f)) continue;
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, denb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const size_t q = (size_t)ty[k] * Wi + tx[k];
+      if (!__ldg(p.stencil[i] + q)) continue;
+      const float3 v = load_c<CT>(p.c[i], q, C);
+      n0 = n0 + w[k] * v.x;
+      if (C == 4) {
+        n1 = n1 + w[k] * v.y;
+        n2 = n2 + w[k] * v.z;
+      }
+      den = den + w[k];
+      const int sx = min((tx[k] << i) + o, p.W - 1), sy = min((ty[k] << i) + o, p.H - 1);
+      const float dq = __ldg(depth + (size_t)sy * p.W + sx);
+      if (!(fabsf(dq - dp) <= thr)) continue;
+      b0 = b0 + w[k] * v.x;
+      if (C == 4) {
+        b1 = b1 + w[k] * v.y;
+        b2 = b2 + w[k] * v.z;
+      }
+      denb = denb + w[k];
+    }
+    if (denb > 0.0f) {
+      n0 = b0;
+      n1 = b1;
+      n2 = b2;
+      den = denb;
+    }
+    if (first) {
+      c0 = n0 / den;
+      if (C == 4) {
+        c1 = n1 / den;
+        c2 = n2 / den;
+      }
+      first = false;
+      continue;
+    }
+    const float om = 1.0f - alpha;
+    c0 = (n0 / den) * alpha + c0 * om;
+    if (C == 4) {
+      c1 = (n1 / den) * alpha + c1 * om;
+      c2 = (n2 / den) * alpha + c2 * om;
+    }
+  }
+  if (C == 4)
+    reinterpret_cast<float4*>(out)[pix] = make_float4(c0, c1, c2, 0.0f);
+  else
+    out[pix] = c0;
+}
+
 template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
   dim3 grid((p.W + MTX - 1) / MTX, (p.H + MTY - 1) / MTY);
@@ -602,6 +685,19 @@ cudaError_t launch_merge_samples(const MergeParams& p, float* out, cudaStream_t 
   } else {
     if (p.half_store) merge_samples_kernel<__half, 1><<<grid, block, 0, s>>>(p, out);
     else merge_samples_kernel<float, 1><<<grid, block, 0, s>>>(p, out);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_bilateral(const MergeParams& p, const float* depth, float rel, float* out, cudaStream_t s) {
+  dim3 grid((p.W + 31) / 32, (p.H + 7) / 8), block(32, 8);
+  if (p.C == 4) {
+    if (p.half_store) merge_bilateral_kernel<__half, 4><<<grid, block, 0, s>>>(p, depth, rel, out);
+    else merge_bilateral_kernel<float, 4><<<grid, block, 0, s>>>(p, depth, rel, out);
+  } else {
+    if (p.half_store) merge_bilateral_kernel<__half, 1><<<grid, block, 0, s>>>(p, depth, rel, out);
+    else merge_bilateral_kernel<float, 1><<<grid, block, 0, s>>>(p, depth, rel, out);
   }
   count_launches(1);
   return cudaGetLastError();

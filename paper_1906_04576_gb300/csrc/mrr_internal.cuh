@@ -224,6 +224,9 @@ cudaError_t launch_chain(const ChainParams& p, cudaStream_t s);
 // Blend of sample-count levels (every c[i] is [H][W]): the levels above 0, and level 0
 // too where enabled[0] is set (full-resolution a_0, S_0, c_0).
 cudaError_t launch_merge_samples(const MergeParams& p, float* out, cudaStream_t s);
+// The direct merge with bilateral taps: c_i over the rendered taps whose sample depth is
+// within rel * d(p) of the pixel's depth (all rendered taps when none is).
+cudaError_t launch_merge_bilateral(const MergeParams& p, const float* depth, float rel, float* out, cudaStream_t s);
 cudaError_t launch_blur(const BlurParams& p, cudaStream_t s);
 // One CTA that waits, as the TMA edge kernel does, on an mbarrier phase nothing will
 // complete, and records the timeout in *fault (tma.cuh's FAULT_CHECK_WAIT).

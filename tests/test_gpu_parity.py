@@ -74,7 +74,10 @@ def run_staged(mrr, ctx, dev, W, H, L):
             b = torch.full_like(subs[i], float("nan"))
             mrr.mrr_blur_level(ctx, i, dev, levels, subs[i], b)
             subs[i] = b
-    mrr.mrr_upsample_merge(ctx, levels, subs, out)
+    if ctx.config.get("merge_mode", 0) == 2:      # the bilateral merge reads the frame's depth
+        mrr.mrr_upsample_merge_bilateral(ctx, dev, levels, subs, out)
+    else:
+        mrr.mrr_upsample_merge(ctx, levels, subs, out)
     torch.cuda.synchronize()
     return edges, levels, subs, out
 

@@ -1,7 +1,7 @@
 """Seeded random configurations against the oracle: frame size, effect, number of levels
 and which of them are enabled, blur variances, blend weights, edge thresholds, storage
-precision and the optional stages (sub-image blur, step-wise blending, sample-count
-levels) drawn at random, each case checked stage by stage as the other parity tests do
+precision and the optional stages (sub-image blur, step-wise or bilateral blending,
+sample-count levels) drawn at random, each case checked stage by stage as the other parity tests do
 (masks and lists bit-exact, sub-images and composite within the FP32 / FP16 bars,
 mrr_render equal to the staged calls bit for bit)."""
 import math
@@ -43,11 +43,11 @@ def draw(case):
     pad = 4 - L
     kw = dict(sigma2=sigma2 + [0.0] * pad, weight=weight + [0.0] * pad, enabled=enabled + [0] * pad,
               depth_rel=float(rng.uniform(0.02, 0.1)), normal_cos=float(rng.uniform(0.8, 0.97)))
-    option = int(rng.integers(0, 4))            # 0 none, 1 blur, 2 step-wise, 3 sample-count levels
+    option = int(rng.integers(0, 4))            # 0 none, 1 blur, 2 step-wise or bilateral, 3 sample-count levels
     if option == 1 and any(enabled[1:L]):
         kw["blur"] = [0] + [int(enabled[i] and rng.random() < 0.7) for i in range(1, L)] + [0] * pad
     elif option == 2:
-        kw["merge_mode"] = 1
+        kw["merge_mode"] = 1 if rng.random() < 0.5 else 2
     elif option == 3:
         kw["sample_levels"] = 1
     precision = "fp16" if rng.random() < 0.4 else "fp32"

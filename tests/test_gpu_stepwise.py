@@ -69,7 +69,7 @@ def test_stepwise_staged_merge_needs_pool_size(mrr):
     assert ei.value.status == mrr.MRR_EINVAL
     mrr.mrr_destroy(ctx)
     with pytest.raises(mrr.MrrError):
-        mrr.mrr_create(make_cfg("ssao", 4, W, H, merge_mode=2))
+        mrr.mrr_create(make_cfg("ssao", 4, W, H, merge_mode=3))
 
 
 def test_stepwise_in_batches_equals_single_frames(mrr):

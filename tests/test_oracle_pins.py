@@ -654,6 +654,39 @@ def test_stepwise_render_error_against_full_resolution_is_small():
     assert float(np.sqrt(np.mean((res["out"] - full) ** 2))) <= 1e-2
 
 
+def test_bilateral_merge_keeps_taps_on_the_pixels_surface():
+    """Two levels, level 0 invisible (w_0 = 0): the output is the level-1 interpolation.
+    Texels left of column k hold 0 at depth 1, the others 1 at depth 2 (their sample
+    pixels 2q + 1 carry the depths).  Pixel 2k, half-way between texels k - 1 and k and at
+    depth 2, reads 1/2 through the plain taps and 1 through the bilateral ones (the tap at
+    depth 1 fails the depth test); on flat depth both readings agree exactly, and where no
+    tap passes the bilateral reading falls back to the plain one."""
+    H, W, k = 16, 32, 7
+    depth = np.full((H, W), 1.0)
+    depth[:, 2 * k:] = 2.0
+    fr = synthetic_frame(depth, flat_normals(H, W))
+    kw = dict(enabled=[1, 1, 0, 0], weight=[0.0, 1.0, 0, 0], blur_depth_rel=0.05)
+    a = [np.zeros((H, W)), np.ones((8, 16))]
+    S = [np.zeros((H, W), np.uint8), np.ones((8, 16), np.uint8)]
+    c1 = np.zeros((8, 16, 1))
+    c1[:, k:] = 1.0
+    c = [np.full((H, W, 1), np.nan), c1]
+    bil = orc.merge(fr, cfg_for("ssao", 2, merge_mode=2, **kw), a, S, c, "f64")[..., 0]
+    plain = orc.merge(fr, cfg_for("ssao", 2, **kw), a, S, c, "f64")[..., 0]
+    assert np.all(plain[:, 2 * k] == 0.5) and np.all(bil[:, 2 * k] == 1.0)
+    assert np.all(bil[:, : 2 * k] == 0.0) and np.all(bil[:, 2 * k:] == 1.0)
+    flat = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    for cc in (c, [np.full((H, W, 1), np.nan), np.random.default_rng(1).random((8, 16, 1))]):
+        assert np.array_equal(orc.merge(flat, cfg_for("ssao", 2, merge_mode=2, **kw), a, S, cc, "f64"),
+                              orc.merge(flat, cfg_for("ssao", 2, **kw), a, S, cc, "f64"))
+    # a pixel whose depth matches no tap (a thin sliver at depth 9) falls back to the plain taps
+    sliver = depth.copy()
+    sliver[:, 2 * k] = 9.0
+    fr2 = synthetic_frame(sliver, flat_normals(H, W))
+    bil2 = orc.merge(fr2, cfg_for("ssao", 2, merge_mode=2, **kw), a, S, c, "f64")[..., 0]
+    assert np.all(bil2[:, 2 * k] == 0.5)
+
+
 # ----------------------------------------------------------------- sample-count levels (Sec. 6)
 
 def test_sample_levels_shade_blocks_of_listed_texels_with_thinned_tables():
