@@ -185,6 +185,8 @@ def effect_config(mrr, sg, spec, W, H, precision):
         kw.update(merge_mode=spec["merge_mode"])
     if "sample_levels" in spec:
         kw.update(sample_levels=spec["sample_levels"])
+    if "pyramid_gathers" in spec:
+        kw.update(pyramid_gathers=spec["pyramid_gathers"])
     return mrr.default_config(eff, spec["levels"], W, H, precision=precision, **kw)
 
 
@@ -234,6 +236,8 @@ def oracle_config(orc, sg, wl):
         kw.update(merge_mode=wl["merge_mode"])
     if "sample_levels" in wl:
         kw.update(sample_levels=wl["sample_levels"])
+    if "pyramid_gathers" in wl:
+        kw.update(pyramid_gathers=wl["pyramid_gathers"])
     return orc.default_config(eff, wl["levels"], **kw)
 
 
@@ -737,6 +741,7 @@ def main():
                        "merge": {0: "direct (Sec. 4.2)", 1: "step-wise (Sec. 3.3)",
                                  2: "direct, bilateral taps (Sec. 3.3)"}[cfg.get("merge_mode", 0)],
                        "levels_kind": "sample-count (Sec. 6)" if cfg.get("sample_levels", 0) else "resolution",
+                       "pyramid_gathers": bool(cfg.get("pyramid_gathers", 0)),
                        "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
                                 f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",
                        "l2": "flushed (256 MiB write) before every timed step, outside the events",

@@ -102,6 +102,12 @@ typedef struct mrr_config {
   int sample_levels;              /* 1: sample-count levels (Sec. 6): levels above 0 are rendered at full
                                      resolution with fewer samples instead of at a lower resolution (see
                                      mrr_shade_level); requires blur all 0 and merge_mode 0 */
+  int pyramid_gathers;            /* 1 (SSAO only, not with sample_levels): the depth gathers of levels
+                                     above 0 read the level's point samples -- the depth at s_i(Q) of
+                                     the level-i block Q the projected pixel lies in -- instead of the
+                                     full-resolution pixel (a point-sampled depth pyramid, built in the
+                                     context's pools: frames up to the max size).  Single-frame calls
+                                     only: batches and servers return MRR_EUNSUPPORTED */
 } mrr_config;
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the

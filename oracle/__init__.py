@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
         ("light_size", ctypes.c_float), ("shadow_bias", ctypes.c_float), ("store_half", ctypes.c_int),
         ("cam", ctypes.c_float * 15), ("light", ctypes.c_float * 15), ("shadow_size", ctypes.c_int),
         ("blur", ctypes.c_int * 4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
-        ("sample_levels", ctypes.c_int),
+        ("sample_levels", ctypes.c_int), ("pyramid_gathers", ctypes.c_int), ("gather_level", ctypes.c_int),
     ]
 
 
@@ -147,7 +147,7 @@ def default_config(effect: str, num_levels: int = 4, **kw) -> dict:
                depth_rel=0.05, normal_cos=0.9, force_level0=0, samples=16, radius=0.5,
                ao_bias=0.0125, gi_min_dist2=0.01, kernel=None, blocker_samples=32, pcf_samples=64,
                blocker_taps=None, pcf_taps=None, light_size=0.5, shadow_bias=0.03, store_half=0,
-               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0)
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0, pyramid_gathers=0)
     cfg.update(kw)
     return cfg
 
@@ -184,6 +184,8 @@ class _Bound:
         p.blur_depth_rel = cfg.get("blur_depth_rel", 0.05)
         p.merge_mode = int(cfg.get("merge_mode", 0))
         p.sample_levels = int(cfg.get("sample_levels", 0))
+        p.pyramid_gathers = int(cfg.get("pyramid_gathers", 0))
+        p.gather_level = 0
         cam = frame.cam.as_array()
         for k in range(15):
             p.cam[k] = cam[k]

@@ -67,6 +67,8 @@ struct orc_params {
   int merge_mode;        // 0: direct upsampling (Sec. 4.2); 1: step-wise chain (Sec. 3.3);
                          // 2: direct upsampling with depth-aware (bilateral) taps (Sec. 3.3)
   int sample_levels;     // 1: levels above 0 at full resolution with fewer samples (Sec. 6)
+  int pyramid_gathers;   // 1: SSAO on levels above 0 gathers depth from the level's point samples
+  int gather_level;      // set per call by shade_level: the level whose samples the gathers read
 };
 
 }  // extern "C"
@@ -191,6 +193,9 @@ template <typename T> V3<T> load_normal(const Inputs& in, int W, int x, int y) {
 // k_y (rB) + k_z (rN) in the normal's hemisphere; each is projected to its pixel, and it is
 // occluded when the depth buffer there lies in front of it by more than the bias and
 // within the radius of the shaded point.  AO = 1 - occluded / N; sky is 1.
+// Pyramid gathers (p.gather_level = i > 0): the depth buffer is read at level i's point
+// samples instead -- the sample pixel s_i(Q) of the level-i block Q the projected pixel
+// lies in, i.e. a depth pyramid made by point sampling.
 template <typename T> T ssao_at(const orc_params& p, const View<T>& v, const Inputs& in, int x, int y) {
   const int W = v.W, H = v.H;
   T d = (T)in.depth[(size_t)y * W + x];
@@ -212,6 +217,10 @@ template <typename T> T ssao_at(const orc_params& p, const View<T>& v, const Inp
     if (!(X >= T(0) && X < (T)W)) continue;
     if (!(Y >= T(0) && Y < (T)H)) continue;
     int ix = (int)X, iy = (int)Y;
+    if (p.gather_level > 0) {  // pyramid gathers: the depth of the pixel's level-i block
+      ix = level_sample(ix >> p.gather_level, p.gather_level, W);
+      iy = level_sample(iy >> p.gather_level, p.gather_level, H);
+    }
     T ds = (T)in.depth[(size_t)iy * W + ix];
     if (ds >= v.farp) continue;
     if (ds <= dS - bias && std::fabs(d - ds) < r) occ += 1;
@@ -577,7 +586,9 @@ int compact(int Wi, int Hi, const uint8_t* S, uint32_t* list) {
 // Sub-image i: c_i(q) = effect at the full-resolution pixel s_i(q), for every q in the
 // work list; texels outside it are left untouched.  C channels per texel.
 template <typename T>
-void shade_level(const orc_params& p, const Inputs& in, int level, const uint32_t* list, int n, T* c) {
+void shade_level(const orc_params& p0, const Inputs& in, int level, const uint32_t* list, int n, T* c) {
+  orc_params p = p0;
+  p.gather_level = (p0.pyramid_gathers && p0.effect == 0) ? level : 0;
   const int W = p.width, H = p.height, C = channels(p);
   const int Wi = level_dim(W, level);
   View<T> v = make_view<T>(W, H, p.cam[12], p.cam[13], p.cam[14]);

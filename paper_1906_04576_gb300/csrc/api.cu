@@ -33,6 +33,7 @@ struct mrr_ctx {
   void* cbuf[MRR_MAX_LEVELS] = {};
   void* bbuf[MRR_MAX_LEVELS] = {};  // blurred sub-images of the levels cfg.blur names
   float* comp[MRR_MAX_LEVELS] = {};  // step-wise blending's composites of levels 1 .. L-2
+  float* pyr[MRR_MAX_LEVELS] = {};   // pyramid gathers: point-sampled depth of levels 1 .. L-1
   uint32_t* counts = nullptr;
   uint32_t* chunk_counts = nullptr;
   size_t chunk_cap = 0;
@@ -232,6 +233,34 @@ ShadeParams level_shade_params(const mrr_ctx* ctx, const mrr_gbuffer& g, int lev
     p.ptaps[j] = j < p.np ? ctx->ptaps[j * step] : make_float2(0.f, 0.f);
   }
   return p;
+}
+
+bool fits_pools(const mrr_ctx* ctx, int W, int H);
+
+// Pyramid gathers: build the point-sampled depth of the enabled levels above 0 (those in
+// `mask`) into the context's pools and point the shading slots at them.
+mrr_status pyramid_impl(mrr_ctx* ctx, const mrr_gbuffer& g, const mrr_levels* lv, unsigned mask, ShadeLevels& sl,
+                        cudaStream_t s) {
+  if (!ctx->cfg.pyramid_gathers) return MRR_OK;
+  if (!fits_pools(ctx, g.width, g.height))
+    return fail(ctx, MRR_EINVAL, "pyramid gathers: frame %dx%d exceeds the context's max size", g.width, g.height);
+  PyramidParams pp;
+  std::memset(&pp, 0, sizeof pp);
+  pp.W = g.width;
+  pp.H = g.height;
+  pp.depth = g.depth;
+  for (int i = 1; i < ctx->cfg.num_levels; ++i) {
+    if (!ctx->cfg.enabled[i] || !((mask >> i) & 1u)) continue;
+    const int k = pp.nlev++;
+    pp.level[k] = i;
+    pp.Wi[k] = lv->width[i];
+    pp.Hi[k] = lv->height[i];
+    pp.out[k] = ctx->pyr[i];
+  }
+  MRR_CUDA(ctx, launch_pyramid(pp, s));
+  sl.pyramid = 1;
+  for (int k = 0; k < sl.nlev; ++k) sl.pyr[k] = sl.level[k] > 0 ? ctx->pyr[sl.level[k]] : nullptr;
+  return MRR_OK;
 }
 
 // Sample-count level `level` of frame g into c ([H][W]).
@@ -642,6 +671,8 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
     if (i == 0) sl.compact |= 1 << k;
   }
   sl.counts = ctx->counts;
+  st = pyramid_impl(ctx, *g, &lv, ~0u, sl, s);
+  if (st != MRR_OK) return st;
   if (sl.nlev)
     MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
   if (c.sample_levels)
@@ -696,6 +727,7 @@ void free_pools(mrr_ctx* ctx) {
     cudaFree(ctx->cbuf[i]);
     cudaFree(ctx->bbuf[i]);
     cudaFree(ctx->comp[i]);
+    cudaFree(ctx->pyr[i]);
   }
   cudaFree(ctx->counts);
   cudaFree(ctx->chunk_counts);
@@ -729,6 +761,7 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
     if (c.blur[i]) MRR_CUDA(ctx, cudaMalloc(&ctx->bbuf[i], n * cbytes(c)));
     if (c.merge_mode == 1 && i >= 1 && i < c.num_levels - 1 && c.enabled[i])
       MRR_CUDA(ctx, cudaMalloc(&ctx->comp[i], n * (c.effect == MRR_SSGI ? 16 : 4)));
+    if (c.pyramid_gathers && i >= 1 && c.enabled[i]) MRR_CUDA(ctx, cudaMalloc(&ctx->pyr[i], n * sizeof(float)));
     chunks += (n + COMPACT_CHUNK - 1) / COMPACT_CHUNK;
   }
   // level 0's horizontal blur for every (2R+1)-bit window, summed exactly as the
@@ -790,6 +823,8 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
   if (!(c.blur_depth_rel >= 0.f) || !(c.blur_depth_rel <= FLT_MAX)) return MRR_EINVAL;
   if (c.merge_mode < 0 || c.merge_mode > 2) return MRR_EINVAL;
   if (c.sample_levels != 0 && c.sample_levels != 1) return MRR_EINVAL;
+  if (c.pyramid_gathers != 0 && c.pyramid_gathers != 1) return MRR_EINVAL;
+  if (c.pyramid_gathers && (c.effect != MRR_SSAO || c.sample_levels)) return MRR_EINVAL;
   if (c.sample_levels) {  // full-resolution sub-images: no level blur, direct blend only
     if (c.merge_mode != 0) return MRR_EINVAL;
     for (int i = 0; i < MRR_MAX_LEVELS; ++i)
@@ -925,6 +960,8 @@ mrr_status mrr_shade_level(mrr_ctx* ctx, int level, const mrr_gbuffer* g, const 
   sl.Wi[0] = lv->width[level];
   sl.Hi[0] = lv->height[level];
   sl.counts = lv->counts;
+  st = pyramid_impl(ctx, *g, lv, 1u << level, sl, (cudaStream_t)stream);
+  if (st != MRR_OK) return st;
   MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
                                     ctx->split_texel, (cudaStream_t)stream));
   return MRR_OK;
@@ -956,6 +993,8 @@ mrr_status mrr_shade_levels(mrr_ctx* ctx, const mrr_gbuffer* g, const mrr_levels
     sl.Hi[k] = lv->height[i];
   }
   sl.counts = lv->counts;
+  st = pyramid_impl(ctx, *g, lv, ~0u, sl, (cudaStream_t)stream);
+  if (st != MRR_OK) return st;
   ShadeParams p = make_shade_params(ctx, *g);
   if (sl.nlev)
     MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), ctx->cfg.precision, sl, ctx->shade_grid,
@@ -1039,6 +1078,8 @@ mrr_status check_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* fr
     if (st != MRR_OK) return batch_fail(b, st, ctxs[k]->err.c_str());
     if (frames[k].width > ctxs[k]->pool_W || frames[k].height > ctxs[k]->pool_H)
       return batch_fail(b, MRR_EINVAL, "a frame exceeds its context's max size");
+    if (ctxs[k]->cfg.pyramid_gathers)
+      return batch_fail(b, MRR_EUNSUPPORTED, "pyramid gathers are not batched (single-frame calls only)");
     if (outs && (!outs[k] || !aligned(outs[k], ctxs[k]->cfg.effect == MRR_SSGI ? 16 : 4)))
       return batch_fail(b, MRR_EINVAL, "output is NULL or misaligned");
   }

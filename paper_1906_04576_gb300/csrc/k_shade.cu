@@ -12,6 +12,8 @@
 // shade_full_kernel: one lane group per pixel over 2-D tiles of 8 rows.
 // shade_blocks_kernel: sample-count levels -- every pixel of a listed texel's block at
 //   full resolution, with the level's thinned sample tables.
+// pyramid_kernel: the point-sampled depth of the levels above 0 that SSAO's gathers read
+//   with pyramid gathers (a separate instantiation of shade_levels_kernel).
 // Both evaluate the same effect function at the same full-resolution pixel, so a level
 // texel's value equals full-resolution shading at its sample pixel bit for bit.
 #include "mrr_internal.cuh"
@@ -23,10 +25,11 @@ namespace {
 
 constexpr int SHADE_THREADS = 256;
 
-template <int EFFECT, typename NT, typename SMT, int SPLIT>
-__device__ __forceinline__ float3 effect_at(const ShadeParams& p, const FrameIn& in, int x, int y, bool valid) {
+template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false>
+__device__ __forceinline__ float3 effect_at(const ShadeParams& p, const FrameIn& in, int x, int y, bool valid,
+                                            const GatherDepth gd = GatherDepth{}) {
   if (EFFECT == MRR_SSAO) {
-    return make_float3(ssao_at<NT, SPLIT>(p, in.depth, (const NT*)in.normal, x, y, valid), 0.f, 0.f);
+    return make_float3(ssao_at<NT, SPLIT, PYR>(p, in.depth, (const NT*)in.normal, x, y, valid, gd), 0.f, 0.f);
   } else if (EFFECT == MRR_SSM) {
     return valid ? make_float3(ssm_at<SMT>(p, in.depth, (const SMT*)in.smap, x, y), 0.f, 0.f)
                  : make_float3(0.f, 0.f, 0.f);
@@ -57,7 +60,7 @@ __device__ __forceinline__ void store_value(void* c, size_t i, float3 v, bool ha
   }
 }
 
-template <int EFFECT, typename NT, typename SMT, int SPLIT>
+template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false>
 __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv,
                                                                      int half_store) {
   // per-level descriptors in shared memory (indexed by a runtime level slot)
@@ -65,6 +68,7 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadePar
   __shared__ const uint32_t* s_list[MRR_MAX_LEVELS];
   __shared__ void* s_c[MRR_MAX_LEVELS];
   __shared__ int s_lvl[MRR_MAX_LEVELS], s_W[MRR_MAX_LEVELS], s_H[MRR_MAX_LEVELS];
+  __shared__ const float* s_pyr[MRR_MAX_LEVELS];
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     s_pre[0] = 0;
@@ -78,6 +82,7 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadePar
       s_lvl[k] = lv.level[k];
       s_W[k] = lv.Wi[k];
       s_H[k] = lv.Hi[k];
+      if (PYR) s_pyr[k] = lv.level[k] > 0 ? lv.pyr[k] : in.depth;
     }
   }
   __syncthreads();
@@ -101,7 +106,14 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadePar
       x = min((qx << i) + o, W - 1);
       y = min((qy << i) + o, H - 1);
     }
-    const float3 v = effect_at<EFFECT, NT, SMT, SPLIT>(p, in, x, y, valid);
+    GatherDepth gd{};
+    if (PYR) {  // the slot's level (0: full resolution), for every lane of the warp
+      const int lvl = valid ? s_lvl[k] : 0;
+      gd.base = valid ? s_pyr[k] : in.depth;
+      gd.shift = lvl;
+      gd.width = lvl > 0 ? s_W[k] : W;
+    }
+    const float3 v = effect_at<EFFECT, NT, SMT, SPLIT, PYR>(p, in, x, y, valid, gd);
     if (valid && sub == 0)
       store_value<EFFECT>(s_c[k], ((lv.compact >> k) & 1) ? (size_t)(g - s_pre[k]) : (size_t)qy * s_W[k] + qx, v,
                           half_store != 0);
@@ -147,6 +159,31 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_blocks_kernel(ShadePar
   }
 }
 
+// Point-sampled depth of the levels above 0 for pyramid gathers: out[k][Q] = depth[s_i(Q)].
+__global__ void __launch_bounds__(256) pyramid_kernel(PyramidParams p) {
+  uint32_t n[MRR_MAX_LEVELS], total = 0;
+#pragma unroll
+  for (int k = 0; k < MRR_MAX_LEVELS; ++k) {
+    n[k] = k < p.nlev ? (uint32_t)p.Wi[k] * (uint32_t)p.Hi[k] : 0u;
+    total += n[k];
+  }
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int k = 0;
+    uint32_t e = g;
+#pragma unroll
+    for (int j = 0; j < MRR_MAX_LEVELS - 1; ++j)
+      if (k == j && e >= n[j]) {
+        e -= n[j];
+        k = j + 1;
+      }
+    const int i = p.level[k], Wi = p.Wi[k];
+    const int qy = (int)(e / (uint32_t)Wi), qx = (int)(e - (uint32_t)qy * Wi);
+    const int o = i == 0 ? 0 : 1 << (i - 1);
+    const int sx = min(qx * (1 << i) + o, p.W - 1), sy = min(qy * (1 << i) + o, p.H - 1);
+    p.out[k][e] = __ldg(p.depth + (size_t)sy * p.W + sx);
+  }
+}
+
 // Resident CTAs of one instantiation (SMs x CTAs per SM), computed once per instantiation.
 template <typename K> int resident_blocks(K kernel) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -161,6 +198,12 @@ template <typename K> int resident_blocks(K kernel) {
 template <int EFFECT, typename NT, typename SMT, int SPLIT>
 void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels& lv, int half_store, int grid_mult,
                      cudaStream_t s) {
+  if (EFFECT == MRR_SSAO && lv.pyramid) {
+    static const int resident_p = resident_blocks(shade_levels_kernel<EFFECT, NT, SMT, SPLIT, true>);
+    shade_levels_kernel<EFFECT, NT, SMT, SPLIT, true><<<resident_p * grid_mult, SHADE_THREADS, 0, s>>>(p, in, lv,
+                                                                                                     half_store);
+    return;
+  }
   static const int resident = resident_blocks(shade_levels_kernel<EFFECT, NT, SMT, SPLIT>);
   shade_levels_kernel<EFFECT, NT, SMT, SPLIT><<<resident * grid_mult, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
 }
@@ -255,6 +298,13 @@ cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int pre
                                 int grid, int split, cudaStream_t s) {
   if (precision == MRR_FP16) levels_dispatch<half4, __half>(p, in, lv, 1, grid, split, s);
   else levels_dispatch<float4, float>(p, in, lv, 0, grid, split, s);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid(const PyramidParams& p, cudaStream_t s) {
+  if (p.nlev == 0) return cudaSuccess;
+  pyramid_kernel<<<152 * 8, 256, 0, s>>>(p);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -130,6 +130,20 @@ struct ShadeLevels {
   // bit k set: slot k stores its values at the entry's list position (a list-aligned,
   // compact sub-image) instead of at texel (qy, qx)
   int compact;
+  // pyramid gathers (SSAO): slot k's depth gathers read pyr[k], the level's point-sampled
+  // depth ([H_i][W_i], depth at s_i(Q)); null for level 0, which reads full resolution
+  int pyramid;
+  const float* pyr[MRR_MAX_LEVELS];
+};
+
+// Point-sampled depth of levels above 0 for pyramid gathers (k_shade.cu): slot k writes
+// out[k][Q] = depth[s_i(Q)] for every texel Q of level level[k].
+struct PyramidParams {
+  int W, H, nlev;
+  const float* depth;
+  int level[MRR_MAX_LEVELS];
+  int Wi[MRR_MAX_LEVELS], Hi[MRR_MAX_LEVELS];
+  float* out[MRR_MAX_LEVELS];
 };
 
 // One sample-count level (Sec. 6): every full-resolution pixel of each listed texel's
@@ -215,6 +229,7 @@ cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int preci
                               cudaStream_t s);
 cudaError_t launch_shade_blocks(const ShadeParams& p, const FrameIn& in, int precision, const BlockLevel& b,
                                 int grid_mult, cudaStream_t s);
+cudaError_t launch_pyramid(const PyramidParams& p, cudaStream_t s);
 cudaError_t launch_merge(const MergeParams& p, float* out, cudaStream_t s);
 // bit patterns [first, last] as floats x: counts into *bad every x where the kernels'
 // reciprocal of x or of -x differs from IEEE division

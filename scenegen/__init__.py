@@ -221,6 +221,11 @@ WORKLOADS = {
                                    samples=64, radius=0.5, levels=4, merge_mode=2),
     "ssao64_4k_bilateral": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
                                 samples=64, radius=0.5, levels=4, merge_mode=2),
+    # with pyramid gathers: levels above 0 gather depth from the level's point samples
+    "ssao64_1080p_pyramid": dict(effect="ssao", width=1920, height=1080, n_boxes=64, n_spheres=16,
+                                 samples=64, radius=0.5, levels=4, pyramid_gathers=1),
+    "ssao64_4k_pyramid": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
+                              samples=64, radius=0.5, levels=4, pyramid_gathers=1),
     # and with sample-count levels (Sec. 6): levels above 0 at full resolution, fewer samples
     "ssao64_1080p_samples": dict(effect="ssao", width=1920, height=1080, n_boxes=64, n_spheres=16,
                                  samples=64, radius=0.5, levels=4, sample_levels=1),

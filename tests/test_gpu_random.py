@@ -1,7 +1,7 @@
 """Seeded random configurations against the oracle: frame size, effect, number of levels
 and which of them are enabled, blur variances, blend weights, edge thresholds, storage
 precision and the optional stages (sub-image blur, step-wise or bilateral blending,
-sample-count levels) drawn at random, each case checked stage by stage as the other parity tests do
+sample-count levels, pyramid gathers) drawn at random, each case checked stage by stage as the other parity tests do
 (masks and lists bit-exact, sub-images and composite within the FP32 / FP16 bars,
 mrr_render equal to the staged calls bit for bit)."""
 import math
@@ -54,6 +54,8 @@ def draw(case):
     if effect != "ssm":
         kw["samples"] = int(rng.choice([8, 16, 24]))
     seed = int(rng.integers(0, 1 << 16))
+    if effect == "ssao" and "sample_levels" not in kw and rng.random() < 0.5:
+        kw["pyramid_gathers"] = 1
     return effect, L, W, H, precision, kw, seed
 
 

@@ -765,6 +765,45 @@ def test_sample_levels_with_one_sample_equal_full_resolution():
         orc.render(fr, dict(cfg, blur=[0, 1, 1, 1]))
 
 
+# ----------------------------------------------------------------- pyramid gathers (SSAO)
+
+def test_pyramid_gathers_read_only_the_level_sample_pixels():
+    """Depth 2 at the level-2 sample pixels (4q + 2) and 1.5 everywhere else, normals facing
+    the camera, radius 0.6.  Level-2 SSAO with pyramid gathers reads only sample pixels, so
+    it sees a flat fronto-parallel plane: AO = 1 at every texel.  Reading full resolution,
+    the nearer pixels between the samples occlude (0.5 < r)."""
+    H, W = 64, 96
+    depth = np.full((H, W), 1.5)
+    depth[2::4, 2::4] = 2.0
+    fr = synthetic_frame(depth, flat_normals(H, W))
+    cfg = cfg_for("ssao", 4, samples=32, radius=0.6)
+    Hi, Wi = orc.level_dim(H, 2), orc.level_dim(W, 2)
+    qy, qx = np.mgrid[0:Hi, 0:Wi]
+    wl = ((qy.astype(np.uint32) << 16) | qx.astype(np.uint32)).ravel()
+    pyr = orc.shade_level(fr, dict(cfg, pyramid_gathers=1), 2, wl, "f64")[..., 0]
+    plain = orc.shade_level(fr, cfg, 2, wl, "f64")[..., 0]
+    assert np.all(pyr == 1.0)
+    assert plain[2:-2, 2:-2].max() < 1.0
+
+
+def test_pyramid_gathers_equal_full_resolution_on_block_constant_depth():
+    """Depth constant over aligned 8 x 8 blocks: every level-i block (i <= 3) lies inside
+    one, so its sample pixel carries the depth of every pixel it stands for and the pyramid
+    gathers read exactly what the full-resolution gathers read -- every sub-image equal."""
+    rng = np.random.default_rng(4)
+    H, W = 48, 72
+    blocks = 2.0 + 0.5 * rng.random((H // 8, W // 8))
+    depth = np.kron(blocks, np.ones((8, 8)))
+    fr = synthetic_frame(depth, flat_normals(H, W))
+    cfg = cfg_for("ssao", 4, samples=32, radius=0.6)
+    res = orc.render(fr, cfg)
+    pyr = orc.render(fr, dict(cfg, pyramid_gathers=1))
+    for i in range(4):
+        assert np.array_equal(res["lists"][i], pyr["lists"][i])
+        assert np.array_equal(res["c"][i], pyr["c"][i], equal_nan=True), i
+    assert (res["c"][1][np.isfinite(res["c"][1])] < 1.0).any()   # the steps do occlude
+
+
 # ----------------------------------------------------------------- sub-image blur (Sec. 4.1)
 
 BINOMIAL = np.array([1.0, 4.0, 6.0, 4.0, 1.0])
