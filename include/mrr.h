@@ -263,6 +263,18 @@ mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, v
  * the result to out_host and synchronises the stream before returning. */
 mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* g_host, float* out_host, void* stream);
 
+/* mrr_render_host for a stream of frames: the same copies and rendering, enqueued on the
+ * context's own streams and not waited for.  Consecutive calls use two device input /
+ * output sets in turn, so one frame's host-to-device copy overlaps the previous frame's
+ * rendering and device-to-host copy (renders themselves run one after another).  The
+ * host planes named by g_host and out_host (pinned for full speed) must stay valid, and
+ * the inputs unmodified, until mrr_render_host_wait returns; out_host holds the image
+ * after it.  Not thread-safe on one context. */
+mrr_status mrr_render_host_async(mrr_ctx* ctx, const mrr_gbuffer* g_host, float* out_host);
+
+/* Waits for every frame mrr_render_host_async has enqueued on the context. */
+mrr_status mrr_render_host_wait(mrr_ctx* ctx);
+
 /* mrr_masks for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of the mask stage.  Host programs that may
  * not call cudaMalloc (a plug-in inside an engine that owns every device allocation, a

@@ -165,6 +165,10 @@ _lib.mrr_check_reciprocal.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.P
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+_lib.mrr_render_host_async.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp]
+_lib.mrr_render_host_async.restype = ctypes.c_int
+_lib.mrr_render_host_wait.argtypes = [_vp]
+_lib.mrr_render_host_wait.restype = ctypes.c_int
 for _fn in ("mrr_level_dims", "mrr_create", "mrr_edges", "mrr_masks", "mrr_shade_level", "mrr_shade_levels",
             "mrr_upsample_merge", "mrr_upsample_merge_bilateral", "mrr_blur_level",
             "mrr_render", "mrr_render_full", "mrr_render_host"):
@@ -676,6 +680,15 @@ TABLE1 = {
     "ssm": [(0.924, 1000.0), (1.848, 1000.0), (3.696, 1000.0), (0.0, 1.0)],
     "ssgi": [(0.924, 1000.0), None, (0.924, 100.0), (0.0, 1.0)],
 }
+
+
+def mrr_render_host_async(ctx: Context, frame: HostFrame, out_host: torch.Tensor) -> None:
+    g = frame.struct()
+    _check(ctx, _lib.mrr_render_host_async(ctx.handle, ctypes.byref(g), out_host.data_ptr()))
+
+
+def mrr_render_host_wait(ctx: Context) -> None:
+    _check(ctx, _lib.mrr_render_host_wait(ctx.handle))
 
 
 def default_config(effect: str, num_levels: int, max_width: int, max_height: int, **kw) -> dict:

@@ -48,12 +48,28 @@ struct mrr_ctx {
   float* h_out = nullptr;
   // mrr_render replays a CUDA graph of its launches while the frame's arguments repeat
   bool use_graph = true;
+  // (two entries, so that frames alternating between two buffer sets both replay)
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  mrr_gbuffer graph_key;
-  float* graph_out = nullptr;
+  cudaGraphExec_t graph_exec[2] = {};
+  mrr_gbuffer graph_key[2];
+  float* graph_out[2] = {};
+  uint64_t graph_kernels[2] = {};
+  int graph_next = 0;  // the entry a new capture replaces
   uint64_t graph_replays = 0;
-  uint64_t graph_kernels = 0;
+  // mrr_render_host_async: two device input / output sets used in turn, and the streams
+  // that overlap one frame's copies with the other's rendering
+  struct HostSet {
+    float* depth = nullptr;
+    void* normal = nullptr;
+    void* color = nullptr;
+    void* smap = nullptr;
+    size_t smap_bytes = 0;
+    float* out = nullptr;
+    bool used = false;
+    cudaEvent_t loaded = nullptr, rendered = nullptr, done = nullptr;
+  } hset[2];
+  int hset_next = 0;
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
 };
 
 struct mrr_batch {
@@ -578,19 +594,24 @@ mrr_gbuffer canonical_key(const mrr_gbuffer* g) {  // field copy: padding bytes 
 mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   if (!ctx->use_graph) return render_launches(ctx, g, out, s);
   const mrr_gbuffer key = canonical_key(g);
-  const bool same = ctx->graph_exec && out == ctx->graph_out && std::memcmp(&ctx->graph_key, &key, sizeof key) == 0;
-  if (!same) {
-    if (ctx->graph_exec) {
-      cudaGraphExecDestroy(ctx->graph_exec);
-      ctx->graph_exec = nullptr;
+  int hit = -1;
+  for (int e = 0; e < 2; ++e)
+    if (ctx->graph_exec[e] && out == ctx->graph_out[e] && std::memcmp(&ctx->graph_key[e], &key, sizeof key) == 0)
+      hit = e;
+  if (hit < 0) {
+    hit = ctx->graph_next;
+    ctx->graph_next ^= 1;
+    if (ctx->graph_exec[hit]) {
+      cudaGraphExecDestroy(ctx->graph_exec[hit]);
+      ctx->graph_exec[hit] = nullptr;
     }
     if (!ctx->capture_stream) MRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     MRR_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
     const uint64_t before = launch_counter().load();
     mrr_status st = render_launches(ctx, g, out, ctx->capture_stream);
     // captured launches do not run: count them per replay instead
-    ctx->graph_kernels = launch_counter().load() - before;
-    launch_counter().fetch_sub(ctx->graph_kernels);
+    ctx->graph_kernels[hit] = launch_counter().load() - before;
+    launch_counter().fetch_sub(ctx->graph_kernels[hit]);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (st != MRR_OK) {
@@ -598,17 +619,17 @@ mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStrea
       return st;
     }
     if (e != cudaSuccess) return fail(ctx, MRR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    e = cudaGraphInstantiate(&ctx->graph_exec[hit], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      ctx->graph_exec = nullptr;
+      ctx->graph_exec[hit] = nullptr;
       return fail(ctx, MRR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
-    ctx->graph_key = key;
-    ctx->graph_out = out;
+    ctx->graph_key[hit] = key;
+    ctx->graph_out[hit] = out;
   }
-  MRR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, s));
-  count_launches((int)ctx->graph_kernels);
+  MRR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec[hit], s));
+  count_launches((int)ctx->graph_kernels[hit]);
   ++ctx->graph_replays;
   return MRR_OK;
 }
@@ -714,10 +735,27 @@ mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out
 }
 
 void free_pools(mrr_ctx* ctx) {
-  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  for (int e = 0; e < 2; ++e) {
+    if (ctx->graph_exec[e]) cudaGraphExecDestroy(ctx->graph_exec[e]);
+    ctx->graph_exec[e] = nullptr;
+  }
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-  ctx->graph_exec = nullptr;
   ctx->capture_stream = nullptr;
+  for (auto& hs : ctx->hset) {
+    cudaFree(hs.depth);
+    cudaFree(hs.normal);
+    cudaFree(hs.color);
+    cudaFree(hs.smap);
+    cudaFree(hs.out);
+    if (hs.loaded) cudaEventDestroy(hs.loaded);
+    if (hs.rendered) cudaEventDestroy(hs.rendered);
+    if (hs.done) cudaEventDestroy(hs.done);
+    hs = mrr_ctx::HostSet();
+  }
+  for (cudaStream_t* st : {&ctx->s_in, &ctx->s_comp, &ctx->s_out}) {
+    if (*st) cudaStreamDestroy(*st);
+    *st = nullptr;
+  }
   cudaFree(ctx->edges);
   cudaFree(ctx->ebits);
   for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
@@ -1392,10 +1430,11 @@ mrr_status mrr_autotune(mrr_ctx* ctx, const mrr_gbuffer* g, void* stream, mrr_tu
   ctx->split_texel = best_lanes;
   ctx->split_pixel = best_pix;
   ctx->shade_grid = shade_grid_blocks() * best_mult;
-  if (ctx->graph_exec) {  // the captured launches used the old settings
-    cudaGraphExecDestroy(ctx->graph_exec);
-    ctx->graph_exec = nullptr;
-  }
+  for (int e = 0; e < 2; ++e)  // the captured launches used the old settings
+    if (ctx->graph_exec[e]) {
+      cudaGraphExecDestroy(ctx->graph_exec[e]);
+      ctx->graph_exec[e] = nullptr;
+    }
   if (out) {
     out->lanes_per_texel = best_lanes;
     out->grid_multiplier = best_mult;
@@ -1466,6 +1505,77 @@ mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, v
   ShadeParams p = make_shade_params(ctx, *g);
   MRR_CUDA(ctx, launch_shade_full(p, make_frame_in(*g), ctx->cfg.precision, out_dev, ctx->split_pixel,
                                   (cudaStream_t)stream));
+  return MRR_OK;
+}
+
+mrr_status mrr_render_host_async(mrr_ctx* ctx, const mrr_gbuffer* gh, float* out_host) {
+  if (!ctx) return MRR_EINVAL;
+  mrr_status st = check_gbuffer(ctx, gh, false);
+  if (st != MRR_OK) return st;
+  if (!out_host) return fail(ctx, MRR_EINVAL, "out_host is NULL");
+  const mrr_config& c = ctx->cfg;
+  const int W = gh->width, H = gh->height;
+  if (W > ctx->pool_W || H > ctx->pool_H) return fail(ctx, MRR_EINVAL, "frame exceeds the context's max size");
+  const size_t npx_max = (size_t)ctx->pool_W * ctx->pool_H, npx = (size_t)W * H;
+  const size_t nbytes = c.precision == MRR_FP16 ? 8 : 16;
+  const size_t sm_bytes = c.effect == MRR_SSM
+                              ? (size_t)gh->shadow_size * gh->shadow_size * (c.precision == MRR_FP16 ? 2 : 4)
+                              : 0;
+  for (cudaStream_t* sp : {&ctx->s_in, &ctx->s_comp, &ctx->s_out})
+    if (!*sp) MRR_CUDA(ctx, cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking));
+  mrr_ctx::HostSet& hs = ctx->hset[ctx->hset_next];
+  if (!hs.depth) {
+    MRR_CUDA(ctx, cudaMalloc(&hs.depth, npx_max * sizeof(float)));
+    MRR_CUDA(ctx, cudaMalloc(&hs.normal, npx_max * nbytes));
+    MRR_CUDA(ctx, cudaMalloc(&hs.out, npx_max * sizeof(float) * channels(c)));
+    if (c.effect == MRR_SSGI) MRR_CUDA(ctx, cudaMalloc(&hs.color, npx_max * 8));
+    for (cudaEvent_t* ev : {&hs.loaded, &hs.rendered, &hs.done})
+      MRR_CUDA(ctx, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  }
+  if (sm_bytes > hs.smap_bytes) {
+    // the set's previous frame may still read its shadow map
+    if (hs.used) MRR_CUDA(ctx, cudaEventSynchronize(hs.rendered));
+    cudaFree(hs.smap);
+    hs.smap = nullptr;
+    hs.smap_bytes = 0;
+    MRR_CUDA(ctx, cudaMalloc(&hs.smap, sm_bytes));
+    hs.smap_bytes = sm_bytes;
+  }
+  // uploads into the set wait until its previous frame was rendered (inputs read)
+  if (hs.used) MRR_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, hs.rendered, 0));
+  mrr_gbuffer g = *gh;
+  MRR_CUDA(ctx, cudaMemcpyAsync(hs.depth, gh->depth, npx * sizeof(float), cudaMemcpyHostToDevice, ctx->s_in));
+  MRR_CUDA(ctx, cudaMemcpyAsync(hs.normal, gh->normal, npx * nbytes, cudaMemcpyHostToDevice, ctx->s_in));
+  g.depth = hs.depth;
+  g.normal = hs.normal;
+  if (c.effect == MRR_SSGI) {
+    MRR_CUDA(ctx, cudaMemcpyAsync(hs.color, gh->color, npx * 8, cudaMemcpyHostToDevice, ctx->s_in));
+    g.color = hs.color;
+  }
+  if (c.effect == MRR_SSM) {
+    MRR_CUDA(ctx, cudaMemcpyAsync(hs.smap, gh->shadow_map, sm_bytes, cudaMemcpyHostToDevice, ctx->s_in));
+    g.shadow_map = hs.smap;
+  }
+  MRR_CUDA(ctx, cudaEventRecord(hs.loaded, ctx->s_in));
+  // rendering waits for the inputs and for the set's previous image to be downloaded
+  MRR_CUDA(ctx, cudaStreamWaitEvent(ctx->s_comp, hs.loaded, 0));
+  if (hs.used) MRR_CUDA(ctx, cudaStreamWaitEvent(ctx->s_comp, hs.done, 0));
+  st = render_impl(ctx, &g, hs.out, ctx->s_comp);
+  if (st != MRR_OK) return st;
+  MRR_CUDA(ctx, cudaEventRecord(hs.rendered, ctx->s_comp));
+  MRR_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, hs.rendered, 0));
+  MRR_CUDA(ctx, cudaMemcpyAsync(out_host, hs.out, npx * sizeof(float) * channels(c), cudaMemcpyDeviceToHost,
+                                ctx->s_out));
+  MRR_CUDA(ctx, cudaEventRecord(hs.done, ctx->s_out));
+  hs.used = true;
+  ctx->hset_next ^= 1;
+  return MRR_OK;
+}
+
+mrr_status mrr_render_host_wait(mrr_ctx* ctx) {
+  if (!ctx) return MRR_EINVAL;
+  for (cudaStream_t st : {ctx->s_in, ctx->s_comp, ctx->s_out})
+    if (st) MRR_CUDA(ctx, cudaStreamSynchronize(st));
   return MRR_OK;
 }
 

@@ -304,6 +304,33 @@ def test_render_host_matches_device_path(mrr):
     mrr.mrr_destroy(ctx)
 
 
+@pytest.mark.parametrize("effect", ["ssao", "ssgi", "ssm"])
+def test_pipelined_host_rendering_matches_device_path(mrr, effect):
+    """Five different frames through mrr_render_host_async (two device sets in turn, copies
+    overlapping rendering), then one wait: every image equals mrr_render of the same frame
+    on the device, bit for bit."""
+    import torch
+    W, H = 176, 100
+    cfg = make_cfg(effect, 4, W, H, samples=16)
+    ctx = mrr.mrr_create(cfg)
+    frames = [sg.gbuffer(s, W, H, 12, 4, shadow_size=256 if effect == "ssm" else 0) for s in range(5)]
+    refs = []
+    for fr in frames:
+        dev = mrr.upload_frame(fr)
+        out = mrr.alloc_output(ctx, W, H)
+        mrr.mrr_render(ctx, dev, out)
+        torch.cuda.synchronize()
+        refs.append(out.cpu())
+    hosts = [mrr.pin_frame(fr) for fr in frames]
+    outs = [torch.full(tuple(refs[0].shape), float("nan")).pin_memory() for _ in frames]
+    for h, o in zip(hosts, outs):
+        mrr.mrr_render_host_async(ctx, h, o)
+    mrr.mrr_render_host_wait(ctx)
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+    mrr.mrr_destroy(ctx)
+
+
 def test_graph_replay_matches_direct_launches(mrr):
     import torch
     W, H = 220, 130
