@@ -538,6 +538,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip mrr_autotune (library defaults)")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="serving mix only: mean request rate per second (default: the workload's)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -559,7 +561,10 @@ def main():
     import scenegen as sg
 
     if sg.WORKLOADS[args.workload]["effect"] == "mix":
-        return run_serve(args, mrr, sg, dict(sg.WORKLOADS[args.workload]), rank, world, dist)
+        wl = dict(sg.WORKLOADS[args.workload])
+        if args.rate:
+            wl["rate"] = args.rate
+        return run_serve(args, mrr, sg, wl, rank, world, dist)
     wl, cfg = workload_config(mrr, sg, args.workload)
     W, H = wl["width"], wl["height"]
     prec = cfg["precision"]
