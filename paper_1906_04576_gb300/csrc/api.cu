@@ -21,7 +21,7 @@ struct mrr_ctx {
   float gauss[MRR_MAX_LEVELS][16];
   int R[MRR_MAX_LEVELS];
   int shade_grid = 0;
-  int split_texel = 2, split_pixel = 1;  // SSAO lanes per texel / pixel
+  int split_texel = 1, split_pixel = 1;  // SSAO lanes per texel / pixel
   std::string err;
   // pools of mrr_render / mrr_masks, sized for max_width x max_height
   int pool_W = 0, pool_H = 0;

@@ -25,11 +25,22 @@ namespace {
 
 constexpr int SHADE_THREADS = 256;
 
-template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false>
+// FIX: the SSAO variant compiled for 64 samples.  Its sample loop unrolls completely and
+// every table entry becomes a constant operand instead of an indexed load.  Resident
+// CTAs per SM the register allocation must allow: left at 2 CTAs (128 registers) the
+// compiler hoists the loads of many samples at once and the kernel loses occupancy,
+// while 6 CTAs (42 registers) keep 48 warps per SM in flight -- the fastest of 3 to 7 at
+// 1920x1080 and 3840x2160.
+constexpr int FIX_SSAO = 64;
+constexpr int shade_min_blocks(bool FIX) { return FIX ? 6 : 2; }
+
+inline bool fixed_counts(const ShadeParams& p) { return p.effect == MRR_SSAO && p.samples == FIX_SSAO; }
+
+template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false, bool FIX = false>
 __device__ __forceinline__ float3 effect_at(const ShadeParams& p, const FrameIn& in, int x, int y, bool valid,
                                             const GatherDepth gd = GatherDepth{}) {
   if (EFFECT == MRR_SSAO) {
-    return make_float3(ssao_at<NT, SPLIT, PYR>(p, in.depth, (const NT*)in.normal, x, y, valid, gd), 0.f, 0.f);
+    return make_float3(ssao_at<NT, SPLIT, PYR, FIX ? FIX_SSAO : 0>(p, in.depth, (const NT*)in.normal, x, y, valid, gd), 0.f, 0.f);
   } else if (EFFECT == MRR_SSM) {
     return valid ? make_float3(ssm_at<SMT>(p, in.depth, (const SMT*)in.smap, x, y), 0.f, 0.f)
                  : make_float3(0.f, 0.f, 0.f);
@@ -60,9 +71,9 @@ __device__ __forceinline__ void store_value(void* c, size_t i, float3 v, bool ha
   }
 }
 
-template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false>
-__global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv,
-                                                                     int half_store) {
+template <int EFFECT, typename NT, typename SMT, int SPLIT, bool PYR = false, bool FIX = false>
+__global__ void __launch_bounds__(SHADE_THREADS, shade_min_blocks(FIX))
+    shade_levels_kernel(ShadeParams p, FrameIn in, ShadeLevels lv, int half_store) {
   // per-level descriptors in shared memory (indexed by a runtime level slot)
   __shared__ uint32_t s_pre[MRR_MAX_LEVELS + 1];
   __shared__ const uint32_t* s_list[MRR_MAX_LEVELS];
@@ -113,20 +124,21 @@ __global__ void __launch_bounds__(SHADE_THREADS, 2) shade_levels_kernel(ShadePar
       gd.shift = lvl;
       gd.width = lvl > 0 ? s_W[k] : W;
     }
-    const float3 v = effect_at<EFFECT, NT, SMT, SPLIT, PYR>(p, in, x, y, valid, gd);
+    const float3 v = effect_at<EFFECT, NT, SMT, SPLIT, PYR, FIX>(p, in, x, y, valid, gd);
     if (valid && sub == 0)
       store_value<EFFECT>(s_c[k], ((lv.compact >> k) & 1) ? (size_t)(g - s_pre[k]) : (size_t)qy * s_W[k] + qx, v,
                           half_store != 0);
   }
 }
 
-template <int EFFECT, typename NT, typename SMT, int SPLIT>
-__global__ void __launch_bounds__(256, 2) shade_full_kernel(ShadeParams p, FrameIn in, float* __restrict__ out) {
+template <int EFFECT, typename NT, typename SMT, int SPLIT, bool FIX = false>
+__global__ void __launch_bounds__(256, shade_min_blocks(FIX))
+    shade_full_kernel(ShadeParams p, FrameIn in, float* __restrict__ out) {
   // block = 32 x 8 lanes; a warp row covers 32 / SPLIT consecutive pixels
   const int x = blockIdx.x * (32 / SPLIT) + (int)threadIdx.x / SPLIT;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const bool valid = x < p.v.W && y < p.v.H;
-  const float3 v = effect_at<EFFECT, NT, SMT, SPLIT>(p, in, valid ? x : 0, valid ? y : 0, valid);
+  const float3 v = effect_at<EFFECT, NT, SMT, SPLIT, false, FIX>(p, in, valid ? x : 0, valid ? y : 0, valid);
   if (valid && (threadIdx.x & (SPLIT - 1)) == 0) store_value<EFFECT>(out, (size_t)y * p.v.W + x, v, false);
 }
 
@@ -204,6 +216,14 @@ void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels&
                                                                                                      half_store);
     return;
   }
+  if constexpr (EFFECT == MRR_SSAO && SPLIT == 1) {
+    if (fixed_counts(p)) {
+      static const int resident_f = resident_blocks(shade_levels_kernel<EFFECT, NT, SMT, SPLIT, false, true>);
+      shade_levels_kernel<EFFECT, NT, SMT, SPLIT, false, true><<<resident_f * grid_mult, SHADE_THREADS, 0, s>>>(
+          p, in, lv, half_store);
+      return;
+    }
+  }
   static const int resident = resident_blocks(shade_levels_kernel<EFFECT, NT, SMT, SPLIT>);
   shade_levels_kernel<EFFECT, NT, SMT, SPLIT><<<resident * grid_mult, SHADE_THREADS, 0, s>>>(p, in, lv, half_store);
 }
@@ -211,6 +231,12 @@ void launch_levels_t(const ShadeParams& p, const FrameIn& in, const ShadeLevels&
 template <int EFFECT, typename NT, typename SMT, int SPLIT>
 void launch_full_t(const ShadeParams& p, const FrameIn& in, float* out, cudaStream_t s) {
   dim3 block(32, 8), grid((p.v.W + 32 / SPLIT - 1) / (32 / SPLIT), (p.v.H + 7) / 8);
+  if constexpr (EFFECT == MRR_SSAO && SPLIT == 1) {
+    if (fixed_counts(p)) {
+      shade_full_kernel<EFFECT, NT, SMT, SPLIT, true><<<grid, block, 0, s>>>(p, in, out);
+      return;
+    }
+  }
   shade_full_kernel<EFFECT, NT, SMT, SPLIT><<<grid, block, 0, s>>>(p, in, out);
 }
 
