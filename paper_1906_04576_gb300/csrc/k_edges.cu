@@ -84,34 +84,29 @@ __global__ void __launch_bounds__(TX* TY) edges_kernel(EdgeParams p, const float
   const bool valid = x < W && y < H;
   const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
   const float d = sd[ly][lx];
-  uint8_t e = 0;
-  if (valid && d < p.v.farp) {
-    const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
-    const float nx = snx[ly][lx], ny = sny[ly][lx], nz = snz[ly][lx];
-    const uint8_t hs = shs[ly][lx];
+  // Every staged entry the tests read exists (the footprint covers the 4-neighbourhood),
+  // so all of them are evaluated and combined with non-short-circuit & and |: the same
+  // decision as testing them in turn, without branches.
+  const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
+  const float nx = snx[ly][lx], ny = sny[ly][lx], nz = snz[ly][lx];
+  const uint8_t hs = shs[ly][lx];
+  const bool ssm = p.ssm != 0;
+  bool e = false;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float dn = sd[ly + oy[k]][lx + ox[k]];
-      if (dn < 0.0f) continue;          // outside the image
-      if (dn >= p.v.farp) {             // sky neighbour
-        e = 1;
-        continue;
-      }
-      const float dot = nx * snx[ly + oy[k]][lx + ox[k]] + ny * sny[ly + oy[k]][lx + ox[k]] +
-                        nz * snz[ly + oy[k]][lx + ox[k]];
-      if (dot < p.normal_cos) e = 1;
-      if (p.ssm && shs[ly + oy[k]][lx + ox[k]] != hs) e = 1;
-    }
-    if (x > 0 && x < W - 1) {
-      const float lap = (sd[ly][lx - 1] + sd[ly][lx + 1]) - 2.0f * d;
-      if (fabsf(lap) > p.depth_rel * d) e = 1;
-    }
-    if (y > 0 && y < H - 1) {
-      const float lap = (sd[ly - 1][lx] + sd[ly + 1][lx]) - 2.0f * d;
-      if (fabsf(lap) > p.depth_rel * d) e = 1;
-    }
+  for (int k = 0; k < 4; ++k) {
+    const float dn = sd[ly + oy[k]][lx + ox[k]];
+    const bool in = !(dn < 0.0f);  // a neighbour inside the image
+    const bool sky = dn >= p.v.farp;
+    const float dot = nx * snx[ly + oy[k]][lx + ox[k]] + ny * sny[ly + oy[k]][lx + ox[k]] +
+                      nz * snz[ly + oy[k]][lx + ox[k]];
+    e = e | (in & (sky | (dot < p.normal_cos) | (ssm & (shs[ly + oy[k]][lx + ox[k]] != hs))));
   }
-  store_edge(p, E, x, y, valid, e != 0);
+  const float thr = p.depth_rel * d;
+  const float lapx = (sd[ly][lx - 1] + sd[ly][lx + 1]) - 2.0f * d;
+  const float lapy = (sd[ly - 1][lx] + sd[ly + 1][lx]) - 2.0f * d;
+  e = e | ((x > 0) & (x < W - 1) & (fabsf(lapx) > thr)) | ((y > 0) & (y < H - 1) & (fabsf(lapy) > thr));
+  e = e & valid & (d < p.v.farp);
+  store_edge(p, E, x, y, valid, e);
 }
 
 // edges_direct_kernel: a lane owns a column of ER vertically adjacent pixels.  Every
@@ -287,16 +282,19 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       const float2 lapx = __fadd2_rn(__fadd2_rn(make_float2(dl0, dl1), make_float2(dr0, dr1)), m2d);
       const float2 lapy = __fadd2_rn(__fadd2_rn(make_float2(du, d0), make_float2(d1, dd)), m2d);
       const float2 thr = __fmul2_rn(make_float2(p.depth_rel, p.depth_rel), make_float2(d0, d1));
+      // The decisions combine with non-short-circuit & and | (every operand is already in
+      // a register, so nothing is saved by skipping one): branch-free predicate logic.
+      const bool hasd0 = y + 1 < H;
       // pixel 0: up neighbour row r0 - 1, down neighbour pixel 1
-      bool e0 = (hasl && (dl0 >= farp2 || hl.x < cosT)) || (hasr && (dr0 >= farp2 || hr.x < cosT)) ||
-                (hasu0 && (du >= farp2 || vu.x < cosT)) || (y + 1 < H && (d1 >= farp2 || vd.x < cosT)) ||
-                (hasl && hasr && fabsf(lapx.x) > thr.x) || (hasu0 && y + 1 < H && fabsf(lapy.x) > thr.x);
+      bool e0 = (hasl & ((dl0 >= farp2) | (hl.x < cosT))) | (hasr & ((dr0 >= farp2) | (hr.x < cosT))) |
+                (hasu0 & ((du >= farp2) | (vu.x < cosT))) | (hasd0 & ((d1 >= farp2) | (vd.x < cosT))) |
+                (hasl & hasr & (fabsf(lapx.x) > thr.x)) | (hasu0 & hasd0 & (fabsf(lapy.x) > thr.x));
       // pixel 1: up neighbour pixel 0, down neighbour row r0 + 2
-      bool e1 = (hasl && (dl1 >= farp2 || hl.y < cosT)) || (hasr && (dr1 >= farp2 || hr.y < cosT)) ||
-                (d0 >= farp2 || vu.y < cosT) || (hasd1 && (dd >= farp2 || vd.y < cosT)) ||
-                (hasl && hasr && fabsf(lapx.y) > thr.y) || (hasd1 && fabsf(lapy.y) > thr.y);
-      e0 = e0 && d0 < farp2;
-      e1 = e1 && d1 < farp2;
+      bool e1 = (hasl & ((dl1 >= farp2) | (hl.y < cosT))) | (hasr & ((dr1 >= farp2) | (hr.y < cosT))) |
+                ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
+                (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
+      e0 = e0 & (d0 < farp2);
+      e1 = e1 & (d1 < farp2);
       store_edge(p, E, x, y, x < W && y < H, e0);
       store_edge(p, E, x, y + 1, x < W && y + 1 < H, e1);
       }
