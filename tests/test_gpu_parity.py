@@ -195,6 +195,17 @@ def test_ssao_fp16_storage(mrr, seed):
     check_frame(mrr, fr, make_cfg("ssao", 4, 190, 110, "fp16", samples=32), "fp16")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_ssao_64_sample_variant(mrr, precision):
+    """64 samples with one lane per texel run the kernels compiled for that count (the
+    unrolled sample loop); the work lists, the full-resolution image and the frame must
+    match the oracle exactly as the runtime-count kernels do."""
+    W, H = 173, 101
+    fr = sg.gbuffer(7, W, H, 20, 6)
+    check_frame(mrr, fr, make_cfg("ssao", 4, W, H, precision, samples=64, lanes_per_texel=1, lanes_per_pixel=1),
+                precision)
+
+
 def test_all_sky_frame(mrr):
     W, H = 64, 40
     fr = sg.gbuffer(0, W, H, 0, 0, eye=(0.0, 2.0, 6.0), target=(0.0, 20.0, 0.0))   # looking up: sky only
