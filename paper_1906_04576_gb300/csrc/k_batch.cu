@@ -47,7 +47,11 @@ __device__ __forceinline__ void batch_store(void* c, size_t i, float3 v, int eff
   }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS, 3) shade_batch_kernel(const BatchItem* __restrict__ items, int nitems,
+// All three effects share one kernel, so its registers are those of the largest (SSGI).
+// The kernel waits mostly on its gathers; capped at 64 registers (4 CTAs, 32 warps per SM,
+// a 16-byte spill) it shades the batched SSGI + SSAO 4K frames 3 % faster than at its
+// unconstrained 71 (3 CTAs); at 48 registers the spills cost more than the warps gain.
+__global__ void __launch_bounds__(BATCH_THREADS, 4) shade_batch_kernel(const BatchItem* __restrict__ items, int nitems,
                                                                     uint32_t* queue_head, int chunk) {
   // segment s = (item, level slot); prefix of the segment lengths
   __shared__ uint32_t s_pre[MAX_BATCH * MRR_MAX_LEVELS + 1];
