@@ -357,24 +357,40 @@ __global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __res
 template <typename CT, int C>
 __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __restrict__ out) {
   const uint32_t n = min(__ldg(p.count), (uint32_t)p.W * (uint32_t)p.H);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t e = __ldg(p.list + k);
-    const int x = (int)(e & 0xFFFFu), y = (int)(e >> 16);
-    if (x >= p.W || y >= p.H) continue;
-    // as the merge kernel blends level 0: one tap of weight 1, a rendered texel
-    const float ahat = 0.0f + 1.0f * __ldg(p.a0c + k);
-    const float wa = p.weight * ahat;
-    const float alpha = (1.0f < wa) ? 1.0f : wa;
-    if (!(alpha > 0.0f)) continue;
-    const float3 v = load_c<CT>(p.c0c, k, C);
-    const float om = 1.0f - alpha;
-    const size_t o = (size_t)y * p.W + x;
-    if (C == 4) {
-      float4* q = reinterpret_cast<float4*>(out) + o;
-      const float4 c = *q;
-      *q = make_float4(v.x * alpha + c.x * om, v.y * alpha + c.y * om, v.z * alpha + c.z * om, 0.0f);
-    } else {
-      out[o] = v.x * alpha + out[o] * om;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // two entries per round, every list-aligned read (entry, a_0, c_0) of both issued before
+  // the first is used: the read-modify-write of the image is the only dependent access
+  for (uint32_t k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < n; k0 += 2 * stride) {
+    uint32_t e[2];
+    float a[2];
+    float3 v[2];
+    bool in[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t k = k0 + u * stride;
+      in[u] = k < n;
+      const uint32_t kk = in[u] ? k : k0;
+      e[u] = __ldg(p.list + kk);
+      a[u] = __ldg(p.a0c + kk);
+      v[u] = load_c<CT>(p.c0c, kk, C);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int x = (int)(e[u] & 0xFFFFu), y = (int)(e[u] >> 16);
+      // as the merge kernel blends level 0: one tap of weight 1, a rendered texel
+      const float ahat = 0.0f + 1.0f * a[u];
+      const float wa = p.weight * ahat;
+      const float alpha = (1.0f < wa) ? 1.0f : wa;
+      if (!in[u] || x >= p.W || y >= p.H || !(alpha > 0.0f)) continue;
+      const float om = 1.0f - alpha;
+      const size_t o = (size_t)y * p.W + x;
+      if (C == 4) {
+        float4* q = reinterpret_cast<float4*>(out) + o;
+        const float4 c = *q;
+        *q = make_float4(v[u].x * alpha + c.x * om, v[u].y * alpha + c.y * om, v[u].z * alpha + c.z * om, 0.0f);
+      } else {
+        out[o] = v[u].x * alpha + out[o] * om;
+      }
     }
   }
 }
