@@ -167,7 +167,9 @@ void mrr_destroy(mrr_ctx* ctx);
  *  or (c) whose normal's dot product with an in-image non-sky 4-neighbour's is below
  *  normal_cos (first derivative of the normals), or (d) for MRR_SSM, whose one-sample
  *  hard shadow differs from an in-image non-sky 4-neighbour's; else 0.  Sky pixels
- *  are 0.  Edge maps are combined by maximum (Sec. 3.1). */
+ *  are 0.  Edge maps are combined by maximum (Sec. 3.1).  For MRR_SSM frames up to the
+ *  context's max size the hard shadows pass through a scratch pool of the context, so
+ *  such calls on one context must not overlap on different streams. */
 mrr_status mrr_edges(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* edges_dev, void* stream);
 
 /* Sec. 3.1 + Sec. 4.1: the masks of every level from the edge image [H][W] with

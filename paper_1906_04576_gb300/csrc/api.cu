@@ -27,6 +27,7 @@ struct mrr_ctx {
   int pool_W = 0, pool_H = 0;
   uint8_t* edges = nullptr;
   uint32_t* ebits = nullptr;  // mrr_render's bit-packed edge image
+  uint32_t* sbits = nullptr;  // soft shadows: the one-sample hard shadows as bits (edge kernels' scratch)
   float* alpha[MRR_MAX_LEVELS] = {};
   uint8_t* stencil[MRR_MAX_LEVELS] = {};
   uint32_t* worklist[MRR_MAX_LEVELS] = {};
@@ -392,6 +393,7 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.zero_words = zero_words;
   p.ebits = ebits;
   p.ewords = (g->width + 31) / 32;
+  if (p.ssm && ctx->sbits && g->width <= ctx->pool_W && g->height <= ctx->pool_H) p.sbits = ctx->sbits;
   const int h = ctx->cfg.precision == MRR_FP16;
   MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
   return MRR_OK;
@@ -758,6 +760,7 @@ void free_pools(mrr_ctx* ctx) {
   }
   cudaFree(ctx->edges);
   cudaFree(ctx->ebits);
+  cudaFree(ctx->sbits);
   for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
     cudaFree(ctx->alpha[i]);
     cudaFree(ctx->stencil[i]);
@@ -786,6 +789,7 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
   const size_t npx = (size_t)W * H;
   MRR_CUDA(ctx, cudaMalloc(&ctx->edges, npx));
   MRR_CUDA(ctx, cudaMalloc(&ctx->ebits, (size_t)((W + 31) / 32) * H * sizeof(uint32_t)));
+  if (c.effect == MRR_SSM) MRR_CUDA(ctx, cudaMalloc(&ctx->sbits, (size_t)((W + 31) / 32) * H * sizeof(uint32_t)));
   size_t chunks = 0;
   for (int i = 0; i < c.num_levels; ++i) {
     const size_t n = (size_t)level_dim(W, i) * level_dim(H, i);

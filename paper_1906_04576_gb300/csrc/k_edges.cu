@@ -4,18 +4,22 @@
 // edges_direct_kernel (SSAO, SSGI): each lane reads its pixel and its 4 neighbours
 //   straight from global memory; the neighbours' lines are the block's own rows, so
 //   they are L1 hits and DRAM sees each G-buffer texel about once.
-// edges_tma_kernel (SSAO, SSGI; rows a multiple of 16 bytes): a persistent CTA walks
+// edges_tma_kernel (rows a multiple of 16 bytes): a persistent CTA walks
 //   32x16 output tiles; the tile's depth and normals plus a one-pixel halo arrive by TMA
 //   into a ring of two shared-memory stages, the next tile's loads in flight while one
-//   is tested (eight such CTAs per SM).  Same tests and arithmetic as
+//   is tested (several such CTAs per SM).  Same tests and arithmetic as
 //   edges_direct_kernel, read from shared memory.
-// edges_kernel (soft shadows): the tile and a one-pixel halo of depth, normals and the
-//   one-sample hard shadow of Sec. 3.1 are staged in shared memory, so each staged
-//   texel's hard shadow (a reconstruction, a light-space projection and a shadow-map
-//   read) is computed once, not once per neighbour test.
+// Soft shadows, rows a multiple of 16 bytes: shadow_bits_kernel writes the one-sample
+//   hard shadow of Sec. 3.1 of every pixel as bits (a reconstruction, a light-space
+//   projection and a shadow-map read per pixel), then edges_tma_kernel<NT, true> adds the
+//   comparisons of those bits with the in-image neighbours' to its tests.
+// edges_kernel (soft shadows, other rows): the tile and a one-pixel halo of depth, normals
+//   and the hard shadows are staged in shared memory, so each staged texel's hard shadow
+//   is computed once, not once per neighbour test.
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "mrr_internal.cuh"
 #include "shade_common.cuh"
@@ -206,7 +210,61 @@ __device__ __forceinline__ float3 smem_normal(const half4* s, int i) {
   return make_float3(__low2float(xy), __high2float(xy), __low2float(zw));
 }
 
-template <typename NT>
+// One-sample hard shadows of Sec. 3.1 as bits (bit b of word w of a row = pixel 32 w + b;
+// 1 lit, 0 shadowed; sky, pixels not beyond the light's near plane or off the map, and
+// columns past the image 1): the first pass of soft-shadow edge detection when the frame's
+// rows allow TMA.  A CTA covers 32 x 32 pixels, a lane SB_ROWS of them (rows ty + 8 k);
+// each step -- depth reads, light-space projections, shadow-map reads -- is issued for all
+// of the lane's pixels before the next, so a lane waits on two load latencies in all.
+constexpr int SB_ROWS = 4;
+template <typename SMT>
+__global__ void __launch_bounds__(TX* TY) shadow_bits_kernel(EdgeParams p, const float* __restrict__ depth,
+                                                              const SMT* __restrict__ smap) {
+  const int W = p.v.W, H = p.v.H;
+  const int x = blockIdx.x * TX + threadIdx.x;
+  float d[SB_ROWS];
+  bool in[SB_ROWS];
+#pragma unroll
+  for (int k = 0; k < SB_ROWS; ++k) {
+    const int y = (blockIdx.y * SB_ROWS + k) * TY + threadIdx.y;
+    in[k] = x < W && y < H;
+    d[k] = __ldg(depth + (in[k] ? (size_t)y * W + x : 0));
+  }
+  bool look[SB_ROWS];
+  size_t si[SB_ROWS];
+  float zl[SB_ROWS];
+#pragma unroll
+  for (int k = 0; k < SB_ROWS; ++k) {
+    const int y = (blockIdx.y * SB_ROWS + k) * TY + threadIdx.y;
+    look[k] = false;
+    si[k] = 0;
+    zl[k] = 0.0f;
+    float zr, Xt, Yt;
+    if (in[k] && d[k] < p.v.farp && light_coords(p.v, p.L, x, y, d[k], zr, Xt, Yt)) {
+      const float S = (float)p.L.S;
+      if (Xt >= 0.0f && Xt < S && Yt >= 0.0f && Yt < S) {
+        look[k] = true;
+        si[k] = (size_t)(int)Yt * p.L.S + (int)Xt;
+        zl[k] = zr - p.shadow_bias;
+      }
+    }
+  }
+  float z[SB_ROWS];
+#pragma unroll
+  for (int k = 0; k < SB_ROWS; ++k) z[k] = load_sm(smap, si[k]);
+#pragma unroll
+  for (int k = 0; k < SB_ROWS; ++k) {
+    const int y = (blockIdx.y * SB_ROWS + k) * TY + threadIdx.y;
+    // hard_shadow's decision: lit unless projected onto the map and behind its depth
+    const bool lit = !look[k] || z[k] >= zl[k];
+    const uint32_t b = __ballot_sync(0xffffffffu, lit);
+    if (threadIdx.x == 0 && y < H) p.sbits[(size_t)y * p.ewords + blockIdx.x] = b;
+  }
+}
+
+// SSM: the edge tests also compare each pixel's hard shadow with its in-image neighbours'
+// (from p.sbits, written by shadow_bits_kernel).
+template <typename NT, bool SSM>
 __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_constant__ CUtensorMap tm_n,
                                                              const __grid_constant__ CUtensorMap tm_d, EdgeParams p,
                                                              uint8_t* __restrict__ E) {
@@ -293,6 +351,25 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       bool e1 = (hasl & ((dl1 >= farp2) | (hl.y < cosT))) | (hasr & ((dr1 >= farp2) | (hr.y < cosT))) |
                 ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
                 (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
+      if constexpr (SSM) {
+        // hard-shadow bits of rows y - 1 .. y + 2 (clamped; the has flags drop rows and
+        // columns outside the image), the words left and right of the tile's word
+        const int wc = x0 >> 5;
+        uint32_t sc[4], sl[4], sr[4];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const uint32_t* row = p.sbits + (size_t)min(max(y - 1 + rr, 0), H - 1) * p.ewords;
+          const uint32_t wl = __ldg(row + max(wc - 1, 0)), wm = __ldg(row + wc),
+                         wr = __ldg(row + min(wc + 1, p.ewords - 1));
+          sc[rr] = (wm >> lane) & 1u;
+          sl[rr] = (__funnelshift_l(wl, wm, 1) >> lane) & 1u;  // pixel x - 1
+          sr[rr] = (__funnelshift_r(wm, wr, 1) >> lane) & 1u;  // pixel x + 1
+        }
+        // pixel 0 in row 1 of the four, pixel 1 in row 2
+        const uint32_t s0 = sc[1], s1 = sc[2];
+        e0 = e0 | (hasl & (sl[1] != s0)) | (hasr & (sr[1] != s0)) | (hasu0 & (sc[0] != s0)) | (hasd0 & (s1 != s0));
+        e1 = e1 | (hasl & (sl[2] != s1)) | (hasr & (sr[2] != s1)) | (s0 != s1) | (hasd1 & (sc[3] != s1));
+      }
       e0 = e0 & (d0 < farp2);
       e1 = e1 & (d1 < farp2);
       store_edge(p, E, x, y, x < W && y < H, e0);
@@ -315,15 +392,16 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
   }
 }
 
-template <typename NT>
+template <typename NT, bool SSM>
 int edges_tma_grid() {
   static int blocks = 0;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(edges_tma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edges_tma_smem<NT>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_tma_kernel<NT>, ETHREADS, edges_tma_smem<NT>());
+    cudaFuncSetAttribute(edges_tma_kernel<NT, SSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edges_tma_smem<NT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_tma_kernel<NT, SSM>, ETHREADS, edges_tma_smem<NT>());
     blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
@@ -347,13 +425,22 @@ bool edge_maps(const EdgeParams& p, const float* depth, const void* normal, CUte
   return ok && encode_tensor_map(td, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, depth, ddims, dstrides, dbox);
 }
 
-template <typename NT>
-bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* normal, uint8_t* E, cudaStream_t s) {
+// The TMA path: false (nothing launched) when the frame's layout does not allow it.  For
+// soft shadows (SMT: the shadow map's storage) the hard-shadow bits are written first.
+template <typename NT, typename SMT = void>
+bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* normal, const void* smap, uint8_t* E,
+                      cudaStream_t s) {
+  constexpr bool SSM = !std::is_void<SMT>::value;
   CUtensorMap tn, td;
   if (!p.fault || !edge_maps<NT>(p, depth, normal, &tn, &td)) return false;
+  if constexpr (SSM) {
+    dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY * SB_ROWS - 1) / (TY * SB_ROWS));
+    shadow_bits_kernel<SMT><<<grid, block, 0, s>>>(p, depth, (const SMT*)smap);
+    count_launches(1);
+  }
   const int tiles = ((p.v.W + ETW - 1) / ETW) * ((p.v.H + ETH - 1) / ETH);
-  const int grid = min(tiles, edges_tma_grid<NT>());
-  edges_tma_kernel<NT><<<grid, ETHREADS, edges_tma_smem<NT>(), s>>>(tn, td, p, E);
+  const int grid = min(tiles, edges_tma_grid<NT, SSM>());
+  edges_tma_kernel<NT, SSM><<<grid, ETHREADS, edges_tma_smem<NT>(), s>>>(tn, td, p, E);
   return true;
 }
 
@@ -380,21 +467,28 @@ cudaError_t launch_check_wait(uint32_t* fault, cudaStream_t s) {
 }
 
 void edges_prepare() {
-  edges_tma_grid<float4>();
-  edges_tma_grid<half4>();
+  edges_tma_grid<float4, false>();
+  edges_tma_grid<half4, false>();
+  edges_tma_grid<float4, true>();
+  edges_tma_grid<half4, true>();
 }
 
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const void* smap, int half_smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
   if (!p.ssm) {
-    const bool tma = half_normal ? launch_edges_tma<half4>(p, depth, normal, E, s)
-                                 : launch_edges_tma<float4>(p, depth, normal, E, s);
+    const bool tma = half_normal ? launch_edges_tma<half4>(p, depth, normal, nullptr, E, s)
+                                 : launch_edges_tma<float4>(p, depth, normal, nullptr, E, s);
     if (!tma) {
       dim3 dgrid((p.v.W + TX - 1) / TX, (p.v.H + TY * ER - 1) / (TY * ER));
       if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);
       else edges_direct_kernel<float4><<<dgrid, block, 0, s>>>(p, depth, (const float4*)normal, E);
     }
+  } else if (p.sbits && (half_normal ? (half_smap ? launch_edges_tma<half4, __half>(p, depth, normal, smap, E, s)
+                                                  : launch_edges_tma<half4, float>(p, depth, normal, smap, E, s))
+                                     : (half_smap ? launch_edges_tma<float4, __half>(p, depth, normal, smap, E, s)
+                                                  : launch_edges_tma<float4, float>(p, depth, normal, smap, E, s)))) {
+    // soft shadows, two passes: shadow bits, then the TMA edge kernel
   } else if (half_normal) {
     if (half_smap)
       edges_kernel<half4, __half><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const __half*)smap, E);

@@ -74,6 +74,10 @@ struct EdgeParams {
   int zero_words;
   uint32_t* ebits;  // non-null: write the edge image bit-packed here, ewords words per row
   int ewords;
+  // soft shadows: scratch for the one-sample hard shadows as bits (ewords words per row).
+  // Non-null lets a frame whose rows allow TMA take the two-pass path (shadow bits, then
+  // the TMA edge kernel); null keeps the one-pass staged kernel.
+  uint32_t* sbits;
 };
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,

@@ -253,8 +253,12 @@ def test_ssgi_skips_half_level(mrr, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_ssm_soft_shadows(mrr, precision):
-    W, H = 180, 120
+@pytest.mark.parametrize("size", [(180, 120), (196, 75), (170, 64)])
+def test_ssm_soft_shadows(mrr, precision, size):
+    """Soft shadows: rows a multiple of 16 bytes take the two-pass edge path (hard-shadow
+    bits, then the TMA kernel; 196 x 75 has a partial last bit word and a ragged last tile
+    row), other widths the one-pass staged kernel (170)."""
+    W, H = size
     fr = sg.gbuffer(4, W, H, 16, 4, shadow_size=512)
     check_frame(mrr, fr, make_cfg("ssm", 4, W, H, precision), precision)
 
