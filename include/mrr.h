@@ -256,6 +256,15 @@ mrr_status mrr_upsample_merge_bilateral(mrr_ctx* ctx, const mrr_gbuffer* g, cons
  * the context's max size.  out_dev as in mrr_upsample_merge. */
 mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream);
 
+/* Tracing hook (an addition for measurement): with two CUDA events (cudaEvent_t passed
+ * as void*, created with timing), every following mrr_render records event_begin on its
+ * stream immediately before the work-list shading launch of the frame path and event_end
+ * immediately after it, so cudaEventElapsedTime gives that launch's device time inside a
+ * real frame; while set, mrr_render launches its kernels one by one instead of replaying
+ * a CUDA graph.  The caller keeps the events alive until tracing ends.  NULL, NULL ends
+ * tracing.  MRR_EINVAL if exactly one event is NULL. */
+mrr_status mrr_trace_shading(mrr_ctx* ctx, void* event_begin, void* event_end);
+
 /* Naive full-resolution rendering (the paper's comparison, Sec. 5): the effect at
  * every pixel.  out_dev as in mrr_upsample_merge. */
 mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream);

@@ -164,6 +164,8 @@ _lib.mrr_check_wait_timeout.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint32)]
 _lib.mrr_check_reciprocal.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
 _lib.mrr_render.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_full.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
+_lib.mrr_trace_shading.argtypes = [_vp, _vp, _vp]
+_lib.mrr_trace_shading.restype = ctypes.c_int
 _lib.mrr_render_host.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp, _vp]
 _lib.mrr_render_host_async.argtypes = [_vp, ctypes.POINTER(mrr_gbuffer), _vp]
 _lib.mrr_render_host_async.restype = ctypes.c_int
@@ -632,6 +634,21 @@ def mrr_render(ctx: Context, frame: DeviceFrame, out: torch.Tensor, stream=None)
 def mrr_render_full(ctx: Context, frame: DeviceFrame, out: torch.Tensor, stream=None) -> None:
     g = frame.struct()
     _check(ctx, _lib.mrr_render_full(ctx.handle, ctypes.byref(g), _ptr(out), _stream(stream)))
+
+
+def mrr_trace_shading(ctx: Context, begin=None, end=None) -> None:
+    """Record two torch.cuda.Event (enable_timing=True) around the frame path's shading
+    launch in every following mrr_render (which then runs without its CUDA graph); no
+    events end tracing.  The events must outlive the traced renders."""
+    if (begin is None) != (end is None):
+        raise ValueError("mrr_trace_shading: both events or neither")
+    if begin is None:
+        _check(ctx, _lib.mrr_trace_shading(ctx.handle, None, None))
+        return
+    for ev in (begin, end):
+        if not ev.cuda_event:
+            ev.record()  # torch creates the underlying event at its first record
+    _check(ctx, _lib.mrr_trace_shading(ctx.handle, _vp(begin.cuda_event), _vp(end.cuda_event)))
 
 
 @dataclass

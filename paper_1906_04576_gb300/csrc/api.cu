@@ -28,6 +28,8 @@ struct mrr_ctx {
   uint8_t* edges = nullptr;
   uint32_t* ebits = nullptr;  // mrr_render's bit-packed edge image
   uint32_t* sbits = nullptr;  // soft shadows: the one-sample hard shadows as bits (edge kernels' scratch)
+  // mrr_trace_shading: events recorded around the frame path's shading launch
+  cudaEvent_t trace_begin = nullptr, trace_end = nullptr;
   float* alpha[MRR_MAX_LEVELS] = {};
   uint8_t* stencil[MRR_MAX_LEVELS] = {};
   uint32_t* worklist[MRR_MAX_LEVELS] = {};
@@ -594,7 +596,7 @@ mrr_gbuffer canonical_key(const mrr_gbuffer* g) {  // field copy: padding bytes 
 }
 
 mrr_status render_impl(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
-  if (!ctx->use_graph) return render_launches(ctx, g, out, s);
+  if (!ctx->use_graph || ctx->trace_begin) return render_launches(ctx, g, out, s);
   const mrr_gbuffer key = canonical_key(g);
   int hit = -1;
   for (int e = 0; e < 2; ++e)
@@ -696,8 +698,10 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   sl.counts = ctx->counts;
   st = pyramid_impl(ctx, *g, &lv, ~0u, sl, s);
   if (st != MRR_OK) return st;
+  if (ctx->trace_begin) MRR_CUDA(ctx, cudaEventRecord(ctx->trace_begin, s));
   if (sl.nlev)
     MRR_CUDA(ctx, launch_shade_levels(p, make_frame_in(*g), c.precision, sl, ctx->shade_grid, ctx->split_texel, s));
+  if (ctx->trace_end) MRR_CUDA(ctx, cudaEventRecord(ctx->trace_end, s));
   if (c.sample_levels)
     for (int i = 1; i < c.num_levels; ++i) {
       if (!c.enabled[i]) continue;
@@ -1498,6 +1502,15 @@ mrr_status mrr_render(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* 
   if (!out_dev || !aligned(out_dev, ctx->cfg.effect == MRR_SSGI ? 16 : 4))
     return fail(ctx, MRR_EINVAL, "out_dev is NULL or misaligned");
   return render_impl(ctx, g, out_dev, (cudaStream_t)stream);
+}
+
+mrr_status mrr_trace_shading(mrr_ctx* ctx, void* event_begin, void* event_end) {
+  if (!ctx) return MRR_EINVAL;
+  if ((event_begin == nullptr) != (event_end == nullptr))
+    return fail(ctx, MRR_EINVAL, "trace events: both or neither");
+  ctx->trace_begin = (cudaEvent_t)event_begin;
+  ctx->trace_end = (cudaEvent_t)event_end;
+  return MRR_OK;
 }
 
 mrr_status mrr_render_full(mrr_ctx* ctx, const mrr_gbuffer* g, float* out_dev, void* stream) {

@@ -418,3 +418,26 @@ def test_frame_larger_than_context_is_rejected(mrr):
         mrr.mrr_render(ctx, dev, out)
     assert ei.value.status == mrr.MRR_EINVAL
     mrr.mrr_destroy(ctx)
+
+
+def test_trace_shading_hook(mrr):
+    """mrr_trace_shading: events around the frame path's shading launch give a positive
+    device time; the traced (graph-less) render equals the graph replay bit for bit."""
+    import torch
+    W, H = 160, 96
+    fr = sg.gbuffer(2, W, H, 16, 4)
+    cfg = make_cfg("ssao", 4, W, H, samples=64)
+    ctx = mrr.mrr_create(cfg)
+    dev = mrr.upload_frame(fr)
+    ref, got = mrr.alloc_output(ctx, W, H), mrr.alloc_output(ctx, W, H)
+    mrr.mrr_render(ctx, dev, ref)
+    tb, te = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mrr.mrr_trace_shading(ctx, tb, te)
+    mrr.mrr_render(ctx, dev, got)
+    torch.cuda.synchronize()
+    assert tb.elapsed_time(te) > 0.0
+    mrr.mrr_trace_shading(ctx)
+    assert torch.equal(ref, got)
+    with pytest.raises(ValueError):
+        mrr.mrr_trace_shading(ctx, tb, None)
+    mrr.mrr_destroy(ctx)
