@@ -87,8 +87,11 @@ typedef struct mrr_config {
   float shadow_bias;              /* light-depth bias */
   int max_width, max_height;      /* largest frame mrr_render / mrr_masks will see (sizes pools) */
   /* tuning knobs (0 = library default); they change speed, never results */
-  int lanes_per_texel;            /* SSAO work-list kernel: lanes sharing one texel's samples: 1, 2 or 4 */
-  int lanes_per_pixel;            /* SSAO full-resolution kernel: lanes sharing one pixel: 1, 2 or 4 */
+  int lanes_per_texel;            /* SSAO work-list kernel: lanes sharing one texel's samples: 1, 2 or 4
+                                     (default 1; with 64 samples and 1 lane the kernel compiled for that
+                                     count runs) */
+  int lanes_per_pixel;            /* SSAO full-resolution kernel: lanes sharing one pixel: 1, 2 or 4
+                                     (default 1, likewise) */
   int no_graph;                   /* 1: mrr_render launches its kernels one by one instead of replaying a
                                      CUDA graph of them (the graph is re-captured whenever the frame
                                      descriptor or output pointer changes) */
