@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "mrr_internal.cuh"
 
@@ -41,6 +42,7 @@ struct mrr_ctx {
   uint32_t* chunk_counts = nullptr;
   size_t chunk_cap = 0;
   float* lut0 = nullptr;  // level 0's horizontal blur table (device), see MaskParams
+  float* lut[MRR_MAX_LEVELS] = {};  // the levels above 0's tables (device), see MaskParams
   uint32_t* fault = nullptr;  // device fault word (bits of tma.cuh)
   // pools of mrr_render_host
   float* h_depth = nullptr;
@@ -344,6 +346,7 @@ MaskParams mask_params(const mrr_ctx* ctx, const mrr_levels* lv) {
   }
   m.label = lv->label;
   m.lut0 = ctx->lut0;
+  for (int i = 1; i < MRR_MAX_LEVELS; ++i) m.lut[i] = ctx->lut[i];
   return m;
 }
 
@@ -777,6 +780,10 @@ void free_pools(mrr_ctx* ctx) {
   cudaFree(ctx->counts);
   cudaFree(ctx->chunk_counts);
   cudaFree(ctx->lut0);
+  for (float*& t : ctx->lut) {
+    cudaFree(t);
+    t = nullptr;
+  }
   cudaFree(ctx->fault);
   cudaFree(ctx->h_depth);
   cudaFree(ctx->h_normal);
@@ -823,6 +830,21 @@ mrr_status alloc_pools(mrr_ctx* ctx) {
     }
     MRR_CUDA(ctx, cudaMalloc(&ctx->lut0, n * sizeof(float)));
     MRR_CUDA(ctx, cudaMemcpy(ctx->lut0, host, n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  // the same tables for the blurred levels above 0, summed the same way
+  for (int i = 1; i < c.num_levels; ++i) {
+    const int R = ctx->R[i];
+    if (R <= 0 || R > MASK_LUT_GLOBAL_R) continue;
+    const int n = 1 << (2 * R + 1);
+    std::vector<float> host(n);
+    for (int b = 0; b < n; ++b) {
+      float acc = 0.0f;
+      for (int t = 0; t <= 2 * R; ++t)
+        if ((b >> t) & 1) acc = acc + ctx->gauss[i][t];
+      host[b] = acc;
+    }
+    MRR_CUDA(ctx, cudaMalloc(&ctx->lut[i], n * sizeof(float)));
+    MRR_CUDA(ctx, cudaMemcpy(ctx->lut[i], host.data(), n * sizeof(float), cudaMemcpyHostToDevice));
   }
   MRR_CUDA(ctx, cudaMalloc(&ctx->counts, MRR_MAX_LEVELS * sizeof(uint32_t)));
   MRR_CUDA(ctx, cudaMemset(ctx->counts, 0, MRR_MAX_LEVELS * sizeof(uint32_t)));

@@ -194,9 +194,11 @@ __device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, in
   // no edge within reach of the tile: a_I = 0 here and both passes would add only zeros
   const bool blur = __syncthreads_or(d != 0u) != 0;
   if (blur) {
+    const float* lut = m.lut[I];
     for (int k = tid; k < DN * Ti; k += MTHREADS) {
       const int r = k / Ti, c = k - r * Ti;
-      sm.h[k] = window_sum((sm.D[r] >> c) & WMASK, sm.g[I]);
+      const uint32_t win = (sm.D[r] >> c) & WMASK;
+      sm.h[k] = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
     }
   }
   __syncthreads();

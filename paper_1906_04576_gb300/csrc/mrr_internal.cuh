@@ -96,6 +96,9 @@ struct MaskParams {
   // level 0's horizontal blur as a table: lut0[b] = the ascending-tap sum of g over the
   // set bits of the (2R+1)-bit window b (null: sum the taps directly; R <= 5 only)
   const float* lut0;
+  // levels >= 1: the same tables for their radii, read from global memory (null: sum the
+  // taps directly; R <= MASK_LUT_GLOBAL_R)
+  const float* lut[MRR_MAX_LEVELS];
   // Frame mode (a0c non-null): the kernel also writes every enabled level's work list
   // (tiles in any order, texels of a tile in row-major order), level 0's a only as a0c
   // (aligned with level 0's list), and neither alpha[0] nor stencil[0].
@@ -106,6 +109,7 @@ struct MaskParams {
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
 };
 constexpr int MASK_LUT_MAX = 512;  // level 0's table for R <= 4 (larger R sums the taps)
+constexpr int MASK_LUT_GLOBAL_R = 6;  // tables of the levels above 0 up to 2^13 entries
 
 // Work-list compaction of all levels in one launch: level l owns chunks
 // [chunk_begin[l], chunk_begin[l+1]) of COMPACT_CHUNK texels each.
