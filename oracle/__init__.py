@@ -77,6 +77,7 @@ def _L():
             getattr(lib, f"orc_shade_full_{suf}").argtypes = [P, vp, vp, vp, vp, vp]
             getattr(lib, f"orc_shade_pixel_{suf}").argtypes = [P, vp, vp, vp, vp, ci, ci, vp]
             getattr(lib, f"orc_view_pos_{suf}").argtypes = [P, ci, ci, ctypes.c_double, vp]
+            getattr(lib, f"orc_make_basis_{suf}").argtypes = [vp, vp]
             getattr(lib, f"orc_merge_{suf}").argtypes = [P, vp, vp, vp, vp]
             getattr(lib, f"orc_blur_level_{suf}").argtypes = [P, vp, ci, vp, vp, vp]
             getattr(lib, f"orc_merge_stepwise_{suf}").argtypes = [P, vp, vp, vp, vp]
@@ -288,6 +289,15 @@ def view_pos(frame, cfg, x, y, d, precision="f64"):
     out = np.zeros(3, _dtype(precision))
     getattr(_L(), f"orc_view_pos_{_suffix(precision)}")(b.ref, int(x), int(y), float(d), _ptr(out))
     return out
+
+
+def make_basis(n, precision="f64"):
+    """The tangent frame the effects build around a unit normal n (Duff et al. 2017):
+    rows t, b, n of a 3x3 array, in the oracle's precision."""
+    nn = np.ascontiguousarray(n, np.float64).reshape(3)
+    out = np.zeros(9, _dtype(precision))
+    getattr(_L(), f"orc_make_basis_{_suffix(precision)}")(_ptr(nn), _ptr(out))
+    return out.reshape(3, 3)
 
 
 def level_config(cfg, level):

@@ -984,6 +984,12 @@ int orc_gauss_weights_f64(double sigma2, double* g) { return gauss_weights<doubl
     LightView<T> L = make_light<T>(*p);                                                                      \
     shade_at(*p, v, L, make_inputs(depth, normal, color, smap), x, y, out);                                  \
   }                                                                                                          \
+  void orc_make_basis_##SUF(const double* n, T* out) {                                                     \
+    V3<T> nn = {(T)n[0], (T)n[1], (T)n[2]}, t, b;                                                            \
+    make_basis(nn, t, b);                                                                                    \
+    T v[9] = {t.x, t.y, t.z, b.x, b.y, b.z, nn.x, nn.y, nn.z};                                               \
+    for (int k = 0; k < 9; ++k) out[k] = v[k];                                                               \
+  }                                                                                                          \
   void orc_view_pos_##SUF(const orc_params* p, int x, int y, double d, T* out) {                            \
     View<T> v = make_view<T>(p->width, p->height, p->cam[12], p->cam[13], p->cam[14]);                      \
     V3<T> P = view_pos(v, x, y, (T)d);                                                                       \
