@@ -27,6 +27,9 @@ def test_reference_arm_prints_one_contract_line():
     assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == "Mpix/s"
     assert j["value"] > 0 and j["higher_is_better"] is True and j["warmup"] >= 3
     assert j["config"]["workload"] == "ssao16_256"
+    # the same config dict the GPU arm prints for this workload
+    import scenegen as sg
+    assert j["config"] == bench.config_of("ssao16_256", dict(sg.WORKLOADS["ssao16_256"]), 0, 1)
     cb = j["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == j["value"] and cb["sample"]
     assert j["e2e"] == {"value": j["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
