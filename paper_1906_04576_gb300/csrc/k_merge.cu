@@ -1,20 +1,22 @@
 // k_merge.cu -- upsampling and blending of the sub-images (Sec. 4.2, Eq. (1)).
 //
-// A CTA owns a 32x16 tile of full-resolution pixels (128 threads, so that many tiles are
-// in flight per SM); warp w owns the 4 consecutive rows 4w .. 4w+3 and lane x the column.  Level texel q sits at full-resolution position
-// 2^i q + o_i, so pixel p reads level coordinate u = (p - o_i) / 2^i, whose floor and
-// fraction are exactly (p - o_i) >> i and ((p - o_i) & (2^i - 1)) * 2^-i; the taps
-// floor(u), floor(u)+1 are clamped to the level.  For every level above 0 the CTA stages
-// the (clamped) taps its tile can touch -- (32/2^i + 2) x (16/2^i + 2) texels -- in shared
-// memory once: a_i, the stencil as 0/1 and c_i with unrendered texels replaced by 0, so
-// that w * c and w * s are exactly the terms a rendered tap adds and +0 otherwise.  The
-// 4 rows of a warp touch only 4 / 3 / 2 footprint rows of levels 1 / 2 / 3, which the lane
-// reads once into registers.  A level none of whose staged a_i is positive is skipped
-// for the tile (alpha = 0 there).  Level 0 (one tap, weight 1) is read from global memory,
-// c only where it is blended.  Per pixel, from the coarsest level down: a_i interpolated
-// plainly, c_i over rendered taps with renormalised weights, alpha = min(w_i a_i, 1) and
-// c' = c_i alpha + c' (1 - alpha); the coarsest level is taken as is.  The renormalising
-// division is skipped when the weight sum is exactly 1 (x / 1 = x).
+// merge_kernel: a thread owns a block of 4 x BH full-resolution pixels at (4a, BH b) (BH = 4,
+// or 2 for three-channel images).  Level texel q sits at full-resolution position
+// 2^i q + o_i, so pixel p reads level coordinate u = (p - o_i) / 2^i: taps floor(u) and
+// floor(u) + 1, clamped to the level, with the fraction ((p - o_i) & (2^i - 1)) 2^-i.  Over
+// a block the taps of every level lie in a window of at most 3 x 3 texels, and which window
+// slot a pixel starts at depends only on its place in the block (the block's phase modulo
+// 2^i changes the fractions, never the slots).  The thread reads each level's window once
+// into registers -- a_i, the stencil as 0/1 and c_i with unrendered texels replaced by 0 --
+// and interpolates separably: first along x for every window row, then along y, for â_i
+// (plain), and for the numerator and denominator of the masked bilinear ĉ_i (rendered taps
+// only, weights renormalised).  Per pixel, from the coarsest level down: alpha =
+// min(w_i â_i, 1) where â_i > 0 and c' = c' + alpha (ĉ_i - c'); the coarsest level is taken
+// as is.  A level none of whose window texels has a_i > 0 leaves the block unchanged.
+// Level 0, when the merge blends it (the staged path), is one tap of weight 1 per pixel,
+// blended exactly as blend0_kernel blends it from level 0's list on the frame path.
+// The interpolation differs from the oracle's four-weight sum only in rounding; the
+// discrete step (whether â_i > 0) is the same, since every tap and weight is non-negative.
 //
 // chain_kernel: the step-wise reading of Sec. 3.3 instead -- one launch per step, each
 // level's composite computed at its own resolution from the previous one.
@@ -25,32 +27,6 @@
 namespace mrr {
 
 namespace {
-
-constexpr int MTHR = 128;               // threads per CTA
-constexpr int RPW = 4;                  // consecutive pixel rows per warp
-constexpr int MTX = 32;                 // tile width (pixels): a warp row
-constexpr int MTY = RPW * (MTHR / 32);  // tile height (pixels)
-
-template <int I> struct Lv {
-  static constexpr int side = (MTX >> I) + 2;  // footprint columns of the tile at level I (row stride)
-  static constexpr int rows = (MTY >> I) + 2;  // footprint rows
-  static constexpr int n = side * rows;
-  static constexpr int o = I == 0 ? 0 : (1 << (I - 1));
-  static constexpr int mask = (1 << I) - 1;
-  // footprint rows that the RPW rows of a warp touch (tap rows included)
-  static constexpr int nr = I == 1 ? 4 : (I == 2 ? 3 : 2);
-};
-// staged entries: level 1, then level 2, then level 3
-template <int I> constexpr int lv_off() { return I <= 1 ? 0 : (I == 2 ? Lv<1>::n : Lv<1>::n + Lv<2>::n); }
-constexpr int NTAP = Lv<1>::n + Lv<2>::n + Lv<3>::n;
-static_assert(MTY % 8 == 0 && MTX % 8 == 0, "tiles cover whole level-3 texels");
-
-template <int C> struct MergeSmem {
-  float a[NTAP];
-  float s[NTAP];
-  float cz[C == 4 ? 3 : 1][NTAP];
-  int any[MTHR / 32];
-};
 
 template <typename CT> __device__ __forceinline__ float3 load_c(const void* c, size_t i, int C);
 
@@ -68,289 +44,230 @@ template <> __device__ __forceinline__ float3 load_c<__half>(const void* c, size
   return make_float3(__low2float(xy), __high2float(xy), __low2float(zw));
 }
 
-// One staged footprint entry kk of level I: the clamped texel's stencil, a and c.
-template <typename CT, int C, int I>
-__device__ __forceinline__ void load_entry(const MergeParams& p, int X0, int Y0, int kk, uint8_t& st, float& av,
-                                           float3& cv) {
-  constexpr int side = Lv<I>::side;
-  const int ly = kk / side, lx = kk - ly * side;
+// ---- merge_kernel
+constexpr int MG_TX = 32, MG_TY = 4;  // threads per CTA: 32 blocks across, 4 down
+template <int C> constexpr int mg_bh() { return C == 4 ? 2 : 4; }  // block height (pixels)
+
+// One axis of a level-I window for a block of B pixels starting at a multiple of 4 (x) or
+// of B (y): slot(c) = the window slot of pixel c's first tap, nt() = window size.  The slots
+// are the same for every phase of the block start modulo 2^I (checked by nt_ok below).
+template <int I, int B> struct MgAxis {
+  static constexpr int o = I == 0 ? 0 : (1 << (I - 1));
+  static constexpr int S = 1 << I;
+  static constexpr int fl(int v) { return v >= 0 ? v / S : -((-v + S - 1) / S); }  // floor(v / 2^I)
+  // phase ph = block start modulo 2^I
+  static constexpr int slot_ph(int ph, int c) { return fl(ph + c - o) - fl(ph - o); }
+  static constexpr int frac_ph(int ph, int c) { return (ph + c - o) - fl(ph + c - o) * S; }
+  static constexpr int slot(int c) { return slot_ph(0, c); }
+  static constexpr int nt() {
+    int m = 0;
+    for (int ph = 0; ph < S; ph += (B < S ? B : S))
+      for (int c = 0; c < B; ++c) {
+        const int e = slot_ph(ph, c) + (frac_ph(ph, c) > 0 ? 1 : 0);
+        m = e > m ? e : m;
+      }
+    return m + 1;
+  }
+  static constexpr bool slots_fixed() {
+    for (int ph = 0; ph < S; ph += (B < S ? B : S))
+      for (int c = 0; c < B; ++c)
+        if (slot_ph(ph, c) != slot_ph(0, c)) return false;
+    return true;
+  }
+  // every block start is a multiple of B (and of 4 along x), so the phase is 0 when 2^I <= B
+  static constexpr bool frac_fixed() { return S <= B; }
+};
+static_assert(MgAxis<1, 4>::nt() == 3 && MgAxis<2, 4>::nt() == 3 && MgAxis<3, 4>::nt() == 2, "windows");
+static_assert(MgAxis<1, 2>::nt() == 2 && MgAxis<2, 2>::nt() == 2 && MgAxis<3, 2>::nt() == 2, "windows");
+static_assert(MgAxis<3, 4>::slots_fixed() && MgAxis<3, 2>::slots_fixed() && MgAxis<2, 2>::slots_fixed(), "slots");
+
+// The fraction of pixel c of a block starting at X0 (a multiple of B) at level I.
+template <int I, int B>
+__device__ __forceinline__ float mg_frac(int X0, int c) {
+  using A = MgAxis<I, B>;
+  if (A::frac_fixed()) return (float)A::frac_ph(0, c) * (1.0f / (float)A::S);
+  return (float)((X0 + c - A::o) & (A::S - 1)) * (1.0f / (float)A::S);
+}
+
+__device__ __forceinline__ float mg_lerp(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+// Level I >= 1 over the thread's block (FIRST: the coarsest level, which sets c').
+template <typename CT, int C, int I, int BH, bool FIRST>
+__device__ __forceinline__ void mg_level(const MergeParams& p, int X0, int Y0, float (&cc)[BH][4][C == 4 ? 3 : 1]) {
+  constexpr int NCH = C == 4 ? 3 : 1;
+  using AX = MgAxis<I, 4>;
+  using AY = MgAxis<I, BH>;
+  constexpr int NX = AX::nt(), NY = AY::nt();
   const int Wi = p.Wi[I], Hi = p.Hi[I];
-  // footprint origin: (X0 - o_I) >> I = X0 / 2^I - 1, X0 and Y0 being multiples of 8
-  const int qx = min(max((X0 >> I) - 1 + lx, 0), Wi - 1);
-  const int qy = min(max((Y0 >> I) - 1 + ly, 0), Hi - 1);
-  const size_t q = (size_t)qy * Wi + qx;
-  st = __ldg(p.stencil[I] + q);
-  av = __ldg(p.alpha[I] + q);
-  cv = load_c<CT>(p.c[I], q, C);  // unrendered texels hold stale values, replaced by 0 below
-}
-
-// Stage the footprints of the enabled levels 1..L-1 (entry k of the concatenation
-// level 1, level 2, level 3 in round k / MTHR); every load is issued before the first is
-// used.  Leaves per warp in sm.any bit I when a staged a_I is positive and bit 4 + I when
-// a staged texel of level I is not rendered.
-template <typename CT, int C, int L>
-__device__ __forceinline__ void stage(const MergeParams& p, MergeSmem<C>& sm, int X0, int Y0) {
-  constexpr int N1 = Lv<1>::n, N2 = Lv<2>::n, ROUNDS = (NTAP + MTHR - 1) / MTHR;
-  uint8_t st[ROUNDS];
-  float av[ROUNDS];
-  float3 cv[ROUNDS];
-  int lev[ROUNDS];
+  const int bx = (X0 - AX::o) >> I, by = (Y0 - AY::o) >> I;  // arithmetic shifts: floors
+  int xs[NX], ys[NY];
 #pragma unroll
-  for (int j = 0; j < ROUNDS; ++j) {
-    const int k = threadIdx.x + j * MTHR;
-    lev[j] = 0;
-    st[j] = 0;
-    av[j] = 0.0f;
-    cv[j] = make_float3(0.f, 0.f, 0.f);
-    if (k < N1) {
-      if (L > 1 && p.enabled[1]) {
-        load_entry<CT, C, 1>(p, X0, Y0, k, st[j], av[j], cv[j]);
-        lev[j] = 1;
-      }
-    } else if (k < N1 + N2) {
-      if (L > 2 && p.enabled[2]) {
-        load_entry<CT, C, (L > 2 ? 2 : 1)>(p, X0, Y0, k - N1, st[j], av[j], cv[j]);
-        lev[j] = 2;
-      }
-    } else if (k < NTAP) {
-      if (L > 3) {
-        load_entry<CT, C, (L > 3 ? 3 : 1)>(p, X0, Y0, k - N1 - N2, st[j], av[j], cv[j]);
-        lev[j] = 3;
-      }
-    }
-  }
-  int any = 0;
+  for (int j = 0; j < NX; ++j) xs[j] = min(max(bx + j, 0), Wi - 1);
 #pragma unroll
-  for (int j = 0; j < ROUNDS; ++j) {
-    if (lev[j] == 0) continue;
-    const int k = threadIdx.x + j * MTHR;
-    const bool on = st[j] != 0;
-    sm.a[k] = av[j];
-    sm.s[k] = on ? 1.0f : 0.0f;
-    sm.cz[0][k] = on ? cv[j].x : 0.0f;
-    if (C == 4) {
-      sm.cz[C == 4 ? 1 : 0][k] = on ? cv[j].y : 0.0f;
-      sm.cz[C == 4 ? 2 : 0][k] = on ? cv[j].z : 0.0f;
+  for (int j = 0; j < NY; ++j) ys[j] = min(max(by + j, 0), Hi - 1);
+  float tA[NY][NX], tD[NY][NX], tN[NY][NX][NCH];
+  uint8_t st[NY][NX];
+  float3 cv[NY][NX];
+#pragma unroll
+  for (int r = 0; r < NY; ++r)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const size_t q = (size_t)ys[r] * Wi + xs[j];
+      st[r][j] = __ldg(p.stencil[I] + q);
+      tA[r][j] = FIRST ? 0.0f : __ldg(p.alpha[I] + q);
+      cv[r][j] = load_c<CT>(p.c[I], q, C);  // stale where not rendered: replaced by 0 below
     }
-    if (av[j] > 0.0f) any |= 1 << lev[j];
-    if (!on) any |= 16 << lev[j];
-  }
-  any = __reduce_or_sync(0xffffffffu, any);
-  if ((threadIdx.x & 31) == 0) sm.any[threadIdx.x >> 5] = any;
-}
-
-// Blend of level I >= 1 into the lane's RPW pixels (FIRST: the coarsest level, taken as
-// is).  ALLON: every staged texel of the level is rendered, so the weight sum is exactly 1.
-template <int C, int I, bool FIRST>
-__device__ __forceinline__ void blend_level(const MergeParams& p, const MergeSmem<C>& sm, int lane, int warp,
-                                            bool allon, float (&c)[RPW][3]) {
-  constexpr int side = Lv<I>::side, off = lv_off<I>(), o = Lv<I>::o, mask = Lv<I>::mask, NR = Lv<I>::nr;
-  const float inv = __int_as_float((127 - I) << 23);  // 2^-I
-  const int lx = ((lane - o) >> I) + 1;
-  const float fx = (float)((lane - o) & mask) * inv;
-  const float gx = 1.0f - fx;
-  const int fb = ((RPW * warp - o) >> I) + 1;  // first footprint row of the warp
-  const int base = off + fb * side + lx;
-  float aL[NR], aR[NR];
   if (!FIRST) {
-    uint32_t nz = 0;
+    uint32_t nz = 0u;
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      aL[j] = sm.a[base + j * side];
-      aR[j] = sm.a[base + j * side + 1];
-      nz |= __float_as_uint(aL[j]) | __float_as_uint(aR[j]);
-    }
-    if (nz == 0u) return;  // every tap +0: alpha = 0 for all the lane's pixels
+    for (int r = 0; r < NY; ++r)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) nz |= __float_as_uint(tA[r][j]);
+    if (nz == 0u) return;  // a_i = 0 over the window: alpha = 0 for the whole block
   }
+  bool allon = true;
+#pragma unroll
+  for (int r = 0; r < NY; ++r)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const bool on = st[r][j] != 0;
+      allon = allon && on;
+      tD[r][j] = on ? 1.0f : 0.0f;
+      tN[r][j][0] = on ? cv[r][j].x : 0.0f;
+      if (NCH == 3) {
+        tN[r][j][NCH == 3 ? 1 : 0] = on ? cv[r][j].y : 0.0f;
+        tN[r][j][NCH == 3 ? 2 : 0] = on ? cv[r][j].z : 0.0f;
+      }
+    }
+  // along x, every window row
+  float hA[NY][4], hD[NY][4], hN[NY][4][NCH];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = AX::slot(c);
+    const float f = mg_frac<I, 4>(X0, c);
+    const bool fixed0 = AX::frac_fixed() && AX::frac_ph(0, c) == 0;
+#pragma unroll
+    for (int r = 0; r < NY; ++r) {
+      if (fixed0) {
+        hA[r][c] = tA[r][j];
+        hD[r][c] = tD[r][j];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = tN[r][j][ch];
+      } else {
+        constexpr int JM = NX - 1;
+        const int j1 = j + 1 < NX ? j + 1 : JM;
+        hA[r][c] = FIRST ? 0.0f : mg_lerp(tA[r][j], tA[r][j1], f);
+        hD[r][c] = allon ? 1.0f : mg_lerp(tD[r][j], tD[r][j1], f);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = mg_lerp(tN[r][j][ch], tN[r][j1][ch], f);
+      }
+    }
+  }
+  // along y, and the blend of Eq. (1)
   const float weight = p.weight[I];
 #pragma unroll
-  for (int rr = 0; rr < RPW; ++rr) {
-    // footprint row of the pixel row relative to fb, and its fraction: the same for
-    // every warp at levels 1 and 2 (RPW w is a multiple of 2^I); the row offset is 0 at
-    // level 3, whose fraction depends on the warp's parity
-    const int d = ((rr - o) >> I) - ((-o) >> I);
-    const int fyi = I <= 2 ? ((rr - o) & mask) : ((RPW * warp + rr - o) & mask);
-    const float fy = (float)fyi * inv;
-    const float gy = 1.0f - fy;
-    float alpha = 0.0f;
-    if (!FIRST) {
-      // all four taps +0: ahat = +0 and alpha = 0
-      if ((__float_as_uint(aL[d]) | __float_as_uint(aR[d]) | __float_as_uint(aL[d + 1]) |
-           __float_as_uint(aR[d + 1])) == 0u)
-        continue;
-    }
-    const float w0 = gx * gy, w1 = fx * gy, w2 = gx * fy, w3 = fx * fy;
-    if (!FIRST) {
-      float ahat = 0.0f;
-      ahat = ahat + w0 * aL[d];
-      ahat = ahat + w1 * aR[d];
-      ahat = ahat + w2 * aL[d + 1];
-      ahat = ahat + w3 * aR[d + 1];
-      const float wa = weight * ahat;
-      alpha = (1.0f < wa) ? 1.0f : wa;
-      if (!(alpha > 0.0f)) continue;
-    }
-    const int t0 = base + d * side;
-    const int idx[4] = {t0, t0 + 1, t0 + side, t0 + side + 1};
-    const float w[4] = {w0, w1, w2, w3};
-    float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+  for (int rr = 0; rr < BH; ++rr) {
+    const int j = AY::slot(rr);
+    const int j1 = j + 1 < NY ? j + 1 : NY - 1;
+    const float f = mg_frac<I, BH>(Y0, rr);
+    const bool fixed0 = AY::frac_fixed() && AY::frac_ph(0, rr) == 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      n0 = n0 + w[k] * sm.cz[0][idx[k]];
-      if (C == 4) {
-        n1 = n1 + w[k] * sm.cz[C == 4 ? 1 : 0][idx[k]];
-        n2 = n2 + w[k] * sm.cz[C == 4 ? 2 : 0][idx[k]];
+    for (int c = 0; c < 4; ++c) {
+      float ah = 0.0f, den, num[NCH];
+      if (fixed0) {
+        ah = hA[j][c];
+        den = hD[j][c];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = hN[j][c][ch];
+      } else {
+        if (!FIRST) ah = mg_lerp(hA[j][c], hA[j1][c], f);
+        den = allon ? 1.0f : mg_lerp(hD[j][c], hD[j1][c], f);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = mg_lerp(hN[j][c][ch], hN[j1][c][ch], f);
       }
-    }
-    if (!allon) {
-      float den = 0.f;
+      if (!allon && den != 1.0f) {
+        const float inv = __fdividef(1.0f, den);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) den = den + w[k] * sm.s[idx[k]];
-      if (den != 1.0f) {
-        n0 = n0 / den;
-        if (C == 4) {
-          n1 = n1 / den;
-          n2 = n2 / den;
-        }
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = num[ch] * inv;
       }
-    }
-    if (FIRST) {
-      c[rr][0] = n0;
-      c[rr][1] = n1;
-      c[rr][2] = n2;
-    } else {
-      const float om = 1.0f - alpha;
-      c[rr][0] = n0 * alpha + c[rr][0] * om;
-      if (C == 4) {
-        c[rr][1] = n1 * alpha + c[rr][1] * om;
-        c[rr][2] = n2 * alpha + c[rr][2] * om;
+      if (FIRST) {
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = num[ch];
+      } else if (ah > 0.0f) {
+        const float wa = weight * ah;
+        const float alpha = wa > 1.0f ? 1.0f : wa;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = fmaf(alpha, num[ch] - cc[rr][c][ch], cc[rr][c][ch]);
       }
-    }
-  }
-}
-
-// The coarsest level when it is level 3 and every staged texel is rendered (the weight sum
-// is then exactly 1): a warp's four rows read the same four texels, only the vertical
-// weight differs, so the lane reads the taps once and takes two rows at a time in packed
-// FP32x2 (each half one correctly rounded multiply or add: the scalar form's bits).
-template <int C>
-__device__ __forceinline__ void first_level3(const MergeSmem<C>& sm, int lane, int warp, float (&c)[RPW][3]) {
-  constexpr int I = 3, side = Lv<3>::side, off = lv_off<3>(), o = Lv<3>::o, mask = Lv<3>::mask;
-  constexpr int NCH = C == 4 ? 3 : 1;
-  const float inv = 0.125f;  // 2^-3
-  const int lx = ((lane - o) >> I) + 1;
-  const float fx = (float)((lane - o) & mask) * inv;
-  const float gx = 1.0f - fx;
-  const int t0 = off + (((RPW * warp - o) >> I) + 1) * side + lx;
-  float tap[NCH][4];
-#pragma unroll
-  for (int ch = 0; ch < NCH; ++ch) {
-    tap[ch][0] = sm.cz[ch][t0];
-    tap[ch][1] = sm.cz[ch][t0 + 1];
-    tap[ch][2] = sm.cz[ch][t0 + side];
-    tap[ch][3] = sm.cz[ch][t0 + side + 1];
-  }
-  const float2 gx2 = make_float2(gx, gx), fx2 = make_float2(fx, fx);
-#pragma unroll
-  for (int rr = 0; rr < RPW; rr += 2) {
-    const float2 fy = make_float2((float)((RPW * warp + rr - o) & mask) * inv,
-                                  (float)((RPW * warp + rr + 1 - o) & mask) * inv);
-    const float2 gy = make_float2(1.0f - fy.x, 1.0f - fy.y);
-    const float2 w[4] = {__fmul2_rn(gx2, gy), __fmul2_rn(fx2, gy), __fmul2_rn(gx2, fy), __fmul2_rn(fx2, fy)};
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-      float2 n = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) n = __fadd2_rn(n, __fmul2_rn(w[k], make_float2(tap[ch][k], tap[ch][k])));
-      c[rr][ch] = n.x;
-      c[rr + 1][ch] = n.y;
     }
   }
 }
 
 template <typename CT, int C, int L>
-__global__ void __launch_bounds__(MTHR) merge_kernel(MergeParams p, float* __restrict__ out) {
-  __shared__ MergeSmem<C> sm;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int X0 = blockIdx.x * MTX, Y0 = blockIdx.y * MTY;
+__global__ void __launch_bounds__(MG_TX* MG_TY) merge_kernel(MergeParams p, float* __restrict__ out, int vec) {
+  constexpr int BH = mg_bh<C>(), NCH = C == 4 ? 3 : 1;
+  const int X0 = 4 * (int)(blockIdx.x * MG_TX + threadIdx.x);
+  const int Y0 = BH * (int)(blockIdx.y * MG_TY + threadIdx.y);
   const int W = p.W, H = p.H;
-  const int x = X0 + lane;
-  // level 0 taps first: they need no shared memory
-  float a0[RPW];
-  uint8_t s0[RPW];
-  const bool en0 = p.enabled[0] != 0;
+  if (X0 >= W || Y0 >= H) return;
+  float cc[BH][4][NCH];
+  // coarsest level first (always blended), then every finer enabled level above 0
+  if (L == 4) mg_level<CT, C, (L == 4 ? 3 : 1), BH, true>(p, X0, Y0, cc);
+  if (L == 3) mg_level<CT, C, (L == 3 ? 2 : 1), BH, true>(p, X0, Y0, cc);
+  if (L == 2) mg_level<CT, C, 1, BH, true>(p, X0, Y0, cc);
+  if (L > 3 && p.enabled[2]) mg_level<CT, C, 2, BH, false>(p, X0, Y0, cc);
+  if (L > 2 && p.enabled[1]) mg_level<CT, C, 1, BH, false>(p, X0, Y0, cc);
+  if (L == 1 || p.enabled[0]) {
+    // level 0: one tap of weight 1 per pixel, blended as blend0_kernel does
 #pragma unroll
-  for (int rr = 0; rr < RPW; ++rr) {
-    const int y = Y0 + RPW * warp + rr;
-    a0[rr] = 0.0f;
-    s0[rr] = 0;
-    if (en0 && x < W && y < H) {
-      a0[rr] = __ldg(p.alpha[0] + (size_t)y * W + x);
-      s0[rr] = __ldg(p.stencil[0] + (size_t)y * W + x);
-    }
-  }
-  if (L > 1) stage<CT, C, L>(p, sm, X0, Y0);
-  __syncthreads();
-  if (x >= W) return;
-  int any = 0;
+    for (int rr = 0; rr < BH; ++rr) {
+      const int y = Y0 + rr;
 #pragma unroll
-  for (int k = 0; k < MTHR / 32; ++k) any |= sm.any[k];
-  float c[RPW][3] = {};
-  // coarsest level first, then the finer enabled levels whose footprint holds a_i > 0
-  if (L == 4) {
-    if (!(any & 128)) first_level3<C>(sm, lane, warp, c);
-    else blend_level<C, (L == 4 ? 3 : 1), true>(p, sm, lane, warp, false, c);
-  }
-  if (L == 3) blend_level<C, (L == 3 ? 2 : 1), true>(p, sm, lane, warp, !(any & 64), c);
-  if (L > 3 && p.enabled[2] && (any & 4)) blend_level<C, (L > 3 ? 2 : 1), false>(p, sm, lane, warp, !(any & 64), c);
-  if (L == 2) blend_level<C, 1, true>(p, sm, lane, warp, !(any & 32), c);
-  if (L > 2 && p.enabled[1] && (any & 2)) blend_level<C, 1, false>(p, sm, lane, warp, !(any & 32), c);
-  if (en0) {
-    const bool first = L == 1;
+      for (int c = 0; c < 4; ++c) {
+        const int x = X0 + c;
+        if (y >= H || x >= W) continue;
+        const size_t q = (size_t)y * W + x;
+        const float a0 = __ldg(p.alpha[0] + q);
+        const bool s0 = __ldg(p.stencil[0] + q) != 0;
+        const float3 v = s0 ? load_c<CT>(p.c[0], q, C) : make_float3(0.f, 0.f, 0.f);
+        const float vv[3] = {v.x, v.y, v.z};
+        if (L == 1) {
 #pragma unroll
-    for (int rr = 0; rr < RPW; ++rr) {
-      const int y = Y0 + RPW * warp + rr;
-      if (y >= H) break;
-      const size_t q = (size_t)y * W + x;
-      const float ahat = 0.0f + 1.0f * a0[rr];
-      const float wa = p.weight[0] * ahat;
-      const float alpha = (1.0f < wa) ? 1.0f : wa;
-      if (!first && !(alpha > 0.0f)) continue;
-      float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
-      if (s0[rr]) {
-        const float3 v = load_c<CT>(p.c[0], q, C);
-        n0 = v.x;
-        n1 = v.y;
-        n2 = v.z;
-        den = 1.0f;
-      } else {
-        n0 = n0 / den;  // no rendered tap: 0/0, as the definition gives
-        n1 = n1 / den;
-        n2 = n2 / den;
-      }
-      if (first) {
-        c[rr][0] = n0;
-        c[rr][1] = n1;
-        c[rr][2] = n2;
-      } else {
+          for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = s0 ? vv[ch] : __int_as_float(0x7fc00000);
+          continue;
+        }
+        const float ahat = 0.0f + 1.0f * a0;
+        const float wa = p.weight[0] * ahat;
+        const float alpha = (1.0f < wa) ? 1.0f : wa;
+        if (!(alpha > 0.0f)) continue;
         const float om = 1.0f - alpha;
-        c[rr][0] = n0 * alpha + c[rr][0] * om;
-        if (C == 4) {
-          c[rr][1] = n1 * alpha + c[rr][1] * om;
-          c[rr][2] = n2 * alpha + c[rr][2] * om;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          // no rendered tap: 0/0, as the definition gives (cannot happen where alpha > 0)
+          const float n = s0 ? vv[ch] : __int_as_float(0x7fc00000);
+          cc[rr][c][ch] = n * alpha + cc[rr][c][ch] * om;
         }
       }
     }
   }
 #pragma unroll
-  for (int rr = 0; rr < RPW; ++rr) {
-    const int y = Y0 + RPW * warp + rr;
+  for (int rr = 0; rr < BH; ++rr) {
+    const int y = Y0 + rr;
     if (y >= H) break;
-    const size_t o = (size_t)y * W + x;
-    if (C == 4)
-      reinterpret_cast<float4*>(out)[o] = make_float4(c[rr][0], c[rr][1], c[rr][2], 0.0f);
-    else
-      out[o] = c[rr][0];
+    const size_t o = (size_t)y * W + X0;
+    if (C == 4) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (X0 + c < W)
+          reinterpret_cast<float4*>(out)[o + c] =
+              make_float4(cc[rr][c][0], cc[rr][c][NCH == 3 ? 1 : 0], cc[rr][c][NCH == 3 ? 2 : 0], 0.0f);
+    } else if (vec && X0 + 3 < W) {
+      *reinterpret_cast<float4*>(out + o) = make_float4(cc[rr][0][0], cc[rr][1][0], cc[rr][2][0], cc[rr][3][0]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (X0 + c < W) out[o + c] = cc[rr][c][0];
+    }
   }
 }
 
@@ -646,12 +563,16 @@ __global__ void __launch_bounds__(256) merge_bilateral_kernel(MergeParams p, con
 
 template <typename CT, int C>
 void launch_merge_t(const MergeParams& p, float* out, cudaStream_t s) {
-  dim3 grid((p.W + MTX - 1) / MTX, (p.H + MTY - 1) / MTY);
+  constexpr int BH = mg_bh<C>();
+  const int bw = (p.W + 3) / 4, bh = (p.H + BH - 1) / BH;
+  dim3 grid((bw + MG_TX - 1) / MG_TX, (bh + MG_TY - 1) / MG_TY), block(MG_TX, MG_TY);
+  // four pixels per 16-byte store when every row starts on a 16-byte boundary
+  const int vec = (p.W % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
   switch (p.L) {
-    case 1: merge_kernel<CT, C, 1><<<grid, MTHR, 0, s>>>(p, out); break;
-    case 2: merge_kernel<CT, C, 2><<<grid, MTHR, 0, s>>>(p, out); break;
-    case 3: merge_kernel<CT, C, 3><<<grid, MTHR, 0, s>>>(p, out); break;
-    default: merge_kernel<CT, C, 4><<<grid, MTHR, 0, s>>>(p, out); break;
+    case 1: merge_kernel<CT, C, 1><<<grid, block, 0, s>>>(p, out, vec); break;
+    case 2: merge_kernel<CT, C, 2><<<grid, block, 0, s>>>(p, out, vec); break;
+    case 3: merge_kernel<CT, C, 3><<<grid, block, 0, s>>>(p, out, vec); break;
+    default: merge_kernel<CT, C, 4><<<grid, block, 0, s>>>(p, out, vec); break;
   }
 }
 
