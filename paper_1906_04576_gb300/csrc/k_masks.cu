@@ -1,19 +1,21 @@
 // k_masks.cu -- the per-level masks of Sec. 3.1 / Table 1, the stencil of Sec. 4.1 and
 // the dense work lists that replace the stencil test on the GPU.
 //
-// masks_kernel: ONE launch computes every level, bit-parallel (and, for a whole frame,
-//   the work lists too -- see frame_lists).  A CTA owns a 32x32
-//   full-resolution tile (16x16 at level 1, 8x8 at level 2, ...) and stages the edge
-//   image of the tile plus a 24-pixel halo as bit rows (one ballot per 32 pixels).  For
-//   each blurred level i it forms the downsampled edge image D_i (block maximum: the OR
-//   of 2^i staged rows, each group of 2^i bits OR-ed into one) over the tile and an R_i
-//   halo, takes the horizontal blur of every texel from its (2R_i+1)-bit window (at
-//   level 0 through a table of the exact window sums), the vertical blur with one fused
-//   multiply-add per tap in ascending order, sets S_i = [a_i > 0] OR-ed with its children
-//   in the previous enabled finer level (inclusive nesting, Fig. 2/3 -- children always
-//   lie in the same tile) and writes a_i, S_i.  The coarsest level is written as a = 1,
-//   S = 1; disabled levels as 0.  Finally every pixel's owning level (the finest enabled
-//   level whose stencil covers it), read from the stencil bit rows.
+// masks_kernel: ONE launch computes every level (and, for a whole frame, the work lists
+//   too).  A CTA owns a 32x32 full-resolution tile (16x16 at level 1, 8x8 at level 2, ...)
+//   and stages the edge image of the tile plus a 24-pixel halo as bit rows.  Every tap of
+//   a truncated Gaussian is positive, so a_i > 0 exactly where the (2R_i+1)^2 window of the
+//   downsampled edge image D_i (block maximum) holds an edge: the stencil before nesting
+//   is a box dilation, computed on bit rows -- one warp per level (row ORs of shifted
+//   words, then column ORs across lanes).  Warp 0 then ORs in the children of the previous
+//   enabled finer level (inclusive nesting, Fig. 2/3 -- children always lie in the same
+//   tile) and, for a whole frame, reserves each level's list room with one atomicAdd.
+//   Last, every thread writes its texels: a_i is evaluated only where the dilation is set
+//   -- the horizontal sums from the texel's (2R_i+1)-bit windows (a table of the exact
+//   window sums where one is given), the vertical taps with one fused multiply-add each in
+//   ascending order, the definition's arithmetic exactly -- and is 0 elsewhere.  The
+//   coarsest level is written as a = 1, S = 1; disabled levels as 0.  Staged calls also get
+//   every pixel's owning level (the finest enabled level whose stencil covers it).
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
 //   every level's stencil into a row-major list of (y << 16) | x.  Pass 1 counts the set
 //   texels of each 4096-texel chunk; pass 2 gives each chunk its exclusive prefix (a
@@ -33,23 +35,17 @@ constexpr int ER = TS + 2 * MG;          // 80 staged edge rows
 constexpr int EWORDS = 3;                // 96 staged edge columns: [x0 - 32, x0 + 64)
 constexpr int EX = 32;                   // column of the tile's first pixel in the staged rows
 constexpr int MAXR = 6;
-constexpr int DROWS = TS / 2 + 2 * MAXR; // 28: largest D region side above level 0 (level 1)
 constexpr int MTHREADS = 128;            // threads per CTA
-constexpr int ROWS0 = TS / (MTHREADS / 32);  // level-0 tile rows per warp
-static_assert(ROWS0 % 4 == 0, "level-0 rows come in groups of four");
 static_assert(ER % (MTHREADS / 32) == 0, "edge rows split evenly over the warps");
-static_assert(DROWS <= 32, "a D row of a level above 0 fits one word");
 
 struct MaskSmem {
   uint4 E[ER];                           // edge rows as bits: word w bit b = column 32 w + b (w = 3: zero)
-  uint32_t D[DROWS];                     // D_i rows of the current level >= 1 as bits
-  float h[DROWS * TS / 2];               // horizontal pass of the current level >= 1
+  uint32_t D[MRR_MAX_LEVELS][32];        // D_i rows over the blur region (levels >= 1) as bits
+  uint32_t B[MRR_MAX_LEVELS][TS];        // [a_i > 0] rows (before nesting), tile texels only
+  uint32_t S[MRR_MAX_LEVELS][TS];        // stencil rows of every level, tile texels only
   float g[MRR_MAX_LEVELS][16];           // the Gaussians of Table 1
-  uint32_t S[MRR_MAX_LEVELS][TS];        // stencil rows of every level as bits (tile texels only)
   float lut[MASK_LUT_MAX];
-  // frame mode: level 0's a over the tile, per-row prefix counts and the tile's first
-  // list position per level
-  float a0t[TS][TS];
+  // frame mode: per-row prefix counts and the tile's first list position per level
   uint32_t rowpre[MRR_MAX_LEVELS][TS];
   uint32_t excl[MRR_MAX_LEVELS];
 };
@@ -110,295 +106,358 @@ __device__ __forceinline__ uint32_t d_row(const MaskSmem& sm, int t) {
   return (uint32_t)(full >> (col0 / G)) & ((1u << DN) - 1u);
 }
 
-// Ballot per-lane stencil decisions of a (Ti x Ti) level into row bit masks; texel
-// k = r * Ti + c is handled by thread k.
-template <int Ti>
-__device__ __forceinline__ void store_rows(uint32_t* rows, int k, bool st) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t b = __ballot_sync(0xffffffffu, st);
-  if (k >= Ti * Ti) return;  // the whole row group lies past the level's last texel
-  if (Ti >= 32) {
-    if (lane == 0) rows[k / Ti] = b;
-  } else if ((lane % Ti) == 0) {
-    rows[k / Ti] = (b >> lane) & ((1u << (Ti & 31)) - 1u);
-  }
+// Bits of the tile texels of level I that lie inside the level, for tile row r (0: none).
+template <int I>
+__device__ __forceinline__ uint32_t valid_row(const MaskParams& m, int x0, int y0, int r) {
+  constexpr int Ti = TS >> I;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  if (r >= Ti || q0y + r >= m.Hi[I]) return 0u;
+  const int n = min(Ti, m.Wi[I] - q0x);
+  return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
 }
 
-// Level 0 with radius R: D_0 is the edge image itself.  Warp w owns tile rows
-// [ROWS0 w, ROWS0 w + ROWS0), lane = column; the lane takes the horizontal sums of the
-// ROWS0 + 2R rows it needs from their bit windows (a table of exact window sums where
-// one is given) and the vertical taps from registers.
+// ---- the stencil before nesting, B_i = [a_i > 0], as bits.  Every tap of the truncated
+// Gaussian is positive, so a_i(q) > 0 exactly when the (2R+1) x (2R+1) window of D_i around
+// q holds an edge: B_i is the box dilation of D_i (a sum of non-negative terms with a
+// positive one stays positive in floating point; the smallest product of two taps is far
+// above the underflow threshold).
+
+// Level 0, radius R: lane = tile row.  Row dilation of staged row er: bit c = OR of the
+// columns x0 + c - R .. x0 + c + R.
 template <int R>
-__device__ __forceinline__ void level0_blur(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  // rows per group: a group's horizontal sums (GR + 2R rows) stay in registers; one group
-  // of 8 rows per warp at Table 1's level-0 radius 3 computes 14 row sums where two groups
-  // of 4 computed 20 (the mask launch 34.1 -> 31.9 us at 3840x2160)
-  constexpr int GR = R <= 3 ? 8 : 4;
-  constexpr int NH = GR + 2 * R;
+__device__ __forceinline__ uint32_t row_dilate0(const MaskSmem& sm, int er) {
+  const uint4 row = sm.E[er];
+  const uint32_t lo = __funnelshift_r(row.x, row.y, 32 - R);  // bit k: column x0 - R + k
+  const uint32_t hi = __funnelshift_r(row.y, row.z, 32 - R);  // bit k: column x0 + 32 - R + k
+  const unsigned long long w = ((unsigned long long)hi << 32) | lo;
+  unsigned long long d = 0ull;
+#pragma unroll
+  for (int t = 0; t <= 2 * R; ++t) d |= w >> t;
+  return (uint32_t)d;
+}
+
+template <int R>
+__device__ __forceinline__ void blur_bits0(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  const int lane = threadIdx.x & 31;
+  // dilated rows of tile rows lane - R (a) and 32 + lane - R (b, lanes < 2R)
+  const uint32_t a = row_dilate0<R>(sm, MG - R + lane);
+  const uint32_t b = lane < 2 * R ? row_dilate0<R>(sm, MG - R + 32 + lane) : 0u;
+  uint32_t v = 0u;
+#pragma unroll
+  for (int t = 0; t <= 2 * R; ++t) {
+    const int src = lane + t;
+    const uint32_t va = __shfl_sync(0xffffffffu, a, src & 31);
+    const uint32_t vb = __shfl_sync(0xffffffffu, b, src & 31);
+    v |= src < 32 ? va : vb;
+  }
+  v &= valid_row<0>(m, x0, y0, lane);
+  sm.B[0][lane] = v;
+  sm.S[0][lane] = v;
+}
+
+// Level I >= 1, radius R: lane t < DN computes row t of D_I over the blur region (level
+// rows q0y - R .. q0y + Ti + R - 1, columns q0x - R ..), lane r < Ti the dilation.
+template <int I, int R>
+__device__ __forceinline__ void blur_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  constexpr int Ti = TS >> I, DN = Ti + 2 * R;
+  static_assert(DN <= 32, "a D region fits one warp");
+  const int lane = threadIdx.x & 31;
+  const uint32_t d = lane < DN ? d_row<I, R>(sm, lane) : 0u;
+  if (lane < DN) sm.D[I][lane] = d;
+  uint32_t h = 0u;
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) h |= d >> k;
+  h &= Ti >= 32 ? 0xFFFFFFFFu : ((1u << Ti) - 1u);
+  uint32_t v = 0u;
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) v |= __shfl_sync(0xffffffffu, h, (lane + k) & 31);
+  v &= valid_row<I>(m, x0, y0, lane);
+  if (lane < Ti) {
+    sm.B[I][lane] = v;
+    sm.S[I][lane] = v;
+  }
+}
+
+// Level I as a constant: mode 1 (a = 1, S = 1) or mode 2 (a = 0, S = 0).
+template <int I>
+__device__ __forceinline__ void fill_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0, int mode) {
+  constexpr int Ti = TS >> I;
+  const int lane = threadIdx.x & 31;
+  const uint32_t v = mode == 1 ? valid_row<I>(m, x0, y0, lane) : 0u;
+  if (lane < Ti) {
+    sm.B[I][lane] = v;
+    sm.S[I][lane] = v;
+  }
+}
+
+// One bit per aligned group of G bits (G = 2, 4 or 8).
+template <int G>
+__device__ __forceinline__ uint32_t group_or_any(uint32_t w) {
+  if (G == 8) {
+    uint32_t x = w | (w >> 1);
+    x |= x >> 2;
+    x |= x >> 4;
+    x &= 0x01010101u;
+    return (x | (x >> 7) | (x >> 14) | (x >> 21)) & 0xFu;
+  }
+  return group_or<G == 8 ? 2 : G>(w);
+}
+
+// Inclusive nesting (Fig. 2/3): S_I |= the OR of every child in the previous enabled finer
+// level P, for the texels inside the level.  Lane = tile row of level I.
+template <int I>
+__device__ __forceinline__ void nest_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0, int P) {
+  constexpr int Ti = TS >> I;
+  const int lane = threadIdx.x & 31;
+  if (lane >= Ti) return;
+  const int F = I - P;
+  uint32_t rows = 0u;
+  for (int j = 0; j < (1 << F); ++j) rows |= sm.S[P][(lane << F) + j];
+  const uint32_t kids = F == 1 ? group_or_any<2>(rows) : (F == 2 ? group_or_any<4>(rows) : group_or_any<8>(rows));
+  sm.S[I][lane] |= kids & valid_row<I>(m, x0, y0, lane);
+}
+
+// ---- a_i at one texel, from the same horizontal sums and the same fused multiply-adds
+// in ascending tap order as the definition: h(t) = the ascending sum of the taps over the
+// set bits of the (2R+1)-bit window (a table of the exact window sums where one is given),
+// a = fma(g_2R, h(2R), ... fma(g_0, h(0), 0)).
+
+// Level 0, tile texel (r, lane): windows from the staged edge rows.
+template <int R>
+__device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int r, int lane) {
   constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
-  const int b = EX - R + lane;           // first staged column of the lane's window
+  const int b = EX - R + lane;  // first staged column of the lane's window
   const int k = b >> 5, sh = b & 31;
-  float g[2 * R + 1];
+  float s = 0.0f;
 #pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) g[t] = m.g[0][t];
+  for (int t = 0; t <= 2 * R; ++t) {
+    const uint4 row = sm.E[MG + r - R + t];
+    const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
+    const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
+    const float h = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
+    s = fmaf(sm.g[0][t], h, s);
+  }
+  return s;
+}
+
+// Level I >= 1, tile texel (r, c): windows from the D rows.
+template <int I, int R>
+__device__ __forceinline__ float alpha_at(const MaskParams& m, const MaskSmem& sm, int r, int c) {
+  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
+  const float* lut = m.lut[I];
+  float s = 0.0f;
+#pragma unroll
+  for (int t = 0; t <= 2 * R; ++t) {
+    const uint32_t win = (sm.D[I][r + t] >> c) & WMASK;
+    const float h = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
+    s = fmaf(sm.g[I][t], h, s);
+  }
+  return s;
+}
+
+// ---- writing the levels
+
+// Level 0 (mode 0 blurred, 1 constant one, 2 disabled).  Frame mode: the tile's level-0
+// list entries (tile-local row-major, at the reserved position) and a_0 beside them; staged
+// mode: a_0 and S_0 for every pixel of the tile.  Warp w takes tile rows w, w + 4, ...
+template <int R>
+__device__ __forceinline__ void write_level0(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mode = m.mode[0];
+  const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
   const int x = x0 + lane;
-#pragma unroll 1
-  for (int ty0 = ROWS0 * warp; ty0 < ROWS0 * (warp + 1); ty0 += GR) {
-    float h[NH];
-    uint32_t any = 0;
-#pragma unroll
-    for (int j = 0; j < NH; ++j) {
-      const uint4 row = sm.E[MG + ty0 - R + j];
-      const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
-      const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
-      any |= win;
-      h[j] = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
-    }
-    const bool blur = __any_sync(0xffffffffu, any != 0u);
-#pragma unroll
-    for (int rr = 0; rr < GR; ++rr) {
-      float s = 0.0f;
-      if (blur) {
-#pragma unroll
-        for (int t = 0; t <= 2 * R; ++t) s = fmaf(g[t], h[rr + t], s);
+  const size_t cap = (size_t)m.Wi[0] * m.Hi[0];
+  for (int r = warp; r < TS; r += MTHREADS / 32) {
+    const int y = y0 + r;
+    const uint32_t bits = sm.S[0][r];
+    const bool on = (bits >> lane) & 1u;
+    if (m.a0c) {
+      if (bits == 0u) continue;
+      if (!on) continue;
+      const float a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
+      const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(bits & ((1u << lane) - 1u));
+      if (pos < cap) {
+        m.list[0][pos] = ((uint32_t)y << 16) | (uint32_t)x;
+        m.a0c[pos] = a;
       }
-      const int y = y0 + ty0 + rr;
-      const bool inside = x < m.W && y < m.H;
-      if (m.a0c) {
-        sm.a0t[ty0 + rr][lane] = s;
-      } else if (inside) {
-        m.alpha[0][(size_t)y * m.W + x] = s;
-        m.stencil[0][(size_t)y * m.W + x] = s > 0.0f ? 1 : 0;
-      }
-      const uint32_t bits = __ballot_sync(0xffffffffu, inside && s > 0.0f);
-      if (lane == 0) sm.S[0][ty0 + rr] = bits;
+    } else {
+      if (y >= m.H || x >= m.W || !m.alpha[0]) continue;
+      float a = 0.0f;
+      if (on) a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
+      m.alpha[0][(size_t)y * m.W + x] = a;
+      m.stencil[0][(size_t)y * m.W + x] = on ? 1 : 0;
     }
   }
 }
 
-// Level I >= 1 with blur radius R, nesting from level P (P < 0: none).
-template <int I, int R, int P>
-__device__ __forceinline__ void blur_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  constexpr int Ti = TS >> I, DN = Ti + 2 * R;
-  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
-  const int tid = threadIdx.x;
+// Level I >= 1 (radius R when blurred): a_I and S_I of every tile texel inside the level,
+// and in frame mode the list entries.  Thread k takes texel k of the tile (row-major).
+template <int I, int R>
+__device__ __forceinline__ void write_level(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+  constexpr int Ti = TS >> I;
+  const int mode = m.mode[I];
+  if (mode == 2 && !m.alpha[I]) return;
   const int q0x = x0 >> I, q0y = y0 >> I;
   const int Wi = m.Wi[I], Hi = m.Hi[I];
-  uint32_t d = 0;
-  if (tid < DN) {
-    d = d_row<I, R>(sm, tid);
-    sm.D[tid] = d;
-  }
-  // no edge within reach of the tile: a_I = 0 here and both passes would add only zeros
-  const bool blur = __syncthreads_or(d != 0u) != 0;
-  if (blur) {
-    const float* lut = m.lut[I];
-    for (int k = tid; k < DN * Ti; k += MTHREADS) {
-      const int r = k / Ti, c = k - r * Ti;
-      const uint32_t win = (sm.D[r] >> c) & WMASK;
-      sm.h[k] = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
-    }
-  }
-  __syncthreads();
-  for (int base = 0; base < Ti * Ti; base += MTHREADS) {
-    const int k = base + tid;
+  for (int k = threadIdx.x; k < Ti * Ti; k += MTHREADS) {
     const int r = k / Ti, c = k - r * Ti;
-    const bool mine = k < Ti * Ti;
-    float s = 0.0f;
-    if (mine && blur) {
-#pragma unroll
-      for (int t = 0; t <= 2 * R; ++t) s = fmaf(m.g[I][t], sm.h[(r + t) * Ti + c], s);
-    }
-    bool st = s > 0.0f;
-    if (P >= 0 && mine) {
-      // inclusive nesting: any set child in the previous enabled finer level
-      constexpr int F = P >= 0 ? I - P : 0, GP = 1 << F;
-      uint32_t rows = 0;
-#pragma unroll
-      for (int j = 0; j < GP; ++j) rows |= sm.S[P >= 0 ? P : 0][r * GP + j];
-      st = st || ((rows >> (c * GP)) & ((1u << GP) - 1u)) != 0u;
-    }
     const int qx = q0x + c, qy = q0y + r;
-    const bool inside = mine && qx < Wi && qy < Hi;
-    st = st && inside;
-    if (inside) {
-      m.alpha[I][(size_t)qy * Wi + qx] = s;
-      m.stencil[I][(size_t)qy * Wi + qx] = st ? 1 : 0;
+    if (qx >= Wi || qy >= Hi) continue;
+    const uint32_t srow = sm.S[I][r];
+    const bool st = (srow >> c) & 1u;
+    float a = 0.0f;
+    if (mode == 1) a = 1.0f;
+    else if (mode == 0 && ((sm.B[I][r] >> c) & 1u)) a = alpha_at<I, R>(m, sm, r, c);
+    const size_t q = (size_t)qy * Wi + qx;
+    m.alpha[I][q] = a;
+    m.stencil[I][q] = st ? 1 : 0;
+    if (m.a0c && st && mode != 2) {
+      const size_t pos = (size_t)sm.excl[I] + sm.rowpre[I][r] + __popc(srow & ((1u << c) - 1u));
+      if (pos < (size_t)Wi * Hi) m.list[I][pos] = ((uint32_t)qy << 16) | (uint32_t)qx;
     }
-    store_rows<Ti>(sm.S[I], k, st);
   }
 }
 
-template <int I, int P>
-__device__ __forceinline__ void blur_dispatch(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+// ---- per-level dispatch over the radius (the specialised signatures fix them at compile time)
+
+template <int I>
+__device__ __forceinline__ void bits_any(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  if (m.mode[I] != 0) {
+    fill_bits<I>(m, sm, x0, y0, m.mode[I]);
+    return;
+  }
   if (I == 0) {
     switch (m.R[0]) {
-      case 1: level0_blur<1>(m, sm, x0, y0); break;
-      case 2: level0_blur<2>(m, sm, x0, y0); break;
-      case 3: level0_blur<3>(m, sm, x0, y0); break;
-      case 4: level0_blur<4>(m, sm, x0, y0); break;
-      case 5: level0_blur<5>(m, sm, x0, y0); break;
-      default: level0_blur<6>(m, sm, x0, y0); break;
+      case 1: blur_bits0<1>(m, sm, x0, y0); break;
+      case 2: blur_bits0<2>(m, sm, x0, y0); break;
+      case 3: blur_bits0<3>(m, sm, x0, y0); break;
+      case 4: blur_bits0<4>(m, sm, x0, y0); break;
+      case 5: blur_bits0<5>(m, sm, x0, y0); break;
+      default: blur_bits0<6>(m, sm, x0, y0); break;
     }
     return;
   }
-  constexpr int J = I > 0 ? I : 1;
+  constexpr int J = I == 0 ? 1 : (I > 2 ? 2 : I);  // blurred levels are 0..2
   switch (m.R[J]) {
-    case 1: blur_level<J, 1, P>(m, sm, x0, y0); break;
-    case 2: blur_level<J, 2, P>(m, sm, x0, y0); break;
-    case 3: blur_level<J, 3, P>(m, sm, x0, y0); break;
-    case 4: blur_level<J, 4, P>(m, sm, x0, y0); break;
-    case 5: blur_level<J, 5, P>(m, sm, x0, y0); break;
-    default: blur_level<J, 6, P>(m, sm, x0, y0); break;
+    case 1: blur_bits<J, 1>(m, sm, x0, y0); break;
+    case 2: blur_bits<J, 2>(m, sm, x0, y0); break;
+    case 3: blur_bits<J, 3>(m, sm, x0, y0); break;
+    case 4: blur_bits<J, 4>(m, sm, x0, y0); break;
+    case 5: blur_bits<J, 5>(m, sm, x0, y0); break;
+    default: blur_bits<J, 6>(m, sm, x0, y0); break;
   }
 }
 
-// Level I written as a constant (mode 1: a = 1, S = 1; mode 2: a = 0, S = 0).  Reads no
-// shared memory, so it needs no barrier before it.
 template <int I>
-__device__ __forceinline__ void fill_level(const MaskParams& m, MaskSmem& sm, int x0, int y0, int mode) {
-  constexpr int Ti = TS >> I;
-  const int q0x = x0 >> I, q0y = y0 >> I;
-  const float av = mode == 1 ? 1.0f : 0.0f;
-  const uint8_t sv = mode == 1 ? 1 : 0;
-  for (int base = 0; base < Ti * Ti; base += MTHREADS) {
-    const int k = base + threadIdx.x;
-    const int r = k / Ti, c = k - r * Ti;
-    const bool inside = k < Ti * Ti && q0x + c < m.Wi[I] && q0y + r < m.Hi[I];
-    if (I == 0 && m.a0c) {
-      if (k < Ti * Ti) sm.a0t[r][c] = av;
-    } else if (inside && m.alpha[I]) {
-      m.alpha[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = av;
-      m.stencil[I][(size_t)(q0y + r) * m.Wi[I] + q0x + c] = sv;
+__device__ __forceinline__ void write_any(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+  if (I == 0) {
+    switch (m.mode[0] == 0 ? m.R[0] : 1) {
+      case 1: write_level0<1>(m, sm, x0, y0); break;
+      case 2: write_level0<2>(m, sm, x0, y0); break;
+      case 3: write_level0<3>(m, sm, x0, y0); break;
+      case 4: write_level0<4>(m, sm, x0, y0); break;
+      case 5: write_level0<5>(m, sm, x0, y0); break;
+      default: write_level0<6>(m, sm, x0, y0); break;
     }
-    store_rows<Ti>(sm.S[I], k, inside && mode == 1);
+    return;
+  }
+  constexpr int J = I == 0 ? 1 : I;
+  if (m.mode[J] != 0) {
+    write_level<J, 1>(m, sm, x0, y0);
+    return;
+  }
+  constexpr int K = J > 2 ? 2 : J;  // blurred levels are 0..2
+  switch (m.R[K]) {
+    case 1: write_level<K, 1>(m, sm, x0, y0); break;
+    case 2: write_level<K, 2>(m, sm, x0, y0); break;
+    case 3: write_level<K, 3>(m, sm, x0, y0); break;
+    case 4: write_level<K, 4>(m, sm, x0, y0); break;
+    case 5: write_level<K, 5>(m, sm, x0, y0); break;
+    default: write_level<K, 6>(m, sm, x0, y0); break;
   }
 }
 
-// Level I, whose previous enabled finer level is P (-1: none).
-template <int I, int P>
-__device__ __forceinline__ void do_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  const int mode = m.mode[I];
-  if (mode == 0) blur_dispatch<I, P>(m, sm, x0, y0);
-  else fill_level<I>(m, sm, x0, y0, mode);
-}
-
-// The levels in order; blurred levels are 0..2 (the coarsest, at most 3, is a fill).
-// Shared-memory order: level I's stencil rows are written before level I+1's first
-// barrier and read after it; D and h of level I+1 are written after level I's last
-// reads of them (its second barrier, and level I+1's first).
-__device__ __forceinline__ void all_levels(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  do_level<0, -1>(m, sm, x0, y0);
-  if (m.L < 2) return;
-  const bool en0 = m.mode[0] != 2;
-  if (en0) do_level<1, 0>(m, sm, x0, y0);
-  else do_level<1, -1>(m, sm, x0, y0);
-  if (m.L < 3) return;
-  const bool en1 = m.mode[1] != 2;
-  if (en1) do_level<2, 1>(m, sm, x0, y0);
-  else if (en0) do_level<2, 0>(m, sm, x0, y0);
-  else do_level<2, -1>(m, sm, x0, y0);
-  if (m.L < 4) return;
-  fill_level<3>(m, sm, x0, y0, m.mode[3]);  // level 3 can only be the coarsest
-}
-
-// Level patterns compiled on their own, so that the kernel holds only the code they run
-// (the generic kernel carries every radius of every level, and its instruction footprint
-// stalls warps on instruction fetch):
+// Level patterns compiled on their own, so that the kernel holds only the code they run:
 //   MASK_SIG_T1_4: four levels, levels 0-2 blurred with radii 3, 5, 6 (Table 1's SSAO and
 //                  soft-shadow rows, sigma^2 = 0.924, 1.848, 3.696);
 //   MASK_SIG_T1_GI: four levels, level 1 disabled, levels 0 and 2 blurred with radius 3
 //                  (Table 1's SSGI rows);
 //   MASK_SIG_T1_3: three levels, levels 0 and 1 blurred with radii 3 and 5.
-// The steps and their order are those of all_levels for the same configuration.
 enum { MASK_SIG_ANY = 0, MASK_SIG_T1_4 = 1, MASK_SIG_T1_GI = 2, MASK_SIG_T1_3 = 3 };
 
+// Warp I computes level I's [a > 0] rows (levels 0..3 on warps 0..3).
 template <int SIG>
-__device__ __forceinline__ void all_levels_sig(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+__device__ __forceinline__ void level_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
+  const int warp = threadIdx.x >> 5;
   if constexpr (SIG == MASK_SIG_T1_4) {
-    level0_blur<3>(m, sm, x0, y0);
-    blur_level<1, 5, 0>(m, sm, x0, y0);
-    blur_level<2, 6, 1>(m, sm, x0, y0);
-    fill_level<3>(m, sm, x0, y0, m.mode[3]);
+    if (warp == 0) blur_bits0<3>(m, sm, x0, y0);
+    else if (warp == 1) blur_bits<1, 5>(m, sm, x0, y0);
+    else if (warp == 2) blur_bits<2, 6>(m, sm, x0, y0);
+    else fill_bits<3>(m, sm, x0, y0, m.mode[3]);
   } else if constexpr (SIG == MASK_SIG_T1_GI) {
-    level0_blur<3>(m, sm, x0, y0);
-    fill_level<1>(m, sm, x0, y0, 2);
-    blur_level<2, 3, 0>(m, sm, x0, y0);
-    fill_level<3>(m, sm, x0, y0, m.mode[3]);
+    if (warp == 0) blur_bits0<3>(m, sm, x0, y0);
+    else if (warp == 1) fill_bits<1>(m, sm, x0, y0, 2);
+    else if (warp == 2) blur_bits<2, 3>(m, sm, x0, y0);
+    else fill_bits<3>(m, sm, x0, y0, m.mode[3]);
   } else if constexpr (SIG == MASK_SIG_T1_3) {
-    level0_blur<3>(m, sm, x0, y0);
-    blur_level<1, 5, 0>(m, sm, x0, y0);
-    fill_level<2>(m, sm, x0, y0, m.mode[2]);
+    if (warp == 0) blur_bits0<3>(m, sm, x0, y0);
+    else if (warp == 1) blur_bits<1, 5>(m, sm, x0, y0);
+    else if (warp == 2) fill_bits<2>(m, sm, x0, y0, m.mode[2]);
   } else {
-    all_levels(m, sm, x0, y0);
+    if (warp == 0) bits_any<0>(m, sm, x0, y0);
+    else if (warp == 1 && m.L > 1) bits_any<1>(m, sm, x0, y0);
+    else if (warp == 2 && m.L > 2) bits_any<2>(m, sm, x0, y0);
+    else if (warp == 3 && m.L > 3) fill_bits<3>(m, sm, x0, y0, m.mode[3]);
   }
 }
 
-// ---- frame mode: the work lists of every enabled level, written by the mask kernel
-//
-// Each tile reserves room for its set texels of each level with one atomicAdd on the
-// level's count (zero before the launch), then writes them there in tile-local
+template <int SIG>
+__device__ __forceinline__ void level_values(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+  if constexpr (SIG == MASK_SIG_T1_4) {
+    write_level0<3>(m, sm, x0, y0);
+    write_level<1, 5>(m, sm, x0, y0);
+    write_level<2, 6>(m, sm, x0, y0);
+    write_level<3, 1>(m, sm, x0, y0);
+  } else if constexpr (SIG == MASK_SIG_T1_GI) {
+    write_level0<3>(m, sm, x0, y0);
+    write_level<1, 1>(m, sm, x0, y0);
+    write_level<2, 3>(m, sm, x0, y0);
+    write_level<3, 1>(m, sm, x0, y0);
+  } else if constexpr (SIG == MASK_SIG_T1_3) {
+    write_level0<3>(m, sm, x0, y0);
+    write_level<1, 5>(m, sm, x0, y0);
+    write_level<2, 1>(m, sm, x0, y0);
+  } else {
+    write_any<0>(m, sm, x0, y0);
+    if (m.L > 1) write_any<1>(m, sm, x0, y0);
+    if (m.L > 2) write_any<2>(m, sm, x0, y0);
+    if (m.L > 3) write_any<3>(m, sm, x0, y0);
+  }
+}
+
+// Frame mode: each tile reserves room for its set texels of each level with one atomicAdd
+// on the level's count (zero before the launch); the entries go there in tile-local
 // row-major order.  The order of the tiles within a list is whatever order the tiles
-// reached their atomics; shading never depends on it (every entry is shaded and stored
-// on its own), and the count is exact.
-__device__ __forceinline__ void frame_lists(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t mine = 0;  // lane i: level i's count
+// reached their atomics; shading never depends on it (every entry is shaded and stored on
+// its own), and the count is exact.
+__device__ __forceinline__ void reserve_lists(const MaskParams& m, MaskSmem& sm) {
+  const int lane = threadIdx.x & 31;
+  uint32_t mine = 0;  // lane i: level i's count
 #pragma unroll
-    for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
-      const uint32_t pc = (i < m.L && lane < (TS >> i)) ? (uint32_t)__popc(sm.S[i][lane]) : 0u;
-      uint32_t inc = pc;
+  for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
+    const uint32_t pc = (i < m.L && lane < (TS >> i)) ? (uint32_t)__popc(sm.S[i][lane]) : 0u;
+    uint32_t inc = pc;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-      }
-      if (lane < (TS >> i)) sm.rowpre[i][lane] = inc - pc;
-      const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
-      if (lane == i) mine = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
     }
-    // the levels' reservations go out together (one round trip, not four)
-    uint32_t start = 0u;
-    if (lane < m.L && m.mode[lane] != 2) {
-      start = mine ? atomicAdd(m.counts + lane, mine) : 0u;
-      sm.excl[lane] = start;
-    }
+    if (lane < (TS >> i)) sm.rowpre[i][lane] = inc - pc;
+    const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == i) mine = cnt;
   }
-  __syncthreads();
-  // level 0: warp w owns rows ROWS0 w .. ROWS0 w + ROWS0 - 1, lane = column
-  if (m.mode[0] != 2) {
-    const size_t cap = (size_t)m.Wi[0] * m.Hi[0];
-#pragma unroll
-    for (int rr = 0; rr < ROWS0; ++rr) {
-      const int r = ROWS0 * warp + rr;
-      const uint32_t bits = sm.S[0][r];
-      if ((bits >> lane) & 1u) {
-        const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(bits & ((1u << lane) - 1u));
-        if (pos < cap) {
-          m.list[0][pos] = ((uint32_t)(y0 + r) << 16) | (uint32_t)(x0 + lane);
-          m.a0c[pos] = sm.a0t[r][lane];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 1; i < MRR_MAX_LEVELS; ++i) {
-    if (i >= m.L || m.mode[i] == 2) continue;
-    const int Ti = TS >> i;
-    for (int k = threadIdx.x; k < Ti * Ti; k += MTHREADS) {
-      const int r = k / Ti, c = k - r * Ti;
-      const uint32_t bits = sm.S[i][r];
-      if ((bits >> c) & 1u) {
-        const size_t pos = (size_t)sm.excl[i] + sm.rowpre[i][r] + __popc(bits & ((1u << c) - 1u));
-        if (pos < (size_t)m.Wi[i] * m.Hi[i])
-          m.list[i][pos] = ((uint32_t)((y0 >> i) + r) << 16) | (uint32_t)((x0 >> i) + c);
-      }
-    }
-  }
+  // the levels' reservations go out together (one round trip, not four)
+  if (lane < m.L && m.mode[lane] != 2) sm.excl[lane] = mine ? atomicAdd(m.counts + lane, mine) : 0u;
 }
 
 template <int SIG>
@@ -474,10 +533,29 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
     for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   __syncthreads();
-  all_levels_sig<SIG>(m, sm, x0, y0);
-  if (m.a0c) frame_lists(m, sm, x0, y0);
+  // 1. [a_i > 0] of every level as bit rows (one warp per level)
+  level_bits<SIG>(m, sm, x0, y0);
+  __syncthreads();
+  // 2. inclusive nesting, finer to coarser (warp 0)
+  if (warp == 0) {
+    int prev = m.mode[0] != 2 ? 0 : -1;
+    for (int i = 1; i < m.L; ++i) {
+      if (m.mode[i] == 2) continue;
+      if (m.mode[i] == 0 && prev >= 0) {
+        if (i == 1) nest_bits<1>(m, sm, x0, y0, prev);
+        else if (i == 2) nest_bits<2>(m, sm, x0, y0, prev);
+        else nest_bits<3>(m, sm, x0, y0, prev);
+        __syncwarp();
+      }
+      prev = i;
+    }
+    // 3. frame mode: list reservations
+    if (m.a0c) reserve_lists(m, sm);
+  }
+  __syncthreads();
+  // 4. a_i where it is positive, every level's outputs
+  level_values<SIG>(m, sm, x0, y0);
   if (m.label) {
-    __syncthreads();
     for (int r = warp; r < TS; r += MTHREADS / 32) {
       const int y = y0 + r, x = x0 + lane;
       if (y >= H || x >= W) continue;

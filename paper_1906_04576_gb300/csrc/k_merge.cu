@@ -91,6 +91,77 @@ __device__ __forceinline__ float mg_frac(int X0, int c) {
 
 __device__ __forceinline__ float mg_lerp(float a, float b, float f) { return fmaf(f, b - a, a); }
 
+// Interpolation of one level's window over the block and the blend of Eq. (1).  MASKED:
+// some window tap is not rendered, so the denominator of the masked bilinear varies.
+template <int I, int BH, int NX, int NY, int NCH, bool FIRST, bool MASKED>
+__device__ __forceinline__ void mg_blend(const MergeParams& p, int X0, int Y0, const float (&tA)[NY][NX],
+                                         const float (&tD)[NY][NX], const float (&tN)[NY][NX][NCH],
+                                         float (&cc)[BH][4][NCH]) {
+  using AX = MgAxis<I, 4>;
+  using AY = MgAxis<I, BH>;
+  // along x, every window row
+  float hA[NY][4], hD[NY][4], hN[NY][4][NCH];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = AX::slot(c);
+    const int j1 = j + 1 < NX ? j + 1 : NX - 1;
+    const float f = mg_frac<I, 4>(X0, c);
+    const bool fixed0 = AX::frac_fixed() && AX::frac_ph(0, c) == 0;
+#pragma unroll
+    for (int r = 0; r < NY; ++r) {
+      if (fixed0) {
+        if (!FIRST) hA[r][c] = tA[r][j];
+        if (MASKED) hD[r][c] = tD[r][j];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = tN[r][j][ch];
+      } else {
+        if (!FIRST) hA[r][c] = mg_lerp(tA[r][j], tA[r][j1], f);
+        if (MASKED) hD[r][c] = mg_lerp(tD[r][j], tD[r][j1], f);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = mg_lerp(tN[r][j][ch], tN[r][j1][ch], f);
+      }
+    }
+  }
+  // along y, and the blend
+  const float weight = p.weight[I];
+#pragma unroll
+  for (int rr = 0; rr < BH; ++rr) {
+    const int j = AY::slot(rr);
+    const int j1 = j + 1 < NY ? j + 1 : NY - 1;
+    const float f = mg_frac<I, BH>(Y0, rr);
+    const bool fixed0 = AY::frac_fixed() && AY::frac_ph(0, rr) == 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float ah = 0.0f, den = 1.0f, num[NCH];
+      if (fixed0) {
+        if (!FIRST) ah = hA[j][c];
+        if (MASKED) den = hD[j][c];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = hN[j][c][ch];
+      } else {
+        if (!FIRST) ah = mg_lerp(hA[j][c], hA[j1][c], f);
+        if (MASKED) den = mg_lerp(hD[j][c], hD[j1][c], f);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = mg_lerp(hN[j][c][ch], hN[j1][c][ch], f);
+      }
+      if (MASKED) {
+        // no rendered tap of positive weight: a_hat is 0 there too (a > 0 only where S = 1)
+        const float inv = den > 0.0f ? __fdividef(1.0f, den) : 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) num[ch] = den == 1.0f ? num[ch] : num[ch] * inv;
+      }
+      if (FIRST) {
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = num[ch];
+      } else {
+        const float alpha = __saturatef(weight * ah);  // min(w a_hat, 1), a_hat >= 0
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = fmaf(alpha, num[ch] - cc[rr][c][ch], cc[rr][c][ch]);
+      }
+    }
+  }
+}
+
 // Level I >= 1 over the thread's block (FIRST: the coarsest level, which sets c').
 template <typename CT, int C, int I, int BH, bool FIRST>
 __device__ __forceinline__ void mg_level(const MergeParams& p, int X0, int Y0, float (&cc)[BH][4][C == 4 ? 3 : 1]) {
@@ -129,77 +200,35 @@ __device__ __forceinline__ void mg_level(const MergeParams& p, int X0, int Y0, f
 #pragma unroll
   for (int r = 0; r < NY; ++r)
 #pragma unroll
-    for (int j = 0; j < NX; ++j) {
-      const bool on = st[r][j] != 0;
-      allon = allon && on;
-      tD[r][j] = on ? 1.0f : 0.0f;
-      tN[r][j][0] = on ? cv[r][j].x : 0.0f;
-      if (NCH == 3) {
-        tN[r][j][NCH == 3 ? 1 : 0] = on ? cv[r][j].y : 0.0f;
-        tN[r][j][NCH == 3 ? 2 : 0] = on ? cv[r][j].z : 0.0f;
+    for (int j = 0; j < NX; ++j) allon = allon && st[r][j] != 0;
+  if (allon) {
+    // every tap rendered: the weight sum is exactly 1, so c_hat is the plain interpolation,
+    // and alpha = sat(w a_hat) blends every pixel (alpha = 0 leaves c' unchanged exactly)
+#pragma unroll
+    for (int r = 0; r < NY; ++r)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        tN[r][j][0] = cv[r][j].x;
+        if (NCH == 3) {
+          tN[r][j][NCH == 3 ? 1 : 0] = cv[r][j].y;
+          tN[r][j][NCH == 3 ? 2 : 0] = cv[r][j].z;
+        }
       }
-    }
-  // along x, every window row
-  float hA[NY][4], hD[NY][4], hN[NY][4][NCH];
+    mg_blend<I, BH, NX, NY, NCH, FIRST, false>(p, X0, Y0, tA, tD, tN, cc);
+  } else {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int j = AX::slot(c);
-    const float f = mg_frac<I, 4>(X0, c);
-    const bool fixed0 = AX::frac_fixed() && AX::frac_ph(0, c) == 0;
+    for (int r = 0; r < NY; ++r)
 #pragma unroll
-    for (int r = 0; r < NY; ++r) {
-      if (fixed0) {
-        hA[r][c] = tA[r][j];
-        hD[r][c] = tD[r][j];
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = tN[r][j][ch];
-      } else {
-        constexpr int JM = NX - 1;
-        const int j1 = j + 1 < NX ? j + 1 : JM;
-        hA[r][c] = FIRST ? 0.0f : mg_lerp(tA[r][j], tA[r][j1], f);
-        hD[r][c] = allon ? 1.0f : mg_lerp(tD[r][j], tD[r][j1], f);
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) hN[r][c][ch] = mg_lerp(tN[r][j][ch], tN[r][j1][ch], f);
+      for (int j = 0; j < NX; ++j) {
+        const bool on = st[r][j] != 0;
+        tD[r][j] = on ? 1.0f : 0.0f;
+        tN[r][j][0] = on ? cv[r][j].x : 0.0f;
+        if (NCH == 3) {
+          tN[r][j][NCH == 3 ? 1 : 0] = on ? cv[r][j].y : 0.0f;
+          tN[r][j][NCH == 3 ? 2 : 0] = on ? cv[r][j].z : 0.0f;
+        }
       }
-    }
-  }
-  // along y, and the blend of Eq. (1)
-  const float weight = p.weight[I];
-#pragma unroll
-  for (int rr = 0; rr < BH; ++rr) {
-    const int j = AY::slot(rr);
-    const int j1 = j + 1 < NY ? j + 1 : NY - 1;
-    const float f = mg_frac<I, BH>(Y0, rr);
-    const bool fixed0 = AY::frac_fixed() && AY::frac_ph(0, rr) == 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float ah = 0.0f, den, num[NCH];
-      if (fixed0) {
-        ah = hA[j][c];
-        den = hD[j][c];
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) num[ch] = hN[j][c][ch];
-      } else {
-        if (!FIRST) ah = mg_lerp(hA[j][c], hA[j1][c], f);
-        den = allon ? 1.0f : mg_lerp(hD[j][c], hD[j1][c], f);
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) num[ch] = mg_lerp(hN[j][c][ch], hN[j1][c][ch], f);
-      }
-      if (!allon && den != 1.0f) {
-        const float inv = __fdividef(1.0f, den);
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) num[ch] = num[ch] * inv;
-      }
-      if (FIRST) {
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = num[ch];
-      } else if (ah > 0.0f) {
-        const float wa = weight * ah;
-        const float alpha = wa > 1.0f ? 1.0f : wa;
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) cc[rr][c][ch] = fmaf(alpha, num[ch] - cc[rr][c][ch], cc[rr][c][ch]);
-      }
-    }
+    mg_blend<I, BH, NX, NY, NCH, FIRST, true>(p, X0, Y0, tA, tD, tN, cc);
   }
 }
 
