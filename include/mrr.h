@@ -302,7 +302,12 @@ mrr_status mrr_render_host_wait(mrr_ctx* ctx);
  *    missing buffers) return MRR_EINVAL before anything is launched.
  *  - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
  *  - The first call on each device looks the array's device address up (with that
- *    device current); make that first call before any stream capture.
+ *    device current) and keeps it; make that first call before any stream capture.
+ *    Under lazy module loading (CUDA's default) that first lookup may also make the
+ *    driver load this library's device code, which reserves device memory once; a
+ *    caller with a strict budget should make the first call during its own set-up.
+ *    The kept address belongs to the device's primary context: after a
+ *    cudaDeviceReset in the same process it is stale, so do not call this again then.
  *  - Every call shares the array: calls that overlap on the GPU (other streams, other
  *    host threads) race on it; order them.  Returns MRR_ECUDA on a launch failure. */
 mrr_status mrr_masks_static(const mrr_config* cfg, const uint8_t* edges_dev, const mrr_levels* lv, void* stream);

@@ -321,7 +321,7 @@ class DeviceFrame:
     normal: torch.Tensor                  # float32 [H][W][4] or float16 [H][W][4]
     cam: object
     color: torch.Tensor | None = None     # float16 [H][W][4]
-    shadow_map: torch.Tensor | None = None  # float32 / float16 [S][S]
+    shadow_map: torch.Tensor | None = None  # float32 [S][S] (light depth stays FP32 in both precisions)
     light: object = None
 
     def struct(self) -> mrr_gbuffer:
@@ -346,7 +346,7 @@ def upload_frame(frame, precision: str = "fp32", device="cuda") -> DeviceFrame:
     color = torch.from_numpy(frame.color).to(device=device, dtype=torch.float16)
     sm = None
     if frame.shadow_map is not None:
-        sm = torch.from_numpy(frame.shadow_map).to(device=device, dtype=ndt)
+        sm = torch.from_numpy(frame.shadow_map).to(device=device, dtype=torch.float32)  # FP32 in both precisions
     return DeviceFrame(frame.width, frame.height, depth, normal.contiguous(), frame.cam, color.contiguous(), sm,
                        frame.light)
 
@@ -439,7 +439,14 @@ def mrr_autotune(ctx: Context, frame: DeviceFrame, stream=None) -> dict:
 
 
 def mrr_masks_static(cfg: dict, edges: torch.Tensor, levels: Levels, stream=None) -> None:
-    """The mask stage without a context and without any allocation (see include/mrr.h)."""
+    """The mask stage without a context and without any allocation (see include/mrr.h).
+
+    The C side cannot check what a device pointer refers to, so the edge image is checked
+    here: a uint8 (H, W) tensor on the current CUDA device."""
+    if (not isinstance(edges, torch.Tensor) or edges.dtype != torch.uint8 or not edges.is_cuda
+            or tuple(edges.shape) != (levels.dims[0][1], levels.dims[0][0]) or not edges.is_contiguous()
+            or edges.device.index != torch.cuda.current_device()):
+        raise ValueError("edges must be a contiguous uint8 (H, W) tensor on the current CUDA device")
     c, keep = make_config(cfg)
     lv = levels.struct()
     st = _lib.mrr_masks_static(ctypes.byref(c), _ptr(edges), ctypes.byref(lv), _stream(stream))
@@ -680,7 +687,7 @@ class HostFrame:
 def pin_frame(frame, precision: str = "fp32") -> HostFrame:
     ndt = torch.float16 if precision == "fp16" else torch.float32
     pin = lambda a, dt=None: (torch.from_numpy(a) if dt is None else torch.from_numpy(a).to(dt)).contiguous().pin_memory()
-    sm = None if frame.shadow_map is None else pin(frame.shadow_map, ndt)
+    sm = None if frame.shadow_map is None else pin(frame.shadow_map, torch.float32)
     return HostFrame(frame.width, frame.height, pin(frame.depth), pin(frame.normal, ndt), frame.cam,
                      pin(frame.color, torch.float16), sm, frame.light)
 

@@ -167,20 +167,6 @@ LightC make_light(const mrr_gbuffer& g) {
   return L;
 }
 
-// Truncated Gaussian of Sec. 3.1: R = ceil(3 sigma), weights exp(-k^2 / (2 sigma^2))
-// normalised over [-R, R] in double (ascending k), rounded once to float.
-int gauss_weights(double sigma2, float* g) {
-  const int R = (int)std::ceil(3.0 * std::sqrt(sigma2));
-  double e[16];
-  double sum = 0.0;
-  for (int k = -R; k <= R; ++k) {
-    e[k + R] = std::exp(-(double)(k * k) / (2.0 * sigma2));
-    sum += e[k + R];
-  }
-  for (int k = 0; k <= 2 * R; ++k) g[k] = (float)(e[k] / sum);
-  return R;
-}
-
 mrr_status check_gbuffer(mrr_ctx* ctx, const mrr_gbuffer* g, bool need_device_align = true) {
   if (!g) return fail(ctx, MRR_EINVAL, "gbuffer is NULL");
   if (g->width < 1 || g->height < 1 || g->width > MAX_DIM || g->height > MAX_DIM)
@@ -327,24 +313,8 @@ mrr_status check_levels(mrr_ctx* ctx, const mrr_levels* lv, bool need_lists) {
 }
 
 MaskParams mask_params(const mrr_ctx* ctx, const mrr_levels* lv) {
-  const mrr_config& c = ctx->cfg;
   MaskParams m;
-  std::memset(&m, 0, sizeof m);
-  m.W = lv->width[0];
-  m.H = lv->height[0];
-  m.L = c.num_levels;
-  for (int i = 0; i < c.num_levels; ++i) {
-    if (!c.enabled[i]) m.mode[i] = 2;
-    else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) m.mode[i] = 1;
-    else m.mode[i] = 0;
-    m.R[i] = ctx->R[i];
-    std::memcpy(m.g[i], ctx->gauss[i], sizeof m.g[i]);
-    m.Wi[i] = lv->width[i];
-    m.Hi[i] = lv->height[i];
-    m.alpha[i] = lv->alpha[i];
-    m.stencil[i] = lv->stencil[i];
-  }
-  m.label = lv->label;
+  mask_level_params(ctx->cfg, lv, m);  // the configuration was validated by mrr_create
   m.lut0 = ctx->lut0;
   for (int i = 1; i < MRR_MAX_LEVELS; ++i) m.lut[i] = ctx->lut[i];
   return m;
@@ -400,7 +370,7 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.ewords = (g->width + 31) / 32;
   if (p.ssm && ctx->sbits && g->width <= ctx->pool_W && g->height <= ctx->pool_H) p.sbits = ctx->sbits;
   const int h = ctx->cfg.precision == MRR_FP16;
-  MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, g->shadow_map, h, E, s));
+  MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, (const float*)g->shadow_map, E, s));
   return MRR_OK;
 }
 
@@ -924,7 +894,7 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
   std::memset(ctx->gauss, 0, sizeof ctx->gauss);
   for (int i = 0; i < c.num_levels; ++i) {
     ctx->R[i] = 0;
-    if (c.enabled[i] && i < c.num_levels - 1 && c.sigma2[i] > 0.f) ctx->R[i] = gauss_weights((double)c.sigma2[i], ctx->gauss[i]);
+    if (c.enabled[i] && i < c.num_levels - 1 && c.sigma2[i] > 0.f) ctx->R[i] = mask_gauss((double)c.sigma2[i], ctx->gauss[i]);
   }
   mrr_status st = alloc_pools(ctx);
   if (st != MRR_OK) {
@@ -1558,7 +1528,7 @@ mrr_status mrr_render_host_async(mrr_ctx* ctx, const mrr_gbuffer* gh, float* out
   const size_t npx_max = (size_t)ctx->pool_W * ctx->pool_H, npx = (size_t)W * H;
   const size_t nbytes = c.precision == MRR_FP16 ? 8 : 16;
   const size_t sm_bytes = c.effect == MRR_SSM
-                              ? (size_t)gh->shadow_size * gh->shadow_size * (c.precision == MRR_FP16 ? 2 : 4)
+                              ? (size_t)gh->shadow_size * gh->shadow_size * sizeof(float)
                               : 0;
   for (cudaStream_t* sp : {&ctx->s_in, &ctx->s_comp, &ctx->s_out})
     if (!*sp) MRR_CUDA(ctx, cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking));
@@ -1635,7 +1605,7 @@ mrr_status mrr_render_host(mrr_ctx* ctx, const mrr_gbuffer* gh, float* out_host,
     if (c.effect == MRR_SSGI) MRR_CUDA(ctx, cudaMalloc(&ctx->h_color, npx_max * 8));
   }
   const size_t sm_bytes = c.effect == MRR_SSM
-                              ? (size_t)gh->shadow_size * gh->shadow_size * (c.precision == MRR_FP16 ? 2 : 4)
+                              ? (size_t)gh->shadow_size * gh->shadow_size * sizeof(float)
                               : 0;
   if (sm_bytes > ctx->h_smap_bytes) {
     cudaFree(ctx->h_smap);

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4) shade_batch_kernel(const Bat
       const int o = i == 0 ? 0 : (1 << (i - 1));
       const int x = min((qx << i) + o, it.p.v.W - 1), y = min((qy << i) + o, it.p.v.H - 1);
       float3 v;
-      if (it.precision == MRR_FP16) v = batch_effect<half4, __half>(it.p, it.in, x, y);
+      if (it.precision == MRR_FP16) v = batch_effect<half4, float>(it.p, it.in, x, y);
       else v = batch_effect<float4, float>(it.p, it.in, x, y);
       const size_t at = ((it.lv.compact >> k) & 1) ? (size_t)(g - s_pre[s]) : (size_t)qy * it.lv.Wi[k] + qx;
       batch_store(it.lv.c[k], at, v, it.p.effect, it.precision == MRR_FP16);

@@ -474,7 +474,7 @@ void edges_prepare() {
 }
 
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
-                         const void* smap, int half_smap, uint8_t* E, cudaStream_t s) {
+                         const float* smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
   if (!p.ssm) {
     const bool tma = half_normal ? launch_edges_tma<half4>(p, depth, normal, nullptr, E, s)
@@ -484,21 +484,13 @@ cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* no
       if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);
       else edges_direct_kernel<float4><<<dgrid, block, 0, s>>>(p, depth, (const float4*)normal, E);
     }
-  } else if (p.sbits && (half_normal ? (half_smap ? launch_edges_tma<half4, __half>(p, depth, normal, smap, E, s)
-                                                  : launch_edges_tma<half4, float>(p, depth, normal, smap, E, s))
-                                     : (half_smap ? launch_edges_tma<float4, __half>(p, depth, normal, smap, E, s)
-                                                  : launch_edges_tma<float4, float>(p, depth, normal, smap, E, s)))) {
+  } else if (p.sbits && (half_normal ? launch_edges_tma<half4, float>(p, depth, normal, smap, E, s)
+                                     : launch_edges_tma<float4, float>(p, depth, normal, smap, E, s))) {
     // soft shadows, two passes: shadow bits, then the TMA edge kernel
   } else if (half_normal) {
-    if (half_smap)
-      edges_kernel<half4, __half><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const __half*)smap, E);
-    else
-      edges_kernel<half4, float><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, (const float*)smap, E);
+    edges_kernel<half4, float><<<grid, block, 0, s>>>(p, depth, (const half4*)normal, smap, E);
   } else {
-    if (half_smap)
-      edges_kernel<float4, __half><<<grid, block, 0, s>>>(p, depth, (const float4*)normal, (const __half*)smap, E);
-    else
-      edges_kernel<float4, float><<<grid, block, 0, s>>>(p, depth, (const float4*)normal, (const float*)smap, E);
+    edges_kernel<float4, float><<<grid, block, 0, s>>>(p, depth, (const float4*)normal, smap, E);
   }
   count_launches(1);
   return cudaGetLastError();

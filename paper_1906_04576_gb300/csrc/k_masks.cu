@@ -23,6 +23,9 @@
 //   texels at once, and a warp shuffle scan plus the per-warp totals give each lane its
 //   output position, so list order = index order and no warp of the shading kernel idles
 //   on an unmasked texel.
+#include <cmath>
+#include <cstring>
+
 #include "mrr_internal.cuh"
 
 namespace mrr {
@@ -670,6 +673,44 @@ int mask_signature(const MaskParams& m) {
   if (m.L == 4 && b0 && m.mode[1] == 2 && m.mode[2] == 0 && m.R[2] == 3) return MASK_SIG_T1_GI;
   if (m.L == 3 && b0 && m.mode[1] == 0 && m.R[1] == 5) return MASK_SIG_T1_3;
   return MASK_SIG_ANY;
+}
+
+int mask_gauss(double sigma2, float* g) {
+  if (!(sigma2 > 0.0)) return 0;
+  const int R = (int)std::ceil(3.0 * std::sqrt(sigma2));
+  if (R > 6) return R;
+  double e[16];
+  double sum = 0.0;
+  for (int k = -R; k <= R; ++k) {
+    e[k + R] = std::exp(-(double)(k * k) / (2.0 * sigma2));
+    sum += e[k + R];
+  }
+  for (int k = 0; k <= 2 * R; ++k) g[k] = (float)(e[k] / sum);
+  return R;
+}
+
+bool mask_level_params(const mrr_config& c, const mrr_levels* lv, MaskParams& m) {
+  std::memset(&m, 0, sizeof m);
+  m.W = lv->width[0];
+  m.H = lv->height[0];
+  m.L = c.num_levels;
+  for (int i = 0; i < c.num_levels; ++i) {
+    if (!c.enabled[i]) {
+      m.mode[i] = 2;
+    } else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) {
+      m.mode[i] = 1;
+    } else {
+      m.mode[i] = 0;
+      m.R[i] = mask_gauss((double)c.sigma2[i], m.g[i]);
+      if (m.R[i] < 1 || m.R[i] > 6) return false;
+    }
+    m.Wi[i] = lv->width[i];
+    m.Hi[i] = lv->height[i];
+    m.alpha[i] = lv->alpha[i];
+    m.stencil[i] = lv->stencil[i];
+  }
+  m.label = lv->label;
+  return true;
 }
 
 cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s) {

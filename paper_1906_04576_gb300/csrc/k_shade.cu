@@ -322,7 +322,7 @@ int shade_grid_blocks() { return 1; }  // the launch scales the resident CTAs of
 
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
                                 int grid, int split, cudaStream_t s) {
-  if (precision == MRR_FP16) levels_dispatch<half4, __half>(p, in, lv, 1, grid, split, s);
+  if (precision == MRR_FP16) levels_dispatch<half4, float>(p, in, lv, 1, grid, split, s);
   else levels_dispatch<float4, float>(p, in, lv, 0, grid, split, s);
   count_launches(1);
   return cudaGetLastError();
@@ -337,7 +337,7 @@ cudaError_t launch_pyramid(const PyramidParams& p, cudaStream_t s) {
 
 cudaError_t launch_shade_blocks(const ShadeParams& p, const FrameIn& in, int precision, const BlockLevel& b,
                                 int grid_mult, cudaStream_t s) {
-  if (precision == MRR_FP16) blocks_dispatch<half4, __half>(p, in, b, 1, grid_mult, s);
+  if (precision == MRR_FP16) blocks_dispatch<half4, float>(p, in, b, 1, grid_mult, s);
   else blocks_dispatch<float4, float>(p, in, b, 0, grid_mult, s);
   count_launches(1);
   return cudaGetLastError();
@@ -345,7 +345,7 @@ cudaError_t launch_shade_blocks(const ShadeParams& p, const FrameIn& in, int pre
 
 cudaError_t launch_shade_full(const ShadeParams& p, const FrameIn& in, int precision, float* out, int split,
                               cudaStream_t s) {
-  if (precision == MRR_FP16) full_dispatch<half4, __half>(p, in, out, split, s);
+  if (precision == MRR_FP16) full_dispatch<half4, float>(p, in, out, split, s);
   else full_dispatch<float4, float>(p, in, out, split, s);
   count_launches(1);
   return cudaGetLastError();

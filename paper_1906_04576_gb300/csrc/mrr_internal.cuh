@@ -94,7 +94,7 @@ struct MaskParams {
   uint8_t* stencil[MRR_MAX_LEVELS];
   uint8_t* label;                // [H][W] or null
   // level 0's horizontal blur as a table: lut0[b] = the ascending-tap sum of g over the
-  // set bits of the (2R+1)-bit window b (null: sum the taps directly; R <= 5 only)
+  // set bits of the (2R+1)-bit window b (null: sum the taps directly; any R <= 6)
   const float* lut0;
   // levels >= 1: the same tables for their radii, read from global memory (null: sum the
   // taps directly; R <= MASK_LUT_GLOBAL_R)
@@ -109,6 +109,17 @@ struct MaskParams {
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
 };
 constexpr int MASK_LUT_MAX = 512;  // level 0's table for R <= 4 (larger R sums the taps)
+
+// The truncated Gaussian of Sec. 3.1 / Table 1: R = ceil(3 sigma), weights
+// exp(-k^2 / (2 sigma^2)) normalised over [-R, R] in double (ascending k), rounded once to
+// float.  Returns R (0 when sigma2 <= 0).
+int mask_gauss(double sigma2, float* g);
+
+// Fills the parts of a MaskParams that follow from the configuration and the level
+// buffers: sizes, per-level mode (0 blur, 1 all ones, 2 disabled), radius and taps, the
+// output planes and the label plane.  Returns false when a
+// blurred level has sigma2 <= 0 or a radius above 6.
+bool mask_level_params(const mrr_config& c, const mrr_levels* lv, MaskParams& m);
 constexpr int MASK_LUT_GLOBAL_R = 6;  // tables of the levels above 0 up to 2^13 entries
 
 // Work-list compaction of all levels in one launch: level l owns chunks
@@ -228,7 +239,7 @@ struct BlurParams {
 
 // ---- launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
-                         const void* smap, int half_smap, uint8_t* E, cudaStream_t s);
+                         const float* smap, uint8_t* E, cudaStream_t s);
 cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s);
 cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,

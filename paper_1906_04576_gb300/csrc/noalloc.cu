@@ -24,8 +24,9 @@
 
 namespace {
 
-// Capacity: enough chunks for every level of a 4096 x 4096 frame (22.3 M texels over
-// four levels at 4096 texels per chunk = 5462 chunks); 8192 entries = 32 KiB.
+// Capacity: enough chunks for every level of a 4096 x 4096 frame (four levels of
+// 4096^2, 2048^2, 1024^2 and 512^2 texels at 4096 texels per chunk = 4096 + 1024 + 256
+// + 64 = 5440 chunks); 8192 entries = 32 KiB.
 constexpr int STATIC_CHUNKS = 8192;
 constexpr int STATIC_MAX_DIM = 4096;
 
@@ -66,39 +67,13 @@ extern "C" mrr_status mrr_masks_static(const mrr_config* cfg, const uint8_t* edg
   const int W = lv->width[0], H = lv->height[0];
   if (W < 1 || H < 1 || W > STATIC_MAX_DIM || H > STATIC_MAX_DIM) return MRR_EINVAL;  // beyond the scratch
   MaskParams m;
-  std::memset(&m, 0, sizeof m);
-  m.W = W;
-  m.H = H;
-  m.L = c.num_levels;
+  if (!mask_level_params(c, lv, m)) return MRR_EINVAL;  // a blurred level with sigma2 <= 0 or R > 6
   CompactParams cp;
   std::memset(&cp, 0, sizeof cp);
   int nchunks = 0;
   for (int i = 0; i < c.num_levels; ++i) {
     if (lv->width[i] != level_dim(W, i) || lv->height[i] != level_dim(H, i)) return MRR_EINVAL;
     if (c.enabled[i] && (!lv->alpha[i] || !lv->stencil[i] || !lv->worklist[i])) return MRR_EINVAL;
-    if (!c.enabled[i]) {
-      m.mode[i] = 2;
-    } else if (i == c.num_levels - 1 || (i == 0 && c.force_level0)) {
-      m.mode[i] = 1;
-    } else {
-      // Gaussian of Table 1: R = ceil(3 sigma), exp(-k^2 / (2 sigma^2)) normalised in double
-      const double s2 = c.sigma2[i];
-      if (!(s2 > 0.0)) return MRR_EINVAL;
-      const int R = (int)std::ceil(3.0 * std::sqrt(s2));
-      if (R > 6) return MRR_EINVAL;
-      double e[16], sum = 0.0;
-      for (int k = -R; k <= R; ++k) {
-        e[k + R] = std::exp(-(double)(k * k) / (2.0 * s2));
-        sum += e[k + R];
-      }
-      for (int k = 0; k <= 2 * R; ++k) m.g[i][k] = (float)(e[k] / sum);
-      m.R[i] = R;
-      m.mode[i] = 0;
-    }
-    m.Wi[i] = lv->width[i];
-    m.Hi[i] = lv->height[i];
-    m.alpha[i] = lv->alpha[i];
-    m.stencil[i] = lv->stencil[i];
     if (!c.enabled[i]) {
       cp.zero_mask |= 1 << i;
       continue;
@@ -115,7 +90,6 @@ extern "C" mrr_status mrr_masks_static(const mrr_config* cfg, const uint8_t* edg
   for (int i = c.num_levels; i < MRR_MAX_LEVELS; ++i) cp.zero_mask |= 1 << i;
   cp.chunk_begin[cp.nlev] = nchunks;
   if (nchunks > STATIC_CHUNKS) return MRR_EINVAL;
-  m.label = lv->label;
   uint32_t* scratch = nullptr;
   if (static_scratch(&scratch) != cudaSuccess) return MRR_ECUDA;
   cp.chunk_counts = scratch;

@@ -75,6 +75,35 @@ def test_batch_equals_single_frames(mrr):
         mrr.mrr_destroy(c)
 
 
+def test_batch_frames_match_the_oracle(mrr):
+    """Every frame of one batch (mixed sizes, effects and storage precisions, one
+    persistent shading launch) against the oracle's composite on its own inputs (FP16
+    storage: the oracle fed the same binary16 normals, shadow map and colour)."""
+    import torch
+    from test_gpu_parity import TOL16, TOL32, oracle_inputs
+    ctxs, frames, outs, exps = [], [], [], []
+    for effect, W, H, prec, seed in JOBS:
+        fr = sg.gbuffer(seed, W, H, 24, 6, shadow_size=512 if effect == "ssm" else 0)
+        cfg = _cfg(effect, W, H, prec)
+        ref = orc.render(oracle_inputs(fr, prec), cfg, "f32")
+        ctx = mrr.mrr_create(cfg)
+        ctxs.append(ctx)
+        frames.append(mrr.upload_frame(fr, prec))
+        outs.append(mrr.alloc_output(ctx, W, H))
+        exps.append((ref["out"], effect == "ssgi", TOL16 if prec == "fp16" else TOL32))
+    b = mrr.mrr_batch_create()
+    mrr.mrr_render_batch(b, ctxs, frames, outs)
+    torch.cuda.synchronize()
+    for o, (ro, gi, tol) in zip(outs, exps):
+        got = o.cpu().numpy()
+        got = got[..., :3] if gi else got
+        exp = ro if gi else ro[..., 0]
+        assert np.abs(got - exp).max() <= tol
+    mrr.mrr_batch_destroy(b)
+    for c in ctxs:
+        mrr.mrr_destroy(c)
+
+
 def test_batch_rejects_repeated_context(mrr):
     W, H = 64, 48
     fr = sg.gbuffer(0, W, H, 4, 0)

@@ -32,14 +32,13 @@ def mrr():
 
 def oracle_inputs(fr, precision):
     """The oracle sees exactly what the kernels read: binary16-rounded colour always,
-    binary16-rounded normals and shadow map in FP16 storage."""
+    binary16-rounded normals in FP16 storage (the shadow map's light depth, like the view
+    depth, stays FP32 in both precisions)."""
     import copy
     o = copy.copy(fr)
     o.color = fr.color.astype(np.float16).astype(np.float32)
     if precision == "fp16":
         o.normal = fr.normal.astype(np.float16).astype(np.float32)
-        if fr.shadow_map is not None:
-            o.shadow_map = fr.shadow_map.astype(np.float16).astype(np.float32)
     return o
 
 

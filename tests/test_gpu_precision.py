@@ -1,4 +1,5 @@
-"""The FP16-storage path (normals, shadow map and sub-images in binary16, all
+"""The FP16-storage path (normals and sub-images in binary16; view depth and the shadow
+map's light depth in FP32, because the edge and occlusion tests compare them; all
 arithmetic in FP32) and the FP32 path against the FP64 oracle on the unrounded inputs.
 
 The error is dominated by discrete flips: one sample's occlusion (1/N), one PCF tap
@@ -48,12 +49,13 @@ def _stats(got, ref):
 # the values measured on a GB300 (320x180, seed 7):
 #   ssao fp32 7.1e-5 / 6.9e-8 / 6.9e-5     ssao fp16 1.1e-4 / 6.9e-8 / 5.2e-5
 #   ssgi fp32 1.4e-6 / 2.3e-6 / 0          ssgi fp16 3.2e-4 / 2.9e-3 / 1.9e-3
-#   ssm  fp32 2.3e-4 / 3.0e-8 / 2.3e-4     ssm  fp16 2.0e-2 / 2.7e-1 / 1.6e-2
-# The FP16 shadow map is the outlier: at light depths 8..16.5 binary16 values are
-# 0.008..0.016 apart, against a 0.03 depth bias, so blocker-search decisions on receivers
-# tilted towards the light flip (the FP32 map alone gives the 2.3e-4 above).
+#   ssm  fp32 2.3e-4 / 3.0e-8 / 2.3e-4
+# Soft shadows in FP16 storage keep the FP32 shadow map: a binary16 light depth is 0.008 to
+# 0.016 apart at light depths 8..16.5, against a 0.03 depth bias, which flipped blocker
+# decisions on receivers tilted towards the light (RMSE 2.0e-2, p99.9 0.27 with a binary16
+# map); with the map in FP32 the bound is that of the FP32 path.
 BOUNDS = {("ssao", "fp32"): (5e-4, 1 / 64, 1e-3), ("ssao", "fp16"): (1e-3, 1 / 64, 2e-3),
-          ("ssm", "fp32"): (1e-3, 1 / 64, 2e-3), ("ssm", "fp16"): (4e-2, 0.5, 4e-2),
+          ("ssm", "fp32"): (1e-3, 1 / 64, 2e-3), ("ssm", "fp16"): (1e-3, 1 / 64, 2e-3),
           ("ssgi", "fp32"): (1e-4, 1e-4, 1e-3), ("ssgi", "fp16"): (2e-3, 2e-2, 1e-2)}
 
 
