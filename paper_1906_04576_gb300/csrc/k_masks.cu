@@ -206,18 +206,49 @@ __device__ __forceinline__ uint32_t group_or_any(uint32_t w) {
   return group_or<G == 8 ? 2 : G>(w);
 }
 
-// Inclusive nesting (Fig. 2/3): S_I |= the OR of every child in the previous enabled finer
-// level P, for the texels inside the level.  Lane = tile row of level I.
+// Phase 2, warp I: level I's final stencil rows and, in frame mode, its row prefix counts
+// and list reservation.  Inclusive nesting (Fig. 2/3) sets S_I where any child in the
+// previous enabled finer level is set; that level's stencil holds its own children, so
+// nesting composes: S_I = B_I OR, for every finer level P, B_P grouped over level I's
+// 2^(I-P) x 2^(I-P) blocks (disabled levels have B = 0).  Every level is thus final
+// without waiting for the others, and the four scans and reservations run side by side.
+// Lane = tile row of level I.
 template <int I>
-__device__ __forceinline__ void nest_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0, int P) {
+__device__ __forceinline__ void final_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   constexpr int Ti = TS >> I;
   const int lane = threadIdx.x & 31;
-  if (lane >= Ti) return;
-  const int F = I - P;
-  uint32_t rows = 0u;
-  for (int j = 0; j < (1 << F); ++j) rows |= sm.S[P][(lane << F) + j];
-  const uint32_t kids = F == 1 ? group_or_any<2>(rows) : (F == 2 ? group_or_any<4>(rows) : group_or_any<8>(rows));
-  sm.S[I][lane] |= kids & valid_row<I>(m, x0, y0, lane);
+  uint32_t s = lane < Ti ? sm.B[I][lane] : 0u;
+  if (I > 0 && m.mode[I] == 0 && lane < Ti) {
+    uint32_t kids = 0u;
+#pragma unroll
+    for (int P = 0; P < I; ++P) {
+      constexpr int FMAX = I;  // F = I - P <= I
+      const int F = I - P;
+      uint32_t rows = 0u;
+#pragma unroll
+      for (int j = 0; j < (1 << FMAX); ++j)
+        if (j < (1 << F)) rows |= sm.B[P][(lane << F) + j];
+      kids |= F == 1 ? group_or_any<2>(rows) : (F == 2 ? group_or_any<4>(rows) : group_or_any<8>(rows));
+    }
+    s |= kids & valid_row<I>(m, x0, y0, lane);
+    sm.S[I][lane] = s;
+  }
+  if (!m.a0c || m.mode[I] == 2) return;
+  // frame mode: each tile reserves room for its set texels of the level with one atomicAdd
+  // on the level's count (zero before the launch); the entries go there in tile-local
+  // row-major order.  The order of the tiles within a list is whatever order the tiles
+  // reached their atomics; shading never depends on it (every entry is shaded and stored
+  // on its own), and the count is exact.
+  const uint32_t pc = (uint32_t)__popc(s);
+  uint32_t inc = pc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane < Ti) sm.rowpre[I][lane] = inc - pc;
+  const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
+  if (lane == 0) sm.excl[I] = cnt ? atomicAdd(m.counts + I, cnt) : 0u;
 }
 
 // ---- a_i at one texel, from the same horizontal sums and the same fused multiply-adds
@@ -438,31 +469,6 @@ __device__ __forceinline__ void level_values(const MaskParams& m, const MaskSmem
   }
 }
 
-// Frame mode: each tile reserves room for its set texels of each level with one atomicAdd
-// on the level's count (zero before the launch); the entries go there in tile-local
-// row-major order.  The order of the tiles within a list is whatever order the tiles
-// reached their atomics; shading never depends on it (every entry is shaded and stored on
-// its own), and the count is exact.
-__device__ __forceinline__ void reserve_lists(const MaskParams& m, MaskSmem& sm) {
-  const int lane = threadIdx.x & 31;
-  uint32_t mine = 0;  // lane i: level i's count
-#pragma unroll
-  for (int i = 0; i < MRR_MAX_LEVELS; ++i) {
-    const uint32_t pc = (i < m.L && lane < (TS >> i)) ? (uint32_t)__popc(sm.S[i][lane]) : 0u;
-    uint32_t inc = pc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    if (lane < (TS >> i)) sm.rowpre[i][lane] = inc - pc;
-    const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane == i) mine = cnt;
-  }
-  // the levels' reservations go out together (one round trip, not four)
-  if (lane < m.L && m.mode[lane] != 2) sm.excl[lane] = mine ? atomicAdd(m.counts + lane, mine) : 0u;
-}
-
 template <int SIG>
 __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskParams m, const uint8_t* __restrict__ E) {
   __shared__ MaskSmem sm;
@@ -473,12 +479,22 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   uint32_t* Ew = reinterpret_cast<uint32_t*>(sm.E);
   if (m.ebits) {
     // bit-packed edge image: the three words of each staged row
-    for (int k = threadIdx.x; k < ER * EWORDS; k += MTHREADS) {
+    // the thread's two words (and its lookup-table entry below) are all requested before
+    // any is stored
+    constexpr int NW = ER * EWORDS, RW = (NW + MTHREADS - 1) / MTHREADS;
+    uint32_t v[RW];
+#pragma unroll
+    for (int j = 0; j < RW; ++j) {
+      const int k = threadIdx.x + j * MTHREADS;
       const int r = k / EWORDS, w = k - r * EWORDS;
       const int y = y0 - MG + r, wx = (x0 >> 5) - 1 + w;
-      uint32_t v = 0u;
-      if (y >= 0 && y < H && wx >= 0 && wx < m.ewords) v = __ldg(m.ebits + (size_t)y * m.ewords + wx);
-      Ew[4 * r + w] = v;
+      v[j] = 0u;
+      if (k < NW && y >= 0 && y < H && wx >= 0 && wx < m.ewords) v[j] = __ldg(m.ebits + (size_t)y * m.ewords + wx);
+    }
+#pragma unroll
+    for (int j = 0; j < RW; ++j) {
+      const int k = threadIdx.x + j * MTHREADS;
+      if (k < NW) Ew[4 * (k / EWORDS) + (k - (k / EWORDS) * EWORDS)] = v[j];
     }
     if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
   } else if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
@@ -539,21 +555,12 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   // 1. [a_i > 0] of every level as bit rows (one warp per level)
   level_bits<SIG>(m, sm, x0, y0);
   __syncthreads();
-  // 2. inclusive nesting, finer to coarser (warp 0)
-  if (warp == 0) {
-    int prev = m.mode[0] != 2 ? 0 : -1;
-    for (int i = 1; i < m.L; ++i) {
-      if (m.mode[i] == 2) continue;
-      if (m.mode[i] == 0 && prev >= 0) {
-        if (i == 1) nest_bits<1>(m, sm, x0, y0, prev);
-        else if (i == 2) nest_bits<2>(m, sm, x0, y0, prev);
-        else nest_bits<3>(m, sm, x0, y0, prev);
-        __syncwarp();
-      }
-      prev = i;
-    }
-    // 3. frame mode: list reservations
-    if (m.a0c) reserve_lists(m, sm);
+  // 2. final stencils (inclusive nesting), prefix counts and list reservations (warp I: level I)
+  if (warp < m.L) {
+    if (warp == 0) final_level<0>(m, sm, x0, y0);
+    else if (warp == 1) final_level<1>(m, sm, x0, y0);
+    else if (warp == 2) final_level<2>(m, sm, x0, y0);
+    else final_level<3>(m, sm, x0, y0);
   }
   __syncthreads();
   // 4. a_i where it is positive, every level's outputs
