@@ -187,6 +187,8 @@ def effect_config(mrr, sg, spec, W, H, precision):
         kw.update(sample_levels=spec["sample_levels"])
     if "pyramid_gathers" in spec:
         kw.update(pyramid_gathers=spec["pyramid_gathers"])
+    if "disjoint" in spec:
+        kw.update(disjoint=spec["disjoint"])
     return mrr.default_config(eff, spec["levels"], W, H, precision=precision, **kw)
 
 
@@ -206,6 +208,7 @@ def config_of(name, wl, rank, world):
                       2: "direct, bilateral taps (Sec. 3.3)"}[wl.get("merge_mode", 0)],
             "levels_kind": "sample-count (Sec. 6)" if wl.get("sample_levels", 0) else "resolution",
             "pyramid_gathers": bool(wl.get("pyramid_gathers", 0)),
+            "decomposition": "disjoint tiles (Sec. 3.1 ablation)" if wl.get("disjoint", 0) else "inclusive nesting",
             "scene": f"{wl['n_boxes']} boxes + {wl['n_spheres']} spheres, {SCENES} seeded scenes "
                      f"(seeds {SCENES * rank}..{SCENES * rank + SCENES - 1}) in rotation, one per step",
             "l2": "GPU arm: L2 flushed (256 MiB write) before every timed step, outside the events; "
@@ -255,6 +258,8 @@ def oracle_config(orc, sg, wl):
         kw.update(sample_levels=wl["sample_levels"])
     if "pyramid_gathers" in wl:
         kw.update(pyramid_gathers=wl["pyramid_gathers"])
+    if "disjoint" in wl:
+        kw.update(disjoint=wl["disjoint"])
     return orc.default_config(eff, wl["levels"], **kw)
 
 
@@ -702,7 +707,7 @@ def main():
 
     # quality gate: RMSE of the multi-resolution image against full-resolution shading,
     # every scene (the gate is the worst one); texels shaded per scene
-    rmses, rmses_ns, shaded = [], [], []
+    rmses, rmses_ns, shaded, dead, rmses_black = [], [], [], [], []
     for k in range(SCENES):
         load_scene(k)
         mrr.mrr_render(ctx, dev, out, stream)
@@ -711,9 +716,20 @@ def main():
         mrr.mrr_masks(ctx, edges, levels, stream)
         torch.cuda.synchronize()
         diff = (out - full)[..., :3] if out.dim() == 3 else (out - full)
-        rmses.append(float(torch.sqrt(torch.mean(diff.double() ** 2)).item()))
         nonsky = dev.depth < fr.cam.far
-        dns = diff[nonsky] if diff.dim() == 2 else diff[nonsky.unsqueeze(-1).expand_as(diff)]
+        if cfg.get("disjoint", 0):
+            # the ablation's dead pixels are undefined (NaN): the RMSE is over the defined
+            # pixels, beside their count and the RMSE with dead pixels drawn black
+            nanmask = torch.isnan(out)
+            black = torch.where(nanmask, torch.zeros_like(out), out)
+            db = (black - full)[..., :3] if out.dim() == 3 else (black - full)
+            rmses_black.append(float(torch.sqrt(torch.mean(db.double() ** 2)).item()))
+            defined = ~(nanmask[..., 0] if out.dim() == 3 else nanmask)
+            dead.append(int((~defined).sum().item()))
+            diff = diff[defined]
+            nonsky = nonsky[defined]
+        rmses.append(float(torch.sqrt(torch.mean(diff.double() ** 2)).item()))
+        dns = diff[nonsky] if diff.dim() <= 2 else diff[nonsky.unsqueeze(-1).expand_as(diff)]
         rmses_ns.append(float(torch.sqrt(torch.mean(dns.double() ** 2)).item()) if dns.numel() else 0.0)
         shaded.append(int(levels.counts[: cfg["num_levels"]].sum().item()))
     rmse = max(rmses)
@@ -781,6 +797,8 @@ def main():
             "rmse_nonsky": round(max(rmses_ns), 6),
             "shaded_texels_mean": round(statistics.mean(shaded), 1),
             "shaded_texels": n_all, "shaded_fraction": round(n_all / (W * H), 5),
+            **({"dead_pixels_max": max(dead), "dead_fraction_max": round(max(dead) / (W * H), 6),
+                "rmse_dead_black_max": round(max(rmses_black), 6)} if dead else {}),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": measured_traffic(args.workload),
                          "kernel": "shade_levels_kernel" + (" + shade_blocks_kernel" if sample_levels else ""),

@@ -111,6 +111,18 @@ typedef struct mrr_config {
                                      full-resolution pixel (a point-sampled depth pyramid, built in the
                                      context's pools: frames up to the max size).  Single-frame calls
                                      only: batches and servers return MRR_EUNSUPPORTED */
+  int disjoint;                   /* 1: complementary tiles without overlap -- the decomposition Sec. 3.1
+                                     describes and rejects, built as an ablation.  Level i keeps only the
+                                     blocks of its own mask of which no finer enabled level renders any
+                                     pixel (no nesting; the coarsest level too), so no area is rendered
+                                     twice; a pixel that no level covers is a "dead pixel".  The
+                                     recomposition takes each pixel from its finest covering level,
+                                     interpolated over that level's rendered texels only, with no
+                                     blending; dead pixels (and pixels whose covering level has no
+                                     rendered tap of positive weight) are NaN, and their label is 255.
+                                     Requires blur all 0, merge_mode 0, sample_levels 0 and
+                                     pyramid_gathers 0; single-frame calls only (batches and servers
+                                     return MRR_EUNSUPPORTED) */
 } mrr_config;
 
 /* A pinhole camera: world-space eye and orthonormal basis (right, up, forward), the

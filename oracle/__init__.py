@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
         ("cam", ctypes.c_float * 15), ("light", ctypes.c_float * 15), ("shadow_size", ctypes.c_int),
         ("blur", ctypes.c_int * 4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
         ("sample_levels", ctypes.c_int), ("pyramid_gathers", ctypes.c_int), ("gather_level", ctypes.c_int),
+        ("disjoint", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,7 @@ def _L():
             getattr(lib, f"orc_blur_level_{suf}").argtypes = [P, vp, ci, vp, vp, vp]
             getattr(lib, f"orc_merge_stepwise_{suf}").argtypes = [P, vp, vp, vp, vp]
             getattr(lib, f"orc_merge_samples_{suf}").argtypes = [P, vp, vp, vp, vp]
+            getattr(lib, f"orc_merge_disjoint_{suf}").argtypes = [P, vp, vp, vp]
             getattr(lib, f"orc_merge_bilateral_{suf}").argtypes = [P, vp, vp, vp, vp, vp]
             getattr(lib, f"orc_shade_blocks_{suf}").argtypes = [P, vp, vp, vp, vp, ci, vp, ci, vp]
         lib.orc_gauss_weights_f32.argtypes = [ctypes.c_double, vp]
@@ -187,6 +189,7 @@ class _Bound:
         p.sample_levels = int(cfg.get("sample_levels", 0))
         p.pyramid_gathers = int(cfg.get("pyramid_gathers", 0))
         p.gather_level = 0
+        p.disjoint = int(cfg.get("disjoint", 0))
         cam = frame.cam.as_array()
         for k in range(15):
             p.cam[k] = cam[k]
@@ -339,6 +342,9 @@ def merge(frame, cfg, a, S, c, precision="f32"):
     S = [np.ascontiguousarray(x, np.uint8) for x in S]
     c = [np.ascontiguousarray(x, dt) for x in c]
     out = np.zeros((frame.height, frame.width, channels(cfg)), dt)
+    if cfg.get("disjoint", 0):
+        getattr(_L(), f"orc_merge_disjoint_{_suffix(precision)}")(b.ref, _ptr_array(S), _ptr_array(c), _ptr(out))
+        return out
     if cfg.get("merge_mode", 0) == 2 and not cfg.get("sample_levels", 0):
         getattr(_L(), f"orc_merge_bilateral_{_suffix(precision)}")(b.ref, _ptr(b.depth), _ptr_array(a),
                                                                    _ptr_array(S), _ptr_array(c), _ptr(out))

@@ -69,6 +69,7 @@ struct orc_params {
   int sample_levels;     // 1: levels above 0 at full resolution with fewer samples (Sec. 6)
   int pyramid_gathers;   // 1: SSAO on levels above 0 gathers depth from the level's point samples
   int gather_level;      // set per call by shade_level: the level whose samples the gathers read
+  int disjoint;          // 1: complementary tiles without overlap (the variant Sec. 3.1 rejects)
 };
 
 }  // extern "C"
@@ -545,7 +546,28 @@ void masks(const orc_params& p, const uint8_t* E, T* const* a, uint8_t* const* S
           S[i][(size_t)y * Wi + x] = s > T(0) ? 1 : 0;
         }
     }
-    if (prev >= 0) {
+    if (p.disjoint) {
+      // Complementary tiles (Sec. 3.1, the variant without overlap): level i keeps only
+      // the blocks of its own mask that no finer level has rendered any part of, so no
+      // area is rendered twice.  Pixels of a block that a finer level rendered only in
+      // part belong to no sub-image: the dead pixels of Fig. 4 (left).
+      for (int qy = 0; qy < Hi; ++qy)
+        for (int qx = 0; qx < Wi; ++qx) {
+          if (!S[i][(size_t)qy * Wi + qx]) continue;
+          bool covered = false;
+          for (int f = 0; f < i && !covered; ++f) {
+            if (!p.enabled[f]) continue;
+            const int Wf = level_dim(W, f), Hf = level_dim(H, f), k = i - f;
+            for (int y = qy << k; y < std::min((qy + 1) << k, Hf) && !covered; ++y)
+              for (int x = qx << k; x < std::min((qx + 1) << k, Wf); ++x)
+                if (S[f][(size_t)y * Wf + x]) {
+                  covered = true;
+                  break;
+                }
+          }
+          if (covered) S[i][(size_t)qy * Wi + qx] = 0;
+        }
+    } else if (prev >= 0) {
       const int Wp = level_dim(W, prev), Hp = level_dim(H, prev);
       const int f = 1 << (i - prev);
       for (int qy = 0; qy < Hi; ++qy)
@@ -755,6 +777,47 @@ void merge(const orc_params& p, T* const* a, uint8_t* const* S, T* const* c, T* 
         }
       }
       for (int ch = 0; ch < C; ++ch) out[((size_t)y * W + x) * C + ch] = cp[ch];
+    }
+  }
+}
+
+// Recomposition of complementary tiles (Sec. 3.1, the variant without overlap): pixel p
+// takes the sub-image of the finest enabled level whose stencil covers it, interpolated
+// bilinearly at p over that level's rendered taps only (weights renormalised), with no
+// blending.  A pixel that no level covers, or whose covering level has no rendered tap of
+// positive weight at p, is undefined: NaN (a dead pixel).
+template <typename T>
+void merge_disjoint(const orc_params& p, uint8_t* const* S, T* const* c, T* out) {
+  const int W = p.width, H = p.height, L = p.num_levels, C = channels(p);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      T v[3] = {T(NAN), T(NAN), T(NAN)};
+      for (int i = 0; i < L; ++i) {
+        if (!p.enabled[i]) continue;
+        const int Wi = level_dim(W, i), Hi = level_dim(H, i);
+        if (!S[i][(size_t)(y >> i) * Wi + (x >> i)]) continue;
+        const T scale = (T)(1 << i);
+        T ux = (T)(x - level_origin(i)) / scale;
+        T uy = (T)(y - level_origin(i)) / scale;
+        int x0 = (int)std::floor(ux), y0 = (int)std::floor(uy);
+        T fx = ux - (T)x0, fy = uy - (T)y0;
+        int xs[2] = {std::min(std::max(x0, 0), Wi - 1), std::min(std::max(x0 + 1, 0), Wi - 1)};
+        int ys[2] = {std::min(std::max(y0, 0), Hi - 1), std::min(std::max(y0 + 1, 0), Hi - 1)};
+        T w[4] = {(T(1) - fx) * (T(1) - fy), fx * (T(1) - fy), (T(1) - fx) * fy, fx * fy};
+        size_t idx[4] = {(size_t)ys[0] * Wi + xs[0], (size_t)ys[0] * Wi + xs[1], (size_t)ys[1] * Wi + xs[0],
+                         (size_t)ys[1] * Wi + xs[1]};
+        T num[3] = {T(0), T(0), T(0)}, den = T(0);
+        for (int k = 0; k < 4; ++k) {
+          if (!S[i][idx[k]] || !(w[k] > T(0))) continue;
+          for (int ch = 0; ch < C; ++ch) num[ch] = num[ch] + w[k] * c[i][idx[k] * C + ch];
+          den = den + w[k];
+        }
+        if (den > T(0))
+          for (int ch = 0; ch < C; ++ch) v[ch] = num[ch] / den;
+        break;
+      }
+      for (int ch = 0; ch < C; ++ch) out[((size_t)y * W + x) * C + ch] = v[ch];
     }
   }
 }
@@ -1008,6 +1071,9 @@ int orc_gauss_weights_f64(double sigma2, double* g) { return gauss_weights<doubl
                               const float* color, const float* smap, int level, const uint32_t* list, int n,\
                               T* c) {                                                                        \
     shade_blocks<T>(*p, make_inputs(depth, normal, color, smap), level, list, n, c);                        \
+  }                                                                                                          \
+  void orc_merge_disjoint_##SUF(const orc_params* p, uint8_t* const* S, T* const* c, T* out) {               \
+    merge_disjoint<T>(*p, S, c, out);                                                                        \
   }                                                                                                          \
   void orc_merge_samples_##SUF(const orc_params* p, T* const* a, uint8_t* const* S, T* const* c, T* out) {  \
     merge_samples<T>(*p, a, S, c, out);                                                                      \

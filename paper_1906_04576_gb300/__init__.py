@@ -61,7 +61,7 @@ class mrr_config(ctypes.Structure):
         ("max_width", ctypes.c_int), ("max_height", ctypes.c_int),
         ("lanes_per_texel", ctypes.c_int), ("lanes_per_pixel", ctypes.c_int), ("no_graph", ctypes.c_int),
         ("blur", I4), ("blur_depth_rel", ctypes.c_float), ("merge_mode", ctypes.c_int),
-        ("sample_levels", ctypes.c_int), ("pyramid_gathers", ctypes.c_int),
+        ("sample_levels", ctypes.c_int), ("pyramid_gathers", ctypes.c_int), ("disjoint", ctypes.c_int),
     ]
 
 
@@ -282,6 +282,7 @@ def make_config(cfg: dict) -> tuple[mrr_config, list]:
     c.merge_mode = int(cfg.get("merge_mode", 0))
     c.sample_levels = int(cfg.get("sample_levels", 0))
     c.pyramid_gathers = int(cfg.get("pyramid_gathers", 0))
+    c.disjoint = int(cfg.get("disjoint", 0))
     return c, keep
 
 
@@ -729,6 +730,7 @@ def default_config(effect: str, num_levels: int, max_width: int, max_height: int
     cfg = dict(effect=effect, precision="fp32", num_levels=num_levels, sigma2=sigma2, weight=weight,
                enabled=enabled, depth_rel=0.05, normal_cos=0.9, force_level0=0, radius=0.5, ao_bias=0.0125,
                gi_min_dist2=0.01, light_size=0.5, shadow_bias=0.03, max_width=max_width, max_height=max_height,
-               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0, pyramid_gathers=0)
+               blur=[0, 0, 0, 0], blur_depth_rel=0.05, merge_mode=0, sample_levels=0, pyramid_gathers=0,
+               disjoint=0)
     cfg.update(kw)
     return cfg

@@ -430,6 +430,24 @@ mrr_status chain_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float*
 mrr_status merge_impl(mrr_ctx* ctx, const mrr_levels* lv, void* const* c, float* out, cudaStream_t s,
                       bool compact_level0 = false, const float* depth = nullptr) {
   const mrr_config& cf = ctx->cfg;
+  if (cf.disjoint) {
+    MergeParams mp;
+    std::memset(&mp, 0, sizeof mp);
+    mp.W = lv->width[0];
+    mp.H = lv->height[0];
+    mp.L = cf.num_levels;
+    mp.C = channels(cf);
+    mp.half_store = cf.precision == MRR_FP16;
+    for (int i = 0; i < cf.num_levels; ++i) {
+      mp.enabled[i] = cf.enabled[i];
+      mp.Wi[i] = lv->width[i];
+      mp.Hi[i] = lv->height[i];
+      mp.stencil[i] = lv->stencil[i];
+      mp.c[i] = c[i];
+    }
+    MRR_CUDA(ctx, launch_merge_disjoint(mp, out, s));
+    return MRR_OK;
+  }
   if (cf.merge_mode == 2 && !cf.sample_levels) {
     if (!depth) return fail(ctx, MRR_EINVAL, "the bilateral merge needs the frame's depth");
     MergeParams mp;
@@ -650,7 +668,7 @@ mrr_status frame_masks(mrr_ctx* ctx, const mrr_gbuffer* g, mrr_levels* lv, cudaS
 mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const mrr_config& c = ctx->cfg;
   const int W = g->width, H = g->height;
-  if (c.num_levels < 2) return render_launches_staged(ctx, g, out, s);
+  if (c.num_levels < 2 || c.disjoint) return render_launches_staged(ctx, g, out, s);
   if (!fits_pools(ctx, W, H)) return fail(ctx, MRR_EINVAL, "frame %dx%d exceeds the context's max size", W, H);
   mrr_levels lv;
   mrr_status st = frame_masks(ctx, g, &lv, s);
@@ -687,7 +705,8 @@ mrr_status render_launches(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaS
   return merge_impl(ctx, &lv, cm, out, s, true, g->depth);
 }
 
-// One level only (level 0 is the coarsest): edges, masks, compaction, shading, merge.
+// One level only (level 0 is the coarsest), or the disjoint-tile ablation: edges, masks,
+// compaction, shading, merge.
 mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out, cudaStream_t s) {
   const int W = g->width, H = g->height;
   mrr_status st = edges_impl(ctx, g, ctx->edges, s);
@@ -863,6 +882,12 @@ mrr_status mrr_create(const mrr_config* cfg, mrr_ctx** out) {
   if (c.sample_levels != 0 && c.sample_levels != 1) return MRR_EINVAL;
   if (c.pyramid_gathers != 0 && c.pyramid_gathers != 1) return MRR_EINVAL;
   if (c.pyramid_gathers && (c.effect != MRR_SSAO || c.sample_levels)) return MRR_EINVAL;
+  if (c.disjoint != 0 && c.disjoint != 1) return MRR_EINVAL;
+  if (c.disjoint) {  // the ablation stands alone: no blur, step-wise or bilateral merge, sample levels, pyramid
+    if (c.merge_mode != 0 || c.sample_levels || c.pyramid_gathers) return MRR_EINVAL;
+    for (int i = 0; i < MRR_MAX_LEVELS; ++i)
+      if (c.blur[i]) return MRR_EINVAL;
+  }
   if (c.sample_levels) {  // full-resolution sub-images: no level blur, direct blend only
     if (c.merge_mode != 0) return MRR_EINVAL;
     for (int i = 0; i < MRR_MAX_LEVELS; ++i)
@@ -1118,6 +1143,8 @@ mrr_status check_batch(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* fr
       return batch_fail(b, MRR_EINVAL, "a frame exceeds its context's max size");
     if (ctxs[k]->cfg.pyramid_gathers)
       return batch_fail(b, MRR_EUNSUPPORTED, "pyramid gathers are not batched (single-frame calls only)");
+    if (ctxs[k]->cfg.disjoint)
+      return batch_fail(b, MRR_EUNSUPPORTED, "disjoint tiles are not batched (single-frame calls only)");
     if (outs && (!outs[k] || !aligned(outs[k], ctxs[k]->cfg.effect == MRR_SSGI ? 16 : 4)))
       return batch_fail(b, MRR_EINVAL, "output is NULL or misaligned");
   }

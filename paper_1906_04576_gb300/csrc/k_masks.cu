@@ -217,8 +217,8 @@ template <int I>
 __device__ __forceinline__ void final_level(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   constexpr int Ti = TS >> I;
   const int lane = threadIdx.x & 31;
-  uint32_t s = lane < Ti ? sm.B[I][lane] : 0u;
-  if (I > 0 && m.mode[I] == 0 && lane < Ti) {
+  uint32_t s = lane < Ti ? (m.disjoint ? sm.S[I][lane] : sm.B[I][lane]) : 0u;
+  if (I > 0 && m.mode[I] == 0 && lane < Ti && !m.disjoint) {
     uint32_t kids = 0u;
 #pragma unroll
     for (int P = 0; P < I; ++P) {
@@ -249,6 +249,28 @@ __device__ __forceinline__ void final_level(const MaskParams& m, MaskSmem& sm, i
   if (lane < Ti) sm.rowpre[I][lane] = inc - pc;
   const uint32_t cnt = __shfl_sync(0xffffffffu, inc, 31);
   if (lane == 0) sm.excl[I] = cnt ? atomicAdd(m.counts + I, cnt) : 0u;
+}
+
+// The disjoint-tile ablation (the variant Sec. 3.1 rejects), warp 0: level I keeps only the
+// blocks of its own mask of which no finer enabled level renders any pixel -- every finer
+// level's final stencil grouped to level I's texels and removed -- coarser levels after
+// finer ones.  Lane = tile row.
+__device__ __forceinline__ void disjoint_bits(const MaskParams& m, MaskSmem& sm) {
+  const int lane = threadIdx.x & 31;
+  for (int I = 1; I < m.L; ++I) {
+    const int Ti = TS >> I;
+    if (lane < Ti) {
+      uint32_t covered = 0u;
+      for (int P = 0; P < I; ++P) {
+        const int F = I - P;
+        uint32_t rows = 0u;
+        for (int j = 0; j < (1 << F); ++j) rows |= sm.S[P][(lane << F) + j];
+        covered |= F == 1 ? group_or_any<2>(rows) : (F == 2 ? group_or_any<4>(rows) : group_or_any<8>(rows));
+      }
+      sm.S[I][lane] = sm.B[I][lane] & ~covered;
+    }
+    __syncwarp();
+  }
 }
 
 // ---- a_i at one texel, from the same horizontal sums and the same fused multiply-adds
@@ -555,6 +577,10 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   // 1. [a_i > 0] of every level as bit rows (one warp per level)
   level_bits<SIG>(m, sm, x0, y0);
   __syncthreads();
+  if (m.disjoint) {  // the ablation's stencils, finer levels first
+    if (warp == 0) disjoint_bits(m, sm);
+    __syncthreads();
+  }
   // 2. final stencils (inclusive nesting), prefix counts and list reservations (warp I: level I)
   if (warp < m.L) {
     if (warp == 0) final_level<0>(m, sm, x0, y0);
@@ -717,6 +743,7 @@ bool mask_level_params(const mrr_config& c, const mrr_levels* lv, MaskParams& m)
     m.stencil[i] = lv->stencil[i];
   }
   m.label = lv->label;
+  m.disjoint = c.disjoint;
   return true;
 }
 

@@ -300,6 +300,54 @@ __global__ void __launch_bounds__(MG_TX* MG_TY) merge_kernel(MergeParams p, floa
   }
 }
 
+// The recomposition of the disjoint-tile ablation: pixel p takes the sub-image of the
+// finest enabled level whose stencil covers it, interpolated bilinearly at p over that
+// level's rendered taps of positive weight (weights renormalised), with no blending; NaN
+// where no level covers p or the covering level has no such tap.  Weights and sums as the
+// direct merge's definition: products of the axis weights, taps in order, IEEE division.
+template <typename CT, int C>
+__global__ void __launch_bounds__(256) merge_disjoint_kernel(MergeParams p, float* __restrict__ out) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= p.W || y >= p.H) return;
+  const float nan = __int_as_float(0x7fc00000);
+  float v[3] = {nan, nan, nan};
+  for (int i = 0; i < p.L; ++i) {
+    if (!p.enabled[i]) continue;
+    const int Wi = p.Wi[i], Hi = p.Hi[i];
+    if (!__ldg(p.stencil[i] + (size_t)(y >> i) * Wi + (x >> i))) continue;
+    const int o = i == 0 ? 0 : (1 << (i - 1)), mask = (1 << i) - 1;
+    const float inv = __int_as_float((127 - i) << 23);  // 2^-i
+    const int nx = x - o, ny = y - o;
+    const int x0 = nx >> i, y0 = ny >> i;  // arithmetic shifts: floors
+    const float fx = (float)(nx & mask) * inv, fy = (float)(ny & mask) * inv;
+    const int xs[2] = {min(max(x0, 0), Wi - 1), min(max(x0 + 1, 0), Wi - 1)};
+    const int ys[2] = {min(max(y0, 0), Hi - 1), min(max(y0 + 1, 0), Hi - 1)};
+    const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
+    float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const size_t q = (size_t)ys[k >> 1] * Wi + xs[k & 1];
+      if (!__ldg(p.stencil[i] + q) || !(w[k] > 0.0f)) continue;
+      const float3 cv = load_c<CT>(p.c[i], q, C);
+      num[0] = num[0] + w[k] * cv.x;
+      num[1] = num[1] + w[k] * cv.y;
+      num[2] = num[2] + w[k] * cv.z;
+      den = den + w[k];
+    }
+    if (den > 0.0f) {
+      v[0] = num[0] / den;
+      v[1] = num[1] / den;
+      v[2] = num[2] / den;
+    }
+    break;
+  }
+  const size_t pix = (size_t)y * p.W + x;
+  if (C == 4)
+    reinterpret_cast<float4*>(out)[pix] = make_float4(v[0], v[1], v[2], 0.0f);
+  else
+    out[pix] = v[0];
+}
+
 template <typename CT, int C>
 __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __restrict__ out) {
   const uint32_t n = min(__ldg(p.count), (uint32_t)p.W * (uint32_t)p.H);
@@ -664,6 +712,19 @@ cudaError_t launch_merge_bilateral(const MergeParams& p, const float* depth, flo
   } else {
     if (p.half_store) merge_bilateral_kernel<__half, 1><<<grid, block, 0, s>>>(p, depth, rel, out);
     else merge_bilateral_kernel<float, 1><<<grid, block, 0, s>>>(p, depth, rel, out);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_disjoint(const MergeParams& p, float* out, cudaStream_t s) {
+  dim3 grid((p.W + 31) / 32, (p.H + 7) / 8), block(32, 8);
+  if (p.C == 4) {
+    if (p.half_store) merge_disjoint_kernel<__half, 4><<<grid, block, 0, s>>>(p, out);
+    else merge_disjoint_kernel<float, 4><<<grid, block, 0, s>>>(p, out);
+  } else {
+    if (p.half_store) merge_disjoint_kernel<__half, 1><<<grid, block, 0, s>>>(p, out);
+    else merge_disjoint_kernel<float, 1><<<grid, block, 0, s>>>(p, out);
   }
   count_launches(1);
   return cudaGetLastError();

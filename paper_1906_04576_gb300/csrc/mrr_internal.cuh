@@ -107,6 +107,7 @@ struct MaskParams {
   int ewords;
   uint32_t* list[MRR_MAX_LEVELS];
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
+  int disjoint;      // complementary tiles without overlap (the variant Sec. 3.1 rejects)
 };
 constexpr int MASK_LUT_MAX = 512;  // level 0's table for R <= 4 (larger R sums the taps)
 
@@ -241,6 +242,9 @@ struct BlurParams {
 cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* normal, int half_normal,
                          const float* smap, uint8_t* E, cudaStream_t s);
 cudaError_t launch_masks(const MaskParams& m, const uint8_t* E, cudaStream_t s);
+// The recomposition of the disjoint-tile ablation (k_merge.cu): each pixel from its finest
+// covering level, no blending, NaN where no level covers it.
+cudaError_t launch_merge_disjoint(const MergeParams& p, float* out, cudaStream_t s);
 cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
 cudaError_t launch_shade_levels(const ShadeParams& p, const FrameIn& in, int precision, const ShadeLevels& lv,
                                 int grid, int split, cudaStream_t s);

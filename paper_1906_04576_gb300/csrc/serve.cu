@@ -190,7 +190,8 @@ mrr_status mrr_server_create(const mrr_server_config* cfg, mrr_server** out) {
   for (int e = 0; e < 3; ++e) enabled += cfg->effect_enabled[e] ? 1 : 0;
   if (!enabled || cfg->slots < 0 || cfg->max_queue < 0) return MRR_EINVAL;
   for (int e = 0; e < 3; ++e)  // requests are served in batches, which take no pyramid gathers
-    if (cfg->effect_enabled[e] && cfg->effect_cfg[e].pyramid_gathers) return MRR_EUNSUPPORTED;
+    if (cfg->effect_enabled[e] && (cfg->effect_cfg[e].pyramid_gathers || cfg->effect_cfg[e].disjoint))
+      return MRR_EUNSUPPORTED;
   mrr_server* s = new (std::nothrow) mrr_server();
   if (!s) return MRR_ENOMEM;
   s->cfg = *cfg;

@@ -231,6 +231,9 @@ WORKLOADS = {
                                  samples=64, radius=0.5, levels=4, sample_levels=1),
     "ssao64_4k_samples": dict(effect="ssao", width=3840, height=2160, n_boxes=64, n_spheres=16,
                               samples=64, radius=0.5, levels=4, sample_levels=1),
+    # the disjoint-tile ablation (complementary tiles without overlap, Sec. 3.1)
+    "ssao64_1080p_disjoint": dict(effect="ssao", width=1920, height=1080, n_boxes=64, n_spheres=16,
+                                  samples=64, radius=0.5, levels=4, disjoint=1),
     # soft shadows, 32 blocker + 64 PCF taps, 2048^2 shadow map, 4 levels, 2560x1440
     "ssm_1440p": dict(effect="ssm", width=2560, height=1440, n_boxes=64, n_spheres=16,
                       blocker_samples=32, pcf_samples=64, shadow_size=2048, levels=4),

@@ -980,3 +980,80 @@ def test_fp64_and_fp32_oracles_agree_statistically():
     diff = f32["out"].astype(np.float64) - f64["out"]
     assert np.sqrt(np.mean(diff ** 2)) < 2e-3
     assert np.quantile(np.abs(diff), 0.999) <= 1.0 / 32 + 1e-6
+
+
+# ----------------------------------------------------------------- disjoint tiles (Sec. 3.1)
+
+def _single_edge_frame(W=64, H=64, at=(20, 20)):
+    """A flat frame whose only edge is one pixel: a depth spike at `at`."""
+    d = np.full((H, W), 3.0)
+    d[at[1], at[0]] = 2.0
+    return synthetic_frame(d, flat_normals(H, W))
+
+
+@pytest.mark.parametrize("at", [(20, 20), (21, 21), (20, 33)])
+def test_disjoint_tiles_two_levels_dead_pixels_closed_form(at):
+    """Two levels, one edge pixel: level 0's region is the (2R+1)^2 = 7x7 square around it
+    (R = 3); without overlap, level 1 gives up every 2x2 block the square touches, which
+    spans 8x8 pixels for a square of odd side wherever it lies, so exactly 8^2 - 7^2 = 15
+    pixels belong to no sub-image, and the recomposition leaves exactly those undefined."""
+    H = W = 64
+    fr = synthetic_frame(np.full((H, W), 3.0), flat_normals(H, W))
+    cfg = cfg_for(levels=2, samples=16, disjoint=1)
+    E = np.zeros((H, W), np.uint8)
+    E[at[1], at[0]] = 1
+    a, S, label = orc.masks(fr, cfg, E)
+    cov0 = S[0].astype(bool)
+    cov1 = np.kron(S[1], np.ones((2, 2), np.uint8))[:H, :W].astype(bool)
+    x, y = at
+    square = np.zeros((H, W), bool)
+    square[y - 3:y + 4, x - 3:x + 4] = True
+    assert np.array_equal(cov0, square)
+    assert not np.any(cov0 & cov1)                       # disjoint
+    dead = ~(cov0 | cov1)
+    assert dead.sum() == 15
+    hull = np.zeros((H, W), bool)
+    hull[(y - 3) // 2 * 2:(y + 3) // 2 * 2 + 2, (x - 3) // 2 * 2:(x + 3) // 2 * 2 + 2] = True
+    assert np.array_equal(dead, hull & ~square)
+    assert np.all(label[dead] == 255) and np.all(label[cov0] == 0) and np.all(label[cov1] == 1)
+    c = [orc.shade_level(fr, cfg, i, orc.compact(S[i])) for i in range(2)]
+    out = orc.merge(fr, cfg, a, S, c)[..., 0]
+    assert np.array_equal(np.isnan(out), dead)
+    assert np.all(out[~dead] == 1.0)                     # a flat plane is unoccluded
+
+
+@pytest.mark.parametrize("effect", ["ssao", "ssgi"])
+def test_disjoint_tiles_are_a_partition_up_to_dead_pixels(effect):
+    fr = sg.gbuffer(6, 160, 96, 20, 6)
+    cfg = cfg_for(effect, 4, samples=16, disjoint=1)
+    E = orc.edges(fr, cfg)
+    a, S, label = orc.masks(fr, cfg, E)
+    H, W = fr.height, fr.width
+    cover = np.zeros((H, W), np.int32)
+    for i in range(4):
+        if not cfg["enabled"][i]:
+            assert S[i].sum() == 0
+            continue
+        cover += np.kron(S[i].astype(np.int32), np.ones((1 << i, 1 << i), np.int32))[:H, :W]
+    assert cover.max() == 1                              # never rendered twice
+    assert np.any(cover == 0)                            # dead pixels, as Fig. 4 (left) shows
+    out = orc.render(fr, cfg)["out"]
+    nan = np.isnan(out[..., 0])
+    assert np.all(nan[cover == 0])                       # undefined where no sub-image is
+    assert not np.any(nan[(cover == 1) & (label == 0)])  # level 0 is its own pixels
+
+
+def test_disjoint_tiles_without_dead_pixels_reduce_to_one_level():
+    # no edge: only the coarsest level renders, and it covers everything
+    H = W = 48
+    fr = synthetic_frame(np.full((H, W), 2.5), flat_normals(H, W))
+    cfg = cfg_for(samples=16, disjoint=1)
+    a, S, label = orc.masks(fr, cfg, orc.edges(fr, cfg))
+    assert all(S[i].sum() == 0 for i in range(3)) and S[3].all()
+    out = orc.render(fr, cfg)["out"]
+    assert not np.isnan(out).any() and np.all(out == 1.0)
+    # every pixel at level 0: the full-resolution image exactly
+    fr = sg.gbuffer(2, 96, 64, 12, 4)
+    cfg = cfg_for(samples=16, disjoint=1, force_level0=1)
+    out = orc.render(fr, cfg, "f32")["out"]
+    assert np.array_equal(out, orc.shade_full(fr, cfg, "f32"))
