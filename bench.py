@@ -166,7 +166,8 @@ def algorithmic_bytes(cfg, n_nonsky, n_sky):
     elif eff == "ssgi":
         per, store = 4 + nb + cfg["samples"] * (4 + nb + 8), (8 if half else 16)
     else:
-        per, store = 4 + (cfg["blocker_samples"] + cfg["pcf_samples"]) * (2 if half else 4), (2 if half else 4)
+        # the shadow map stays FP32 in both storage precisions
+        per, store = 4 + (cfg["blocker_samples"] + cfg["pcf_samples"]) * 4, (2 if half else 4)
     return n_nonsky * (per + store) + n_sky * (4 + store)
 
 
@@ -352,7 +353,7 @@ def run_serve(args, mrr, sg, wl, rank, world, dist):
     specs = wl["effects"]
     names = [e["effect"] for e in specs]
     cfgs = {e["effect"]: effect_config(mrr, sg, e, Wm, Hm, e["precision"]) for e in specs}
-    srv = mrr.mrr_server_create(cfgs, slots=wl["slots"], hbm_reserve=8 << 30)
+    srv = mrr.mrr_server_create(cfgs, slots=wl["slots"], hbm_reserve=8 << 30, per_effect=wl.get("per_effect", 2))
     slots = mrr.mrr_server_slots(srv)
     # resident G-buffer pool: scenes_per_resolution seeded scenes per resolution
     pool = {}
@@ -366,23 +367,22 @@ def run_serve(args, mrr, sg, wl, rank, world, dist):
     n_req = wl["requests"]
     gaps, pick = sg.poisson_stream(0xA11 + rank, n_req, wl["rate"], len(wl["resolutions"]) * len(names))
     scene_pick = np.arange(n_req) % wl["scenes_per_resolution"]
-    # output ring per (resolution, effect): a buffer is reused only after its last request completed
-    RING = 16
-    ring = {}
-    for ri, (W, H) in enumerate(wl["resolutions"]):
-        for e in names:
-            shape = (H, W, 4) if e == "ssgi" else (H, W)
-            ring[(ri, e)] = [[torch.empty(shape, dtype=torch.float32, device="cuda"), None] for _ in range(RING)]
-    ring_pos = {k: 0 for k in ring}
+    # every request gets an output buffer of its own (kept until it completes), and
+    # consecutive requests of one resolution read different G-buffers: the batches' graphs
+    # are keyed on topology, never on pointers
+    def fresh_out(ri, e):
+        W, H = wl["resolutions"][ri]
+        return torch.empty((H, W, 4) if e == "ssgi" else (H, W), dtype=torch.float32, device="cuda")
     # warm-up: one request of every kind
     for ri in range(len(wl["resolutions"])):
         for e in names:
-            t = mrr.mrr_submit(srv, e, pool[(ri, 0, prec[e])], ring[(ri, e)][0][0])
+            t = mrr.mrr_submit(srv, e, pool[(ri, 0, prec[e])], fresh_out(ri, e))
             mrr.mrr_wait(srv, t, -1)
     torch.cuda.synchronize()
+    stats0 = mrr.mrr_server_stats(srv)
     if dist is not None:
         dist.barrier()
-    tickets, pixels = [], 0
+    tickets, pixels, live = [], 0, {}
     t_start = time.perf_counter()
     arrival = t_start
     l0 = mrr.mrr_kernel_launches()
@@ -393,18 +393,21 @@ def run_serve(args, mrr, sg, wl, rank, world, dist):
         ri, ei = divmod(int(pick[i]), len(names))
         e = names[ei]
         W, H = wl["resolutions"][ri]
-        slot = ring[(ri, e)][ring_pos[(ri, e)] % RING]
-        ring_pos[(ri, e)] += 1
-        if slot[1] is not None:
-            mrr.mrr_wait(srv, slot[1], -1)
-        t = mrr.mrr_submit(srv, e, pool[(ri, int(scene_pick[i]), prec[e])], slot[0])
-        slot[1] = t
+        out = fresh_out(ri, e)
+        t = mrr.mrr_submit(srv, e, pool[(ri, int(scene_pick[i]), prec[e])], out)
+        live[t] = out
         tickets.append(t)
         pixels += W * H
+        # outputs of finished requests go back to the allocator
+        if i % 64 == 63:
+            for tk in [tk for tk in live if mrr.mrr_poll(srv, tk)[0]]:
+                del live[tk]
     for t in tickets:
         mrr.mrr_wait(srv, t, -1)
     t_end = time.perf_counter()
     launches = mrr.mrr_kernel_launches() - l0
+    stats1 = mrr.mrr_server_stats(srv)
+    live.clear()
     info = [mrr.mrr_request_info(srv, t) for t in tickets]
     lat = [(i["done_ns"] - i["submit_ns"]) * 1e-6 for i in info]
     qwait = [(i["start_ns"] - i["submit_ns"]) * 1e-6 for i in info]
@@ -422,12 +425,17 @@ def run_serve(args, mrr, sg, wl, rank, world, dist):
             "data": "synthetic", "config": {
                 "workload": args.workload, "arrivals": f"Poisson {wl['rate']:.0f}/s, {n_req} requests",
                 "mix": "uniform over " + ", ".join(f"{w}x{h}" for w, h in wl["resolutions"]) + " x " + ", ".join(names),
-                "slots": slots, "scenes": f"{wl['scenes_per_resolution']} seeded scenes per resolution, resident",
+                "slots": slots, "per_effect": wl.get("per_effect", 2),
+                "scenes": f"{wl['scenes_per_resolution']} seeded scenes per resolution, resident, in rotation; "
+                          "a new output buffer per request",
                 "l2": "not flushed: a live request stream", "parallelism": f"replicas x{world}"},
             "offered_mpix_s": round(pixels / offered_s / 1e6, 3),
             "sustained": bool(wall <= offered_s * 1.05),
             "queue_wait_p50_ms": round(pct(qwait, 0.5), 4), "queue_wait_p99_ms": round(pct(qwait, 0.99), 4),
             "device_ms_p50": round(pct([i["device_ms"] for i in info], 0.5), 4),
+            "batches": int(stats1["batches"] - stats0["batches"]),
+            "graph_instantiations": int(stats1["graph_instantiations"] - stats0["graph_instantiations"]),
+            "graph_updates": int(stats1["graph_updates"] - stats0["graph_updates"]),
             "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)

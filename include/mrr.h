@@ -388,10 +388,14 @@ mrr_status mrr_batch_autotune(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuf
  * pyramids, work lists, sub-images -- plus a stream and a batch object each); fewer if
  * creating the next set would leave less than hbm_reserve bytes of free device memory.
  * A scheduler thread admits pending requests in arrival order as slots free up, packs
- * up to one request per effect into one batch (one persistent shading launch, see
- * mrr_render_batch) and overlaps batches on the slots' streams.  Every result equals
- * mrr_render of the same frame with the same configuration.  The paper renders frames
- * one by one; this is the serving extension of its Sec. 3 pipeline. */
+ * up to per_effect requests of each effect into one batch (one persistent shading launch,
+ * see mrr_render_batch; a slot holds per_effect contexts per effect) and overlaps batches
+ * on the slots' streams.  A batch runs as a CUDA graph keyed on its topology -- which
+ * contexts, in a fixed order -- not on its buffers: each batch is captured afresh and
+ * applied to the cached graph of its topology with cudaGraphExecUpdate, and only a
+ * topology not seen before is instantiated (mrr_server_stats counts both).  Every result
+ * equals mrr_render of the same frame with the same configuration.  The paper renders
+ * frames one by one; this is the serving extension of its Sec. 3 pipeline. */
 typedef struct mrr_server mrr_server;
 
 typedef struct mrr_server_config {
@@ -403,6 +407,9 @@ typedef struct mrr_server_config {
   int max_queue;              /* pending requests beyond which mrr_submit returns MRR_EBUSY (0 = 1024) */
   int mock_device_us;         /* test mode: no device work at all; a batch completes after this many
                                  microseconds of host time (scheduler tests without a GPU) */
+  int per_effect;             /* requests of one effect a batch may hold (0 = 2); at most 8 requests in
+                                 all: per_effect * enabled effects <= 8, else MRR_EINVAL */
+  int direct_launches;        /* 1: batches launched kernel by kernel, without graphs */
 } mrr_server_config;
 
 typedef struct mrr_request {
@@ -438,6 +445,16 @@ mrr_status mrr_wait(mrr_server* s, uint64_t ticket, int64_t timeout_ns);
 mrr_status mrr_request_info(mrr_server* s, uint64_t ticket, mrr_request_info_t* out);
 /* Forget a completed request's record. */
 mrr_status mrr_release(mrr_server* s, uint64_t ticket);
+
+typedef struct mrr_server_stats_t {
+  uint64_t batches;               /* batches dispatched */
+  uint64_t completed;             /* requests completed */
+  uint64_t graph_instantiations;  /* batch graphs instantiated (a topology not cached) */
+  uint64_t graph_updates;         /* batch graphs updated in place (a cached topology) */
+} mrr_server_stats_t;
+
+/* Counters of the server's scheduler since it was created.  Thread-safe. */
+mrr_status mrr_server_stats(mrr_server* s, mrr_server_stats_t* out);
 
 /* Number of kernels this library has launched in this process (all contexts), for
  * accounting of GPU work in benchmarks. */

@@ -16,6 +16,7 @@ device memory and streams.  The functions carry the C names of include/mrr.h:
     mrr_render_batch(b, ctxs, frames, outs)   mrr_batch_autotune(b, ctxs, frames)
     mrr_masks_static(cfg, edges, levels)
     mrr_server_create(cfgs) -> Server   mrr_submit / mrr_poll / mrr_wait / mrr_request_info / mrr_release
+    mrr_server_stats(s)
 
 Importing raises if libmrr.so has not been built (``__graft_entry__.build()`` or
 ``python paper_1906_04576_gb300/_build.py``): there is no CPU fallback.
@@ -91,7 +92,13 @@ class mrr_tuning(ctypes.Structure):
 
 class mrr_server_config(ctypes.Structure):
     _fields_ = [("effect_cfg", mrr_config * 3), ("effect_enabled", ctypes.c_int * 3), ("slots", ctypes.c_int),
-                ("hbm_reserve", ctypes.c_size_t), ("max_queue", ctypes.c_int), ("mock_device_us", ctypes.c_int)]
+                ("hbm_reserve", ctypes.c_size_t), ("max_queue", ctypes.c_int), ("mock_device_us", ctypes.c_int),
+                ("per_effect", ctypes.c_int), ("direct_launches", ctypes.c_int)]
+
+
+class mrr_server_stats_t(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("graph_instantiations", ctypes.c_uint64), ("graph_updates", ctypes.c_uint64)]
 
 
 class mrr_request(ctypes.Structure):
@@ -134,6 +141,8 @@ _lib.mrr_poll.restype = ctypes.c_int
 _lib.mrr_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64]
 _lib.mrr_wait.restype = ctypes.c_int
 _lib.mrr_request_info.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(mrr_request_info_t)]
+_lib.mrr_server_stats.argtypes = [_vp, ctypes.POINTER(mrr_server_stats_t)]
+_lib.mrr_server_stats.restype = ctypes.c_int
 _lib.mrr_request_info.restype = ctypes.c_int
 _lib.mrr_release.argtypes = [_vp, ctypes.c_uint64]
 _lib.mrr_release.restype = ctypes.c_int
@@ -524,7 +533,7 @@ class Server:
 
 
 def mrr_server_create(effect_cfgs: dict, slots: int = 4, hbm_reserve: int = 0, max_queue: int = 0,
-                      mock_device_us: int = 0) -> Server:
+                      mock_device_us: int = 0, per_effect: int = 0, direct_launches: bool = False) -> Server:
     """effect_cfgs: {'ssao': cfg, 'ssm': cfg, 'ssgi': cfg} (any subset)."""
     sc = mrr_server_config()
     keep = []
@@ -535,6 +544,7 @@ def mrr_server_create(effect_cfgs: dict, slots: int = 4, hbm_reserve: int = 0, m
         sc.effect_cfg[e] = c
         sc.effect_enabled[e] = 1
     sc.slots, sc.hbm_reserve, sc.max_queue, sc.mock_device_us = slots, hbm_reserve, max_queue, mock_device_us
+    sc.per_effect, sc.direct_launches = per_effect, int(direct_launches)
     h = _vp()
     st = _lib.mrr_server_create(ctypes.byref(sc), ctypes.byref(h))
     if st != MRR_OK:
@@ -587,6 +597,15 @@ def mrr_request_info(s: Server, ticket: int) -> dict:
     if st != MRR_OK:
         raise MrrError(st, "mrr_request_info")
     return {k: getattr(i, k) for k, _ in mrr_request_info_t._fields_}
+
+
+def mrr_server_stats(s: Server) -> dict:
+    """Scheduler counters: batches, completed requests, batch graphs instantiated / updated."""
+    o = mrr_server_stats_t()
+    st = _lib.mrr_server_stats(s.handle, ctypes.byref(o))
+    if st != MRR_OK:
+        raise MrrError(st, "mrr_server_stats")
+    return {k: getattr(o, k) for k, _ in mrr_server_stats_t._fields_}
 
 
 def mrr_release(s: Server, ticket: int) -> None:

@@ -92,6 +92,17 @@ struct mrr_batch {
   float* key_out[MAX_BATCH] = {};
   int key_chunk = 0, key_grid = 0;
   uint64_t key_kernels = 0;
+  // serving: graphs keyed on topology (the contexts, in order) rather than on pointers,
+  // updated in place for every new set of frames (mrr_batch_enqueue_graph)
+  struct TopoGraph {
+    cudaGraphExec_t exec = nullptr;
+    int n = 0, chunk = 0, grid = 0;
+    mrr_ctx* ctx[MAX_BATCH] = {};
+    uint64_t kernels = 0, last_use = 0;
+  };
+  static constexpr int TOPO_CACHE = 16;
+  TopoGraph topo[TOPO_CACHE];
+  uint64_t topo_clock = 0, graph_instantiations = 0, graph_updates = 0;
   std::string err;
 };
 
@@ -1116,6 +1127,8 @@ mrr_status mrr_batch_create(mrr_batch** out) {
 void mrr_batch_destroy(mrr_batch* b) {
   if (!b) return;
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  for (auto& t : b->topo)
+    if (t.exec) cudaGraphExecDestroy(t.exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   if (b->staging_done) cudaEventDestroy(b->staging_done);
   cudaFree(b->items_dev);
@@ -1308,6 +1321,88 @@ mrr_status mrr_batch_enqueue_direct(mrr_batch* b, mrr_ctx* const* ctxs, const mr
   cudaEventRecord(b->staging_done, stream);
   b->staging_pending = true;
   return MRR_OK;
+}
+
+// Serving: enqueue a batch as a CUDA graph keyed on its topology -- which contexts, in
+// order, and the launch shape of the batched shading -- rather than on its pointers.
+// Every request brings new frames and outputs, so the launches are captured afresh; when a
+// graph of the same topology was instantiated before, the new capture is applied to it
+// with cudaGraphExecUpdate (new kernel parameters and grid sizes for the same nodes), which
+// costs far less than instantiating; a topology not seen before (or an update the driver
+// refuses) is instantiated into the least recently used of TOPO_CACHE entries.
+mrr_status mrr_batch_enqueue_graph(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames,
+                                   float* const* outs, int n, cudaStream_t stream) {
+  mrr_status st = check_batch(b, ctxs, frames, outs, n);
+  if (st != MRR_OK) return st;
+  st = wait_staging(b);
+  if (st != MRR_OK) return st;
+  mrr_batch::TopoGraph* hit = nullptr;
+  for (auto& t : b->topo) {
+    if (!t.exec || t.n != n || t.chunk != b->chunk || t.grid != b->grid_mult) continue;
+    bool same = true;
+    for (int k = 0; k < n && same; ++k) same = t.ctx[k] == ctxs[k];
+    if (same) {
+      hit = &t;
+      break;
+    }
+  }
+  if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return batch_fail(b, MRR_ECUDA, "begin capture");
+  const uint64_t before = launch_counter().load();
+  st = batch_launches(b, ctxs, frames, outs, n, b->chunk, batch_grid_blocks() * b->grid_mult, b->capture_stream);
+  const uint64_t captured = launch_counter().load() - before;
+  launch_counter().fetch_sub(captured);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->capture_stream, &graph);
+  if (st != MRR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return batch_fail(b, MRR_ECUDA, cudaGetErrorString(e));
+  bool updated = false;
+  if (hit) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(hit->exec, graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();  // an update the driver refuses leaves no sticky error
+      cudaGraphExecDestroy(hit->exec);
+      hit->exec = nullptr;
+    }
+  } else {
+    hit = &b->topo[0];
+    for (auto& t : b->topo)
+      if (!t.exec || t.last_use < hit->last_use) hit = &t;
+    if (hit->exec) cudaGraphExecDestroy(hit->exec);
+    hit->exec = nullptr;
+  }
+  if (!updated) {
+    e = cudaGraphInstantiate(&hit->exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      hit->exec = nullptr;
+      return batch_fail(b, MRR_ECUDA, "graph instantiate");
+    }
+    ++b->graph_instantiations;
+  } else {
+    ++b->graph_updates;
+  }
+  cudaGraphDestroy(graph);
+  hit->n = n;
+  hit->chunk = b->chunk;
+  hit->grid = b->grid_mult;
+  for (int k = 0; k < n; ++k) hit->ctx[k] = ctxs[k];
+  hit->kernels = captured;
+  hit->last_use = ++b->topo_clock;
+  if (cudaGraphLaunch(hit->exec, stream) != cudaSuccess) return batch_fail(b, MRR_ECUDA, "graph launch");
+  count_launches((int)captured);
+  cudaEventRecord(b->staging_done, stream);
+  b->staging_pending = true;
+  return MRR_OK;
+}
+
+void mrr_batch_graph_counts(const mrr_batch* b, uint64_t* instantiations, uint64_t* updates) {
+  *instantiations = b ? b->graph_instantiations : 0;
+  *updates = b ? b->graph_updates : 0;
 }
 
 extern "C" {

@@ -286,3 +286,8 @@ inline void count_launches(int n) { launch_counter().fetch_add((uint64_t)n, std:
 // Serving uses the batch path without graph capture (api.cu).
 mrr_status mrr_batch_enqueue_direct(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames,
                                     float* const* outs, int n, cudaStream_t stream);
+// Serving: the batch as a CUDA graph keyed on its topology (contexts in order), captured
+// afresh and applied to a cached graph of that topology with cudaGraphExecUpdate.
+mrr_status mrr_batch_enqueue_graph(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer* frames,
+                                   float* const* outs, int n, cudaStream_t stream);
+void mrr_batch_graph_counts(const mrr_batch* b, uint64_t* instantiations, uint64_t* updates);

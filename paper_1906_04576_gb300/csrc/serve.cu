@@ -1,13 +1,15 @@
 // serve.cu -- the serving loop: frame requests of mixed size and effect, admitted as
 // slots free up, grouped into batched launches, with per-request latency records.
 //
-// A slot is the device state one batch needs: one context per effect (level pyramids,
-// work lists, sub-images -- resident for the server's lifetime), a stream and a batch
-// object.  The number of slots is bounded by the configuration and by free device
-// memory (slots are created until the next one would eat into the reserve).  A
-// scheduler thread takes pending requests in arrival order, packs up to one request per
-// effect into a batch (one persistent shading launch for all of them), enqueues it on a
-// free slot's stream and records an event; it polls the events of busy slots and
+// A slot is the device state one batch needs: per_effect contexts per effect (level
+// pyramids, work lists, sub-images -- resident for the server's lifetime), a stream and a
+// batch object.  The number of slots is bounded by the configuration and by free device
+// memory (slots are created until the next one would eat into the reserve).  A scheduler
+// thread takes pending requests in arrival order, packs up to per_effect requests of each
+// effect into a batch (one persistent shading launch for all of them), orders the batch's
+// contexts by effect and index so that a given set of contexts always forms the same
+// topology, enqueues it on a free slot's stream as a graph keyed on that topology (see
+// mrr_batch_enqueue_graph) and records an event; it polls the events of busy slots and
 // completes their requests.  Requests that arrive while others run are dispatched as
 // soon as a slot frees, so work of different requests overlaps on the device.
 // mrr_submit / mrr_poll / mrr_wait are thread-safe.  Test mode (mock_device_us > 0)
@@ -41,8 +43,10 @@ struct Req {
   float device_ms = 0.f;
 };
 
+constexpr int MAX_PER_EFFECT = 8;
+
 struct Slot {
-  mrr_ctx* ctx[3] = {nullptr, nullptr, nullptr};
+  mrr_ctx* ctx[3][MAX_PER_EFFECT] = {};
   cudaStream_t stream = nullptr;
   mrr_batch* batch = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
@@ -72,7 +76,8 @@ namespace {
 bool mock(const mrr_server* s) { return s->cfg.mock_device_us > 0; }
 
 void destroy_slot(Slot& sl) {
-  for (auto& c : sl.ctx) mrr_destroy(c);
+  for (auto& row : sl.ctx)
+    for (auto& c : row) mrr_destroy(c);
   if (sl.batch) mrr_batch_destroy(sl.batch);
   if (sl.ev_start) cudaEventDestroy(sl.ev_start);
   if (sl.ev_done) cudaEventDestroy(sl.ev_done);
@@ -86,8 +91,10 @@ mrr_status create_slot(const mrr_server_config& cfg, Slot& sl) {
     mrr_config c = cfg.effect_cfg[e];
     c.effect = (mrr_effect)e;
     c.no_graph = 1;
-    mrr_status st = mrr_create(&c, &sl.ctx[e]);
-    if (st != MRR_OK) return st;
+    for (int k = 0; k < cfg.per_effect; ++k) {
+      mrr_status st = mrr_create(&c, &sl.ctx[e][k]);
+      if (st != MRR_OK) return st;
+    }
   }
   if (mrr_batch_create(&sl.batch) != MRR_OK) return MRR_ENOMEM;
   if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return MRR_ECUDA;
@@ -114,33 +121,41 @@ void finish_slot(mrr_server* s, Slot& sl, mrr_status st) {
   s->cv_done.notify_all();
 }
 
-// Pack pending requests into a batch for slot `sl` (at most one per effect, arrival
-// order, skipping requests that would repeat an effect) and enqueue it.  Caller holds
-// the lock.
+// Pack pending requests into a batch for slot `sl` (at most per_effect of each effect, in
+// arrival order, skipping requests whose effect is full) and enqueue it.  The batch lists
+// its contexts by effect, then index.  Caller holds the lock.
 void dispatch(mrr_server* s, Slot& sl) {
-  mrr_ctx* ctxs[3];
-  mrr_gbuffer frames[3];
-  float* outs[3];
+  const int per = s->cfg.per_effect;
+  uint64_t chosen[3][MAX_PER_EFFECT];
+  int count[3] = {0, 0, 0};
   int n = 0;
-  bool used[3] = {false, false, false};
   const int64_t t_dispatch = now_ns();  // one dispatch time for the whole batch
-  for (auto it = s->pending.begin(); it != s->pending.end() && n < 3;) {
+  for (auto it = s->pending.begin(); it != s->pending.end() && n < mrr::MAX_BATCH;) {
     Req& q = s->reqs[*it];
     const int e = (int)q.r.effect;
-    if (used[e]) {
+    if (count[e] >= per) {
       ++it;
       continue;
     }
-    used[e] = true;
-    ctxs[n] = sl.ctx[e];
-    frames[n] = q.r.frame;
-    outs[n] = q.r.out_dev;
+    chosen[e][count[e]++] = q.ticket;
     q.start_ns = t_dispatch;
     sl.tickets.push_back(q.ticket);
     ++n;
     it = s->pending.erase(it);
   }
   if (n == 0) return;
+  mrr_ctx* ctxs[mrr::MAX_BATCH];
+  mrr_gbuffer frames[mrr::MAX_BATCH];
+  float* outs[mrr::MAX_BATCH];
+  int k = 0;
+  for (int e = 0; e < 3; ++e)
+    for (int j = 0; j < count[e]; ++j) {
+      const Req& q = s->reqs[chosen[e][j]];
+      ctxs[k] = sl.ctx[e][j];
+      frames[k] = q.r.frame;
+      outs[k] = q.r.out_dev;
+      ++k;
+    }
   sl.busy = true;
   ++s->batches;
   if (mock(s)) {
@@ -148,7 +163,8 @@ void dispatch(mrr_server* s, Slot& sl) {
     return;
   }
   cudaEventRecord(sl.ev_start, sl.stream);
-  mrr_status st = mrr_batch_enqueue_direct(sl.batch, ctxs, frames, outs, n, sl.stream);
+  mrr_status st = s->cfg.direct_launches ? mrr_batch_enqueue_direct(sl.batch, ctxs, frames, outs, n, sl.stream)
+                                         : mrr_batch_enqueue_graph(sl.batch, ctxs, frames, outs, n, sl.stream);
   cudaEventRecord(sl.ev_done, sl.stream);
   if (st != MRR_OK) finish_slot(s, sl, st);
 }
@@ -188,7 +204,9 @@ mrr_status mrr_server_create(const mrr_server_config* cfg, mrr_server** out) {
   if (!cfg) return MRR_EINVAL;
   int enabled = 0;
   for (int e = 0; e < 3; ++e) enabled += cfg->effect_enabled[e] ? 1 : 0;
-  if (!enabled || cfg->slots < 0 || cfg->max_queue < 0) return MRR_EINVAL;
+  if (!enabled || cfg->slots < 0 || cfg->max_queue < 0 || cfg->per_effect < 0) return MRR_EINVAL;
+  const int per = cfg->per_effect ? cfg->per_effect : 2;
+  if (per > MAX_PER_EFFECT || per * enabled > mrr::MAX_BATCH) return MRR_EINVAL;
   for (int e = 0; e < 3; ++e)  // requests are served in batches, which take no pyramid gathers
     if (cfg->effect_enabled[e] && (cfg->effect_cfg[e].pyramid_gathers || cfg->effect_cfg[e].disjoint))
       return MRR_EUNSUPPORTED;
@@ -197,6 +215,7 @@ mrr_status mrr_server_create(const mrr_server_config* cfg, mrr_server** out) {
   s->cfg = *cfg;
   if (s->cfg.slots == 0) s->cfg.slots = 4;
   if (s->cfg.max_queue == 0) s->cfg.max_queue = 1024;
+  s->cfg.per_effect = per;
   if (mock(s)) {
     s->slots.resize(s->cfg.slots);
   } else {
@@ -303,6 +322,21 @@ mrr_status mrr_request_info(mrr_server* s, uint64_t ticket, mrr_request_info_t* 
   out->start_ns = q.start_ns;
   out->done_ns = q.done_ns;
   out->device_ms = q.device_ms;
+  return MRR_OK;
+}
+
+mrr_status mrr_server_stats(mrr_server* s, mrr_server_stats_t* out) {
+  if (!s || !out) return MRR_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  out->batches = s->batches;
+  out->completed = s->completed;
+  out->graph_instantiations = out->graph_updates = 0;
+  for (const Slot& sl : s->slots) {
+    uint64_t inst = 0, upd = 0;
+    if (sl.batch) mrr_batch_graph_counts(sl.batch, &inst, &upd);
+    out->graph_instantiations += inst;
+    out->graph_updates += upd;
+  }
   return MRR_OK;
 }
 

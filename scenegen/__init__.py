@@ -249,5 +249,5 @@ WORKLOADS = {
                                dict(effect="ssm", blocker_samples=32, pcf_samples=64, shadow_size=2048, levels=4,
                                     precision="fp32"),
                                dict(effect="ssgi", samples=32, radius=1.0, levels=4, precision="fp16")],
-                      n_boxes=64, n_spheres=16, scenes_per_resolution=2, slots=4),
+                      n_boxes=64, n_spheres=16, scenes_per_resolution=6, slots=4, per_effect=2),
 }

@@ -68,3 +68,41 @@ def test_mixed_requests_equal_frames_rendered_alone(mrr):
     mrr.mrr_server_destroy(srv)
     for c in alone.values():
         mrr.mrr_destroy(c)
+
+
+def test_graphs_are_reused_across_requests_with_fresh_buffers(mrr):
+    """Waves of requests, every one with its own newly allocated inputs and output: the
+    batches repeat topologies (the same contexts in the same order), so their graphs are
+    updated in place rather than instantiated again, and every result still equals the
+    frame rendered alone."""
+    import torch
+    W, H = 480, 272
+    cfgs = {e: _cfg(e, W, H) for e in ("ssao", "ssgi")}
+    srv = mrr.mrr_server_create(cfgs, slots=1, per_effect=2)
+    alone = {e: mrr.mrr_create(cfgs[e]) for e in cfgs}
+    sizes = [(480, 272), (320, 180), (400, 224), (211, 97)]
+    for wave in range(4):
+        jobs = [("ssao", *sizes[wave % 4]), ("ssao", *sizes[(wave + 1) % 4]), ("ssgi", *sizes[(wave + 2) % 4])]
+        devs, outs = [], []
+        for k, (effect, w, h) in enumerate(jobs):
+            fr = sg.gbuffer(10 * wave + k, w, h, 20, 6)
+            devs.append(mrr.upload_frame(fr, PREC[effect]))        # fresh device buffers
+            o = mrr.alloc_output(mrr.Context(0, cfgs[effect]), w, h)
+            o.fill_(float("nan"))
+            outs.append(o)
+        torch.cuda.synchronize()
+        tickets = [mrr.mrr_submit(srv, e, d, o) for (e, _, _), d, o in zip(jobs, devs, outs)]
+        for t in tickets:
+            assert mrr.mrr_wait(srv, t, 30_000_000_000) == mrr.MRR_OK
+        for (effect, w, h), d, o in zip(jobs, devs, outs):
+            ref = mrr.alloc_output(alone[effect], w, h)
+            mrr.mrr_render(alone[effect], d, ref)
+            torch.cuda.synchronize()
+            assert torch.equal(o, ref), (wave, effect)
+    st = mrr.mrr_server_stats(srv)
+    assert st["completed"] == 12
+    assert st["graph_updates"] >= 1
+    assert st["graph_instantiations"] + st["graph_updates"] == st["batches"]
+    mrr.mrr_server_destroy(srv)
+    for c in alone.values():
+        mrr.mrr_destroy(c)

@@ -27,7 +27,7 @@ def _cfgs(W=4096, H=4096):
 
 
 def test_every_request_completes_and_effects_share_batches(mrr):
-    srv = mrr.mrr_server_create(_cfgs(), slots=1, mock_device_us=20_000)
+    srv = mrr.mrr_server_create(_cfgs(), slots=1, mock_device_us=20_000, per_effect=1)
     assert mrr.mrr_server_slots(srv) == 1
     t0 = mrr.mrr_submit(srv, "ssao", (640, 360))     # dispatched at once: the slot is free
     time.sleep(0.005)
@@ -53,7 +53,7 @@ def test_every_request_completes_and_effects_share_batches(mrr):
 
 
 def test_slots_overlap(mrr):
-    srv = mrr.mrr_server_create(_cfgs(), slots=3, mock_device_us=50_000)
+    srv = mrr.mrr_server_create(_cfgs(), slots=3, mock_device_us=50_000, per_effect=1)
     ts = [mrr.mrr_submit(srv, "ssao", (64, 64)) for _ in range(3)]
     for t in ts:
         assert mrr.mrr_wait(srv, t, 2_000_000_000) == mrr.MRR_OK
@@ -78,6 +78,29 @@ def test_queue_bound_and_timeouts(mrr):
     for t in (t0, t1, t2):
         assert mrr.mrr_wait(srv, t, 5_000_000_000) == mrr.MRR_OK
     mrr.mrr_server_destroy(srv)
+
+
+def test_batches_hold_per_effect_requests_of_each_effect(mrr):
+    srv = mrr.mrr_server_create(_cfgs(), slots=1, mock_device_us=20_000, per_effect=2)
+    t0 = mrr.mrr_submit(srv, "ssgi", (640, 360))     # occupies the slot
+    time.sleep(0.005)
+    effects = ["ssao", "ssao", "ssao", "ssgi", "ssm", "ssm"]
+    tickets = [mrr.mrr_submit(srv, e, (640, 360)) for e in effects]
+    for t in [t0] + tickets:
+        assert mrr.mrr_wait(srv, t, 2_000_000_000) == mrr.MRR_OK
+    start = [mrr.mrr_request_info(srv, t)["start_ns"] for t in tickets]
+    first = {i for i in range(6) if start[i] == min(start)}
+    # two SSAO, the SSGI and both SSM go together; the third SSAO waits for the next batch
+    assert first == {0, 1, 3, 4, 5}
+    assert start[2] > min(start)
+    st = mrr.mrr_server_stats(srv)
+    assert st["batches"] == 3 and st["completed"] == 7
+    assert st["graph_instantiations"] == 0 and st["graph_updates"] == 0   # no device work in mock mode
+    mrr.mrr_server_destroy(srv)
+    # at most eight requests per batch: 3 effects x 3 is refused
+    with pytest.raises(mrr.MrrError) as ei:
+        mrr.mrr_server_create(_cfgs(), slots=1, mock_device_us=1000, per_effect=3)
+    assert ei.value.status == mrr.MRR_EINVAL
 
 
 def test_requests_the_server_cannot_take_are_rejected(mrr):
