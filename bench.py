@@ -563,6 +563,7 @@ def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
 
 
 def main():
+    global SCENES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -571,10 +572,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip mrr_autotune (library defaults)")
+    ap.add_argument("--scenes", type=int, default=SCENES,
+                    help="seeded scenes in rotation (fewer keep a profiler capture's device memory small)")
     ap.add_argument("--rate", type=float, default=None,
                     help="serving mix only: mean request rate per second (default: the workload's)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    SCENES = max(1, args.scenes)
     if args.impl == "reference":
         return run_reference(args)
 

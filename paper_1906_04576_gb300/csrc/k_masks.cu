@@ -11,9 +11,10 @@
 //   enabled finer level (inclusive nesting, Fig. 2/3 -- children always lie in the same
 //   tile) and, for a whole frame, reserves each level's list room with one atomicAdd.
 //   Last, every thread writes its texels: a_i is evaluated only where the dilation is set
-//   -- the horizontal sums from the texel's (2R_i+1)-bit windows (a table of the exact
-//   window sums where one is given), the vertical taps with one fused multiply-add each in
-//   ascending order, the definition's arithmetic exactly -- and is 0 elsewhere.  The
+//   -- the horizontal sums over the (2R_i+1)-bit windows (a table of the exact window sums
+//   where one is given; above level 0 each row's sums are computed once, beside its D row,
+//   and shared by the texels of the column), the vertical taps with one fused multiply-add
+//   each in ascending order, the definition's arithmetic exactly -- and is 0 elsewhere.  The
 //   coarsest level is written as a = 1, S = 1; disabled levels as 0.  Staged calls also get
 //   every pixel's owning level (the finest enabled level whose stencil covers it).
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
@@ -41,9 +42,16 @@ constexpr int MAXR = 6;
 constexpr int MTHREADS = 128;            // threads per CTA
 static_assert(ER % (MTHREADS / 32) == 0, "edge rows split evenly over the warps");
 
+// Horizontal window sums of the blurred levels above 0, column-major: h(t, c) at [c][t],
+// t = row of the D region, c = tile column.  The row pitches (34 at level 1, 36 at level 2)
+// put a warp's 32 reads of one tap (two rows x 16 columns, four rows x 8 columns) in 32
+// different banks.
+constexpr int H1P = 34, H2P = 36;
+
 struct MaskSmem {
   uint4 E[ER];                           // edge rows as bits: word w bit b = column 32 w + b (w = 3: zero)
-  uint32_t D[MRR_MAX_LEVELS][32];        // D_i rows over the blur region (levels >= 1) as bits
+  float H1[TS / 2][H1P];                 // level 1's h(t, c)
+  float H2[TS / 4][H2P];                 // level 2's h(t, c)
   uint32_t B[MRR_MAX_LEVELS][TS];        // [a_i > 0] rows (before nesting), tile texels only
   uint32_t S[MRR_MAX_LEVELS][TS];        // stencil rows of every level, tile texels only
   float g[MRR_MAX_LEVELS][16];           // the Gaussians of Table 1
@@ -159,14 +167,29 @@ __device__ __forceinline__ void blur_bits0(const MaskParams& m, MaskSmem& sm, in
 }
 
 // Level I >= 1, radius R: lane t < DN computes row t of D_I over the blur region (level
-// rows q0y - R .. q0y + Ti + R - 1, columns q0x - R ..), lane r < Ti the dilation.
+// rows q0y - R .. q0y + Ti + R - 1, columns q0x - R ..) and, for every tile column c, the
+// horizontal sum h(t, c) of the taps over the set bits of the row's (2R+1)-bit window at c
+// (the table of exact window sums where one is given); lane r < Ti the dilation.  The sums
+// are shared by the 2R+1 texels of a column that read them.
 template <int I, int R>
 __device__ __forceinline__ void blur_bits(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   constexpr int Ti = TS >> I, DN = Ti + 2 * R;
   static_assert(DN <= 32, "a D region fits one warp");
+  static_assert(I == 1 || I == 2, "blurred levels above 0 are 1 and 2");
+  constexpr int HP = I == 1 ? H1P : H2P;
+  static_assert(DN <= HP, "a D region fits the pitch");
+  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
   const int lane = threadIdx.x & 31;
   const uint32_t d = lane < DN ? d_row<I, R>(sm, lane) : 0u;
-  if (lane < DN) sm.D[I][lane] = d;
+  if (lane < DN) {
+    float* hs = I == 1 ? &sm.H1[0][0] : &sm.H2[0][0];
+    const float* lut = m.lut[I];
+#pragma unroll
+    for (int c = 0; c < Ti; ++c) {
+      const uint32_t win = (d >> c) & WMASK;
+      hs[c * HP + lane] = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
+    }
+  }
   uint32_t h = 0u;
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) h |= d >> k;
@@ -296,18 +319,13 @@ __device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int
   return s;
 }
 
-// Level I >= 1, tile texel (r, c): windows from the D rows.
+// Level I >= 1, tile texel (r, c): the horizontal sums of rows r .. r + 2R of the D region.
 template <int I, int R>
-__device__ __forceinline__ float alpha_at(const MaskParams& m, const MaskSmem& sm, int r, int c) {
-  constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
-  const float* lut = m.lut[I];
+__device__ __forceinline__ float alpha_at(const MaskSmem& sm, int r, int c) {
+  const float* h = I == 1 ? &sm.H1[c][r] : &sm.H2[c][r];
   float s = 0.0f;
 #pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) {
-    const uint32_t win = (sm.D[I][r + t] >> c) & WMASK;
-    const float h = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
-    s = fmaf(sm.g[I][t], h, s);
-  }
+  for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[I][t], h[t], s);
   return s;
 }
 
@@ -363,7 +381,7 @@ __device__ __forceinline__ void write_level(const MaskParams& m, const MaskSmem&
     const bool st = (srow >> c) & 1u;
     float a = 0.0f;
     if (mode == 1) a = 1.0f;
-    else if (mode == 0 && ((sm.B[I][r] >> c) & 1u)) a = alpha_at<I, R>(m, sm, r, c);
+    else if (mode == 0 && ((sm.B[I][r] >> c) & 1u)) a = alpha_at<I, R>(sm, r, c);
     const size_t q = (size_t)qy * Wi + qx;
     m.alpha[I][q] = a;
     m.stencil[I][q] = st ? 1 : 0;
