@@ -321,36 +321,24 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       const float3 n1 = smem_normal(sn, (ly + 1) * T::NW + cn), nd = smem_normal(sn, (ly + 2) * T::NW + cn);
       const float3 nl0 = smem_normal(sn, ly * T::NW + cn - 1), nr0 = smem_normal(sn, ly * T::NW + cn + 1);
       const float3 nl1 = smem_normal(sn, (ly + 1) * T::NW + cn - 1), nr1 = smem_normal(sn, (ly + 1) * T::NW + cn + 1);
-      // n_p . n_q for both pixels at once (two independent IEEE products and sums in the
-      // order x, y, z -- the same bits as the scalar expression, products commuting)
-      const float2 N0x = make_float2(n0.x, n1.x), N0y = make_float2(n0.y, n1.y), N0z = make_float2(n0.z, n1.z);
-      auto dot2 = [&](float3 a, float3 b) {
-        const float2 px = __fmul2_rn(N0x, make_float2(a.x, b.x));
-        const float2 py = __fmul2_rn(N0y, make_float2(a.y, b.y));
-        const float2 pz = __fmul2_rn(N0z, make_float2(a.z, b.z));
-        return __fadd2_rn(__fadd2_rn(px, py), pz);
-      };
-      const float2 hl = dot2(nl0, nl1), hr = dot2(nr0, nr1), vu = dot2(nu, n0), vd = dot2(n1, nd);
+      // n_p . n_q in the order x, y, z, one IEEE operation each
+      auto dot = [](float3 a, float3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; };
+      const float hl0 = dot(n0, nl0), hl1 = dot(n1, nl1), hr0 = dot(n0, nr0), hr1 = dot(n1, nr1);
+      const float vu0 = dot(n0, nu), vu1 = dot(n1, n0), vd0 = dot(n0, n1), vd1 = dot(n1, nd);
       const float cosT = p.normal_cos, farp2 = farp;
       const bool hasl = x > 0, hasr = x < W - 1;
       const bool hasu0 = y > 0, hasd1 = y + 1 < H - 1;
-      // Laplacians along x for both rows and along y
-      // a - b is a + (-b) exactly; -2 d is exact
-      const float2 m2d = __fmul2_rn(make_float2(-2.0f, -2.0f), make_float2(d0, d1));
-      const float2 lapx = __fadd2_rn(__fadd2_rn(make_float2(dl0, dl1), make_float2(dr0, dr1)), m2d);
-      const float2 lapy = __fadd2_rn(__fadd2_rn(make_float2(du, d0), make_float2(d1, dd)), m2d);
-      const float2 thr = __fmul2_rn(make_float2(p.depth_rel, p.depth_rel), make_float2(d0, d1));
-      // The decisions combine with non-short-circuit & and | (every operand is already in
-      // a register, so nothing is saved by skipping one): branch-free predicate logic.
+      const float m2d0 = -2.0f * d0, m2d1 = -2.0f * d1;
+      const float lapx0 = (dl0 + dr0) + m2d0, lapx1 = (dl1 + dr1) + m2d1;
+      const float lapy0 = (du + d1) + m2d0, lapy1 = (d0 + dd) + m2d1;
+      const float thr0 = p.depth_rel * d0, thr1 = p.depth_rel * d1;
       const bool hasd0 = y + 1 < H;
-      // pixel 0: up neighbour row r0 - 1, down neighbour pixel 1
-      bool e0 = (hasl & ((dl0 >= farp2) | (hl.x < cosT))) | (hasr & ((dr0 >= farp2) | (hr.x < cosT))) |
-                (hasu0 & ((du >= farp2) | (vu.x < cosT))) | (hasd0 & ((d1 >= farp2) | (vd.x < cosT))) |
-                (hasl & hasr & (fabsf(lapx.x) > thr.x)) | (hasu0 & hasd0 & (fabsf(lapy.x) > thr.x));
-      // pixel 1: up neighbour pixel 0, down neighbour row r0 + 2
-      bool e1 = (hasl & ((dl1 >= farp2) | (hl.y < cosT))) | (hasr & ((dr1 >= farp2) | (hr.y < cosT))) |
-                ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
-                (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
+      bool e0 = (hasl & ((dl0 >= farp2) | (hl0 < cosT))) | (hasr & ((dr0 >= farp2) | (hr0 < cosT))) |
+                (hasu0 & ((du >= farp2) | (vu0 < cosT))) | (hasd0 & ((d1 >= farp2) | (vd0 < cosT))) |
+                (hasl & hasr & (fabsf(lapx0) > thr0)) | (hasu0 & hasd0 & (fabsf(lapy0) > thr0));
+      bool e1 = (hasl & ((dl1 >= farp2) | (hl1 < cosT))) | (hasr & ((dr1 >= farp2) | (hr1 < cosT))) |
+                ((d0 >= farp2) | (vu1 < cosT)) | (hasd1 & ((dd >= farp2) | (vd1 < cosT))) |
+                (hasl & hasr & (fabsf(lapx1) > thr1)) | (hasd1 & (fabsf(lapy1) > thr1));
       if constexpr (SSM) {
         // hard-shadow bits of rows y - 1 .. y + 2 (clamped; the has flags drop rows and
         // columns outside the image), the words left and right of the tile's word

@@ -41,6 +41,7 @@ constexpr int EX = 32;                   // column of the tile's first pixel in 
 constexpr int MAXR = 6;
 constexpr int MTHREADS = 128;            // threads per CTA
 static_assert(ER % (MTHREADS / 32) == 0, "edge rows split evenly over the warps");
+static_assert(MTHREADS == 128, "four warps: one per level in the bit phase");
 
 // Horizontal window sums of the blurred levels above 0, column-major: h(t, c) at [c][t],
 // t = row of the D region, c = tile column.  The row pitches (34 at level 1, 36 at level 2)
@@ -59,6 +60,10 @@ struct MaskSmem {
   // frame mode: per-row prefix counts and the tile's first list position per level
   uint32_t rowpre[MRR_MAX_LEVELS][TS];
   uint32_t excl[MRR_MAX_LEVELS];
+  // frame mode, level 0: rows of the pixels within r1 of an edge (alpha 1 without a_0),
+  // and per warp the pixels whose a_0 is still needed, (row << 5) | column
+  uint32_t sure[TS];
+  uint16_t ring[MTHREADS / 32][TS * TS / (MTHREADS / 32)];
 };
 
 // Sum of the taps g[t] whose bit t is set in win, in ascending t, one rounding per add.
@@ -164,6 +169,34 @@ __device__ __forceinline__ void blur_bits0(const MaskParams& m, MaskSmem& sm, in
   v &= valid_row<0>(m, x0, y0, lane);
   sm.B[0][lane] = v;
   sm.S[0][lane] = v;
+}
+
+// Frame mode, level 0: bit c of sure[lane] is set when an edge pixel lies within
+// Chebyshev distance r1 = m.sure0 (0..6) of tile pixel (lane, c) -- the box dilation of the
+// staged edge rows, as blur_bits0 computes it for a runtime radius.
+__device__ __forceinline__ void sure_bits0(const MaskParams& m, MaskSmem& sm) {
+  const int lane = threadIdx.x & 31;
+  const int r1 = m.sure0;
+  auto rowd = [&](int er) {
+    const uint4 row = sm.E[er];
+    // clamped funnel shifts: r1 = 0 shifts by 32
+    const uint32_t lo = __funnelshift_rc(row.x, row.y, 32 - r1);  // bit k: column x0 - r1 + k
+    const uint32_t hi = __funnelshift_rc(row.y, row.z, 32 - r1);  // bit k: column x0 + 32 - r1 + k
+    const unsigned long long w = ((unsigned long long)hi << 32) | lo;
+    unsigned long long d = 0ull;
+    for (int t = 0; t <= 2 * r1; ++t) d |= w >> t;
+    return (uint32_t)d;
+  };
+  const uint32_t a = rowd(MG - r1 + lane);
+  const uint32_t b = lane < 2 * r1 ? rowd(MG - r1 + 32 + lane) : 0u;
+  uint32_t v = 0u;
+  for (int t = 0; t <= 2 * r1; ++t) {
+    const int src = lane + t;
+    const uint32_t va = __shfl_sync(0xffffffffu, a, src & 31);
+    const uint32_t vb = __shfl_sync(0xffffffffu, b, src & 31);
+    v |= src < 32 ? va : vb;
+  }
+  sm.sure[lane] = v;
 }
 
 // Level I >= 1, radius R: lane t < DN computes row t of D_I over the blur region (level
@@ -301,11 +334,11 @@ __device__ __forceinline__ void disjoint_bits(const MaskParams& m, MaskSmem& sm)
 // set bits of the (2R+1)-bit window (a table of the exact window sums where one is given),
 // a = fma(g_2R, h(2R), ... fma(g_0, h(0), 0)).
 
-// Level 0, tile texel (r, lane): windows from the staged edge rows.
+// Level 0, tile texel (r, c): windows from the staged edge rows.
 template <int R>
-__device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int r, int lane) {
+__device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int r, int c) {
   constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
-  const int b = EX - R + lane;  // first staged column of the lane's window
+  const int b = EX - R + c;  // first staged column of the texel's window
   const int k = b >> 5, sh = b & 31;
   float s = 0.0f;
 #pragma unroll
@@ -332,35 +365,53 @@ __device__ __forceinline__ float alpha_at(const MaskSmem& sm, int r, int c) {
 // ---- writing the levels
 
 // Level 0 (mode 0 blurred, 1 constant one, 2 disabled).  Frame mode: the tile's level-0
-// list entries (tile-local row-major, at the reserved position) and a_0 beside them; staged
-// mode: a_0 and S_0 for every pixel of the tile.  Warp w takes tile rows w, w + 4, ...
+// list entries (tile-local row-major, at the reserved position) and a_0 beside them -- 1
+// where an edge lies within r1 (the blend's alpha is 1 there either way), else the exact
+// a_0, evaluated for the warp's queued pixels 32 at a time so that no lane idles on a pixel
+// that needs none; staged mode: a_0 and S_0 for every pixel of the tile.  Warp w takes tile
+// rows w, w + 4, ...
 template <int R>
-__device__ __forceinline__ void write_level0(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+__device__ __forceinline__ void write_level0(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mode = m.mode[0];
   const bool use_lut = m.lut0 != nullptr && (1 << (2 * R + 1)) <= MASK_LUT_MAX;
   const int x = x0 + lane;
   const size_t cap = (size_t)m.Wi[0] * m.Hi[0];
+  if (m.a0c) {
+    const uint32_t below = (1u << lane) - 1u;
+    uint16_t* q = sm.ring[warp];
+    int qn = 0;
+    for (int r = warp; r < TS; r += MTHREADS / 32) {
+      const uint32_t bits = sm.S[0][r];
+      if (bits == 0u) continue;
+      const uint32_t ring = mode == 0 ? bits & ~(m.sure0 >= 0 ? sm.sure[r] : 0u) : 0u;
+      const bool on = (bits >> lane) & 1u, queued = (ring >> lane) & 1u;
+      const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(bits & below);
+      if (on && pos < cap) {
+        m.list[0][pos] = ((uint32_t)(y0 + r) << 16) | (uint32_t)x;
+        if (!queued) m.a0c[pos] = 1.0f;
+      }
+      if (queued) q[qn + __popc(ring & below)] = (uint16_t)((r << 5) | lane);
+      qn += __popc(ring);
+    }
+    __syncwarp();
+    for (int k = lane; k < qn; k += 32) {
+      const int r = q[k] >> 5, c = q[k] & 31;
+      const float a = alpha0_at<R>(sm, use_lut, r, c);
+      const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(sm.S[0][r] & ((1u << c) - 1u));
+      if (pos < cap) m.a0c[pos] = a;
+    }
+    return;
+  }
   for (int r = warp; r < TS; r += MTHREADS / 32) {
     const int y = y0 + r;
     const uint32_t bits = sm.S[0][r];
     const bool on = (bits >> lane) & 1u;
-    if (m.a0c) {
-      if (bits == 0u) continue;
-      if (!on) continue;
-      const float a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
-      const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(bits & ((1u << lane) - 1u));
-      if (pos < cap) {
-        m.list[0][pos] = ((uint32_t)y << 16) | (uint32_t)x;
-        m.a0c[pos] = a;
-      }
-    } else {
-      if (y >= m.H || x >= m.W || !m.alpha[0]) continue;
-      float a = 0.0f;
-      if (on) a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
-      m.alpha[0][(size_t)y * m.W + x] = a;
-      m.stencil[0][(size_t)y * m.W + x] = on ? 1 : 0;
-    }
+    if (y >= m.H || x >= m.W || !m.alpha[0]) continue;
+    float a = 0.0f;
+    if (on) a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
+    m.alpha[0][(size_t)y * m.W + x] = a;
+    m.stencil[0][(size_t)y * m.W + x] = on ? 1 : 0;
   }
 }
 
@@ -423,7 +474,7 @@ __device__ __forceinline__ void bits_any(const MaskParams& m, MaskSmem& sm, int 
 }
 
 template <int I>
-__device__ __forceinline__ void write_any(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+__device__ __forceinline__ void write_any(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   if (I == 0) {
     switch (m.mode[0] == 0 ? m.R[0] : 1) {
       case 1: write_level0<1>(m, sm, x0, y0); break;
@@ -483,10 +534,13 @@ __device__ __forceinline__ void level_bits(const MaskParams& m, MaskSmem& sm, in
     else if (warp == 2 && m.L > 2) bits_any<2>(m, sm, x0, y0);
     else if (warp == 3 && m.L > 3) fill_bits<3>(m, sm, x0, y0, m.mode[3]);
   }
+  // frame mode: warp 3 (otherwise at most filling the coarsest level) also marks where
+  // level 0's alpha is 1 without a_0
+  if (warp == 3 && m.a0c && m.sure0 >= 0) sure_bits0(m, sm);
 }
 
 template <int SIG>
-__device__ __forceinline__ void level_values(const MaskParams& m, const MaskSmem& sm, int x0, int y0) {
+__device__ __forceinline__ void level_values(const MaskParams& m, MaskSmem& sm, int x0, int y0) {
   if constexpr (SIG == MASK_SIG_T1_4) {
     write_level0<3>(m, sm, x0, y0);
     write_level<1, 5>(m, sm, x0, y0);
@@ -762,6 +816,21 @@ bool mask_level_params(const mrr_config& c, const mrr_levels* lv, MaskParams& m)
   }
   m.label = lv->label;
   m.disjoint = c.disjoint;
+  m.sure0 = -1;
+  if (m.mode[0] == 0) {
+    const int R = m.R[0];
+    const float w = c.weight[0];
+    for (int r1 = 0; r1 <= R; ++r1) {
+      bool all = true;
+      for (int dy = -r1; dy <= r1 && all; ++dy)
+        for (int dx = -r1; dx <= r1 && all; ++dx) {
+          const float prod = m.g[0][R + dy] * m.g[0][R + dx];
+          all = w * prod >= 1.0f;
+        }
+      if (!all) break;
+      m.sure0 = r1;
+    }
+  }
   return true;
 }
 

@@ -108,6 +108,12 @@ struct MaskParams {
   uint32_t* list[MRR_MAX_LEVELS];
   uint32_t* counts;  // entries per level, zero before the launch (the tiles add to it)
   int disjoint;      // complementary tiles without overlap (the variant Sec. 3.1 rejects)
+  // Frame mode, level 0 blurred: the Chebyshev radius r1 within which any one edge pixel
+  // already makes min(w_0 a_0, 1) = 1 (-1: none).  a_0 is a fused multiply-add chain of
+  // non-negative terms, so it is at least fl(g[R+dy] g[R+dx]) for an edge at (dx, dy), and
+  // fl(w_0 a_0) >= 1 wherever fl(w_0 fl(g[R+dy] g[R+dx])) >= 1 for every offset of the
+  // box; there a0c holds 1, which the level-0 blend turns into the same alpha of 1.
+  int sure0;
 };
 constexpr int MASK_LUT_MAX = 512;  // level 0's table for R <= 4 (larger R sums the taps)
 
