@@ -100,27 +100,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def l2_copy_gbs(torch, mib=32, reps=200):
-    """L2 bandwidth for the gather roofline (MEASURED_PEAKS.json has none): a copy between
-    two buffers that stay resident in L2 (2 x 32 MiB of the 126 MB), read + write bytes
-    over CUDA-event time, best of 3 runs of back-to-back copies.  Smaller copies read
-    lower (8 MiB: about half) because each launch's ramp-up and drain weigh more."""
-    a = torch.ones(mib << 18, dtype=torch.float32, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    best = 0.0
-    for _ in range(3):
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        for _ in range(reps):
-            b.copy_(a)
-        e.record()
-        torch.cuda.synchronize()
-        best = max(best, 2 * a.numel() * 4 * reps / (s.elapsed_time(e) * 1e-3) / 1e9)
-    return best
-
-
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -788,7 +767,6 @@ def main():
         n_all += counts[i]
     peak, peak_kind = measured_peaks()
     achieved = alg / (k_ms * 1e-3) / 1e9
-    l2_gbs = l2_copy_gbs(torch)
 
     sum_multi = max_over_ranks(sum(t_multi))
     sum_full = max_over_ranks(sum(t_full))
@@ -815,10 +793,7 @@ def main():
                          "frac": round(achieved / peak, 4), "traffic": measured_traffic(args.workload),
                          "kernel": "shade_levels_kernel" + (" + shade_blocks_kernel" if sample_levels else ""),
                          "kernel_ms": round(k_ms, 5),
-                         "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs",
-                         "l2": {"achieved": round(achieved, 2), "peak": round(l2_gbs, 1), "unit": "GB/s",
-                                "frac": round(achieved / l2_gbs, 4),
-                                "peak_kind": "L2-resident copy (2 x 32 MiB), measured in this run"}},
+                         "algorithmic_bytes": int(alg), "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": round(world * e2e_steps * W * H / e2e_s / 1e6, 3), "unit": "Mpix/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "api": "mrr_render_host_async + mrr_render_host_wait (pinned host buffers; each step's "
