@@ -571,6 +571,7 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
   // stage the edge rows y0-24 .. y0+55, columns x0-32 .. x0+63, as bits (zero outside the image)
   uint32_t* Ew = reinterpret_cast<uint32_t*>(sm.E);
+  uint32_t seen = 0u;  // OR of the edge bits this thread staged
   if (m.ebits) {
     // bit-packed edge image: the three words of each staged row
     // the thread's two words (and its lookup-table entry below) are all requested before
@@ -589,6 +590,7 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
     for (int j = 0; j < RW; ++j) {
       const int k = threadIdx.x + j * MTHREADS;
       if (k < NW) Ew[4 * (k / EWORDS) + (k - (k / EWORDS) * EWORDS)] = v[j];
+      seen |= v[j];
     }
     if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
   } else if ((W & 15) == 0 && ((uintptr_t)E & 15) == 0) {
@@ -620,6 +622,7 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
         const uint32_t q3 = (__vcmpne4(v[j].w, 0u) & 0x01010101u) * 0x01020408u;
         const uint32_t bits = (q0 >> 24) | ((q1 >> 24) << 4) | ((q2 >> 24) << 8) | ((q3 >> 24) << 12);
         reinterpret_cast<uint16_t*>(Ew + 4 * r)[sg] = (uint16_t)bits;
+        seen |= bits;
       }
     }
     if (threadIdx.x < ER) Ew[4 * threadIdx.x + EWORDS] = 0u;
@@ -635,6 +638,7 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
         const bool e = row_in && x >= 0 && x < W && __ldg(E + (size_t)y * W + x) != 0;
         const uint32_t b = __ballot_sync(0xffffffffu, e);
         if (lane == 0) Ew[4 * r + w] = b;
+        seen |= b;
       }
       if (lane == 0) Ew[4 * r + EWORDS] = 0u;
     }
@@ -645,9 +649,18 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   }
   if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
     for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
-  __syncthreads();
-  // 1. [a_i > 0] of every level as bit rows (one warp per level)
-  level_bits<SIG>(m, sm, x0, y0);
+  const bool any_edge = __syncthreads_or(seen != 0u) != 0;
+  // 1. [a_i > 0] of every level as bit rows (one warp per level).  With no edge anywhere in
+  // the staged rows every blurred level's window sums are 0 (each D row is made of staged
+  // rows only), so [a > 0] is empty there and only the constant levels have bits.
+  if (any_edge) {
+    level_bits<SIG>(m, sm, x0, y0);
+  } else if (warp < m.L) {
+    if (warp == 0) fill_bits<0>(m, sm, x0, y0, m.mode[0]);
+    else if (warp == 1) fill_bits<1>(m, sm, x0, y0, m.mode[1]);
+    else if (warp == 2) fill_bits<2>(m, sm, x0, y0, m.mode[2]);
+    else fill_bits<3>(m, sm, x0, y0, m.mode[3]);
+  }
   __syncthreads();
   if (m.disjoint) {  // the ablation's stencils, finer levels first
     if (warp == 0) disjoint_bits(m, sm);
