@@ -502,6 +502,64 @@ __device__ __forceinline__ void write_any(const MaskParams& m, MaskSmem& sm, int
   }
 }
 
+// ---- frame mode, a tile with no edge in its staged rows: every blurred or disabled level
+// is 0 over the tile and the coarsest level is 1, so the tile's outputs are written
+// directly -- the same values and list entries (in the same tile-local row-major order)
+// as the general path, without its nesting, scans and per-texel tests.
+
+// Level I (blurred or disabled): a = 0 and S = 0 for every tile texel inside the level;
+// thread t takes column t mod Ti of rows t / Ti, t / Ti + 128 / Ti, ...
+template <int I>
+__device__ __forceinline__ void empty_zero_level(const MaskParams& m, int x0, int y0) {
+  constexpr int Ti = TS >> I, RS = MTHREADS / Ti;
+  static_assert(I >= 1 && MTHREADS % Ti == 0, "levels above 0");
+  if (!m.alpha[I]) return;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  const int nvx = min(Ti, m.Wi[I] - q0x), nvy = min(Ti, m.Hi[I] - q0y);
+  const int c = threadIdx.x & (Ti - 1);
+  if (c >= nvx) return;
+  for (int r = threadIdx.x / Ti; r < nvy; r += RS) {
+    const size_t q = (size_t)(q0y + r) * m.Wi[I] + q0x + c;
+    m.alpha[I][q] = 0.0f;
+    m.stencil[I][q] = 0;
+  }
+}
+
+// Level I (the coarsest, a = 1 and S = 1 everywhere), by one warp: the tile's texels and
+// their list entries at one reservation.
+template <int I>
+__device__ __forceinline__ void empty_one_level(const MaskParams& m, int x0, int y0) {
+  constexpr int Ti = TS >> I;
+  static_assert(I >= 1, "levels above 0");
+  const int lane = threadIdx.x & 31;
+  const int q0x = x0 >> I, q0y = y0 >> I;
+  const int nvx = min(Ti, m.Wi[I] - q0x), nvy = min(Ti, m.Hi[I] - q0y);
+  const uint32_t n = (uint32_t)(nvx * nvy);
+  uint32_t base = 0u;
+  if (m.list[I] && lane == 0 && n) base = atomicAdd(m.counts + I, n);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const size_t cap = (size_t)m.Wi[I] * m.Hi[I];
+  for (int r = 0; r < nvy; ++r)
+    for (int c = lane; c < nvx; c += 32) {
+      const int qx = q0x + c, qy = q0y + r;
+      const size_t q = (size_t)qy * m.Wi[I] + qx;
+      m.alpha[I][q] = 1.0f;
+      m.stencil[I][q] = 1;
+      const size_t pos = (size_t)base + (size_t)r * nvx + c;
+      if (m.list[I] && pos < cap) m.list[I][pos] = ((uint32_t)qy << 16) | (uint32_t)qx;
+    }
+}
+
+template <int I>
+__device__ __forceinline__ void empty_level(const MaskParams& m, int x0, int y0) {
+  if (I >= m.L) return;
+  if (m.mode[I] == 1) {
+    if ((threadIdx.x >> 5) == 3) empty_one_level<I>(m, x0, y0);
+  } else {
+    empty_zero_level<I>(m, x0, y0);
+  }
+}
+
 // Level patterns compiled on their own, so that the kernel holds only the code they run:
 //   MASK_SIG_T1_4: four levels, levels 0-2 blurred with radii 3, 5, 6 (Table 1's SSAO and
 //                  soft-shadow rows, sigma^2 = 0.924, 1.848, 3.696);
@@ -650,6 +708,14 @@ __global__ void __launch_bounds__(MTHREADS, 2048 / MTHREADS) masks_kernel(MaskPa
   if (m.lut0 && m.mode[0] == 0 && (1 << (2 * m.R[0] + 1)) <= MASK_LUT_MAX)
     for (int k = threadIdx.x; k < (1 << (2 * m.R[0] + 1)); k += MTHREADS) sm.lut[k] = __ldg(m.lut0 + k);
   const bool any_edge = __syncthreads_or(seen != 0u) != 0;
+  if (!any_edge && m.a0c && !m.label && !m.disjoint && m.mode[0] != 1) {
+    // frame mode, no edge in reach: level 0 has no pixel (nothing to write on the frame
+    // path), the others are constant over the tile
+    empty_level<1>(m, x0, y0);
+    empty_level<2>(m, x0, y0);
+    empty_level<3>(m, x0, y0);
+    return;
+  }
   // 1. [a_i > 0] of every level as bit rows (one warp per level).  With no edge anywhere in
   // the staged rows every blurred level's window sums are 0 (each D row is made of staged
   // rows only), so [a > 0] is empty there and only the constant levels have bits.
