@@ -313,8 +313,18 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       // the lane's two vertically adjacent pixels (rows r0, r0 + 1 of the tile)
       const int r0 = 2 * warp + 2 * (ETHREADS / 32) * pr, x = x0 + lane, y = y0 + r0;
       const int ly = r0 + 1, cd = lane + DOFF, cn = lane + T::NOFF;
-      const float du = sd[(ly - 1) * DW + cd], d0 = sd[ly * DW + cd], d1 = sd[(ly + 1) * DW + cd],
-                  dd = sd[(ly + 2) * DW + cd];
+      const float d0 = sd[ly * DW + cd], d1 = sd[(ly + 1) * DW + cd];
+      // sky pixels are never edges: with soft shadows, whose tests also read the hard-shadow
+      // bits, a warp whose 64 pixels are all sky stores its two zero words without them (3-6
+      // us per 1440p frame; for the lighter SSAO/SSGI tests the vote costs more than it saves)
+      if constexpr (SSM) {
+        if (__all_sync(0xffffffffu, (d0 >= farp) & (d1 >= farp))) {
+          store_edge(p, E, x, y, x < W && y < H, false);
+          store_edge(p, E, x, y + 1, x < W && y + 1 < H, false);
+          continue;
+        }
+      }
+      const float du = sd[(ly - 1) * DW + cd], dd = sd[(ly + 2) * DW + cd];
       const float dl0 = sd[ly * DW + cd - 1], dr0 = sd[ly * DW + cd + 1];
       const float dl1 = sd[(ly + 1) * DW + cd - 1], dr1 = sd[(ly + 1) * DW + cd + 1];
       const float3 nu = smem_normal(sn, (ly - 1) * T::NW + cn), n0 = smem_normal(sn, ly * T::NW + cn);
