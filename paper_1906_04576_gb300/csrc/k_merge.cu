@@ -378,12 +378,18 @@ __global__ void __launch_bounds__(256) blend0_kernel(Blend0Params p, float* __re
       if (!in[u] || x >= p.W || y >= p.H || !(alpha > 0.0f)) continue;
       const float om = 1.0f - alpha;
       const size_t o = (size_t)y * p.W + x;
+      // alpha = 1: v 1 + c 0 is v itself (c' is finite and the effects' values are
+      // non-negative, never -0), so the image is written without being read
       if (C == 4) {
         float4* q = reinterpret_cast<float4*>(out) + o;
-        const float4 c = *q;
-        *q = make_float4(v[u].x * alpha + c.x * om, v[u].y * alpha + c.y * om, v[u].z * alpha + c.z * om, 0.0f);
+        if (alpha == 1.0f) {
+          *q = make_float4(v[u].x, v[u].y, v[u].z, 0.0f);
+        } else {
+          const float4 c = *q;
+          *q = make_float4(v[u].x * alpha + c.x * om, v[u].y * alpha + c.y * om, v[u].z * alpha + c.z * om, 0.0f);
+        }
       } else {
-        out[o] = v[u].x * alpha + out[o] * om;
+        out[o] = alpha == 1.0f ? v[u].x : v[u].x * alpha + out[o] * om;
       }
     }
   }
