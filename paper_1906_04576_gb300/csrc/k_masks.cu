@@ -7,16 +7,22 @@
 //   a truncated Gaussian is positive, so a_i > 0 exactly where the (2R_i+1)^2 window of the
 //   downsampled edge image D_i (block maximum) holds an edge: the stencil before nesting
 //   is a box dilation, computed on bit rows -- one warp per level (row ORs of shifted
-//   words, then column ORs across lanes).  Warp 0 then ORs in the children of the previous
-//   enabled finer level (inclusive nesting, Fig. 2/3 -- children always lie in the same
-//   tile) and, for a whole frame, reserves each level's list room with one atomicAdd.
+//   words, then column ORs across lanes).  Warp I then ORs into level I the children of
+//   the finer enabled levels (inclusive nesting, Fig. 2/3 -- children always lie in the
+//   same tile) and, for a whole frame, reserves level I's list room with one atomicAdd.
+//   A tile with no edge anywhere in its staged rows (most of a typical frame) has empty
+//   masks at every blurred level: it skips the bit phase, and on the frame path writes its
+//   constant levels directly.
 //   Last, every thread writes its texels: a_i is evaluated only where the dilation is set
 //   -- the horizontal sums over the (2R_i+1)-bit windows (a table of the exact window sums
 //   where one is given; above level 0 each row's sums are computed once, beside its D row,
 //   and shared by the texels of the column), the vertical taps with one fused multiply-add
 //   each in ascending order, the definition's arithmetic exactly -- and is 0 elsewhere.  The
-//   coarsest level is written as a = 1, S = 1; disabled levels as 0.  Staged calls also get
-//   every pixel's owning level (the finest enabled level whose stencil covers it).
+//   coarsest level is written as a = 1, S = 1; disabled levels as 0.  On the frame path
+//   level 0's a_0 feeds only the level-0 blend's min(w_0 a_0, 1), so within the radius r1
+//   of an edge, where that is 1 whatever a_0's exact value (MaskParams::sure0), 1 is
+//   written instead.  Staged calls also get every pixel's owning level (the finest enabled
+//   level whose stencil covers it).
 // compact_count_kernel / compact_scatter_kernel: deterministic stream compaction of
 //   every level's stencil into a row-major list of (y << 16) | x.  Pass 1 counts the set
 //   texels of each 4096-texel chunk; pass 2 gives each chunk its exclusive prefix (a
