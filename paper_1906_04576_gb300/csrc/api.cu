@@ -365,7 +365,7 @@ mrr_status masks_impl(mrr_ctx* ctx, const uint8_t* E, const mrr_levels* lv, cuda
 }
 
 mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream_t s, uint32_t* zero = nullptr,
-                      int zero_words = 0, uint32_t* ebits = nullptr) {
+                      int zero_words = 0, uint32_t* ebits = nullptr, bool concurrent = false) {
   EdgeParams p;
   std::memset(&p, 0, sizeof p);
   p.v = make_view(g->width, g->height, g->cam);
@@ -380,6 +380,7 @@ mrr_status edges_impl(mrr_ctx* ctx, const mrr_gbuffer* g, uint8_t* E, cudaStream
   p.ebits = ebits;
   p.ewords = (g->width + 31) / 32;
   if (p.ssm && ctx->sbits && g->width <= ctx->pool_W && g->height <= ctx->pool_H) p.sbits = ctx->sbits;
+  p.concurrent = concurrent ? 1 : 0;
   const int h = ctx->cfg.precision == MRR_FP16;
   MRR_CUDA(ctx, launch_edges(p, g->depth, g->normal, h, (const float*)g->shadow_map, E, s));
   return MRR_OK;
@@ -653,10 +654,10 @@ mrr_status render_launches_staged(mrr_ctx* ctx, const mrr_gbuffer* g, float* out
 // The frame path's first two launches (at least two levels): edges, bit-packed, also
 // clearing the per-level counts; masks that also write every enabled level's work list
 // and level 0's a_0 list-aligned (into the level-0 alpha pool).
-mrr_status frame_masks(mrr_ctx* ctx, const mrr_gbuffer* g, mrr_levels* lv, cudaStream_t s) {
+mrr_status frame_masks(mrr_ctx* ctx, const mrr_gbuffer* g, mrr_levels* lv, cudaStream_t s, bool batched = false) {
   const mrr_config& c = ctx->cfg;
   const int W = g->width, H = g->height;
-  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS, ctx->ebits);
+  mrr_status st = edges_impl(ctx, g, ctx->edges, s, ctx->counts, MRR_MAX_LEVELS, ctx->ebits, batched);
   if (st != MRR_OK) return st;
   *lv = pool_levels(ctx, W, H);
   MaskParams m = mask_params(ctx, lv);
@@ -1177,7 +1178,7 @@ mrr_status batch_launches(mrr_batch* b, mrr_ctx* const* ctxs, const mrr_gbuffer*
     if (framed[k]) {
       if (!fits_pools(ctx, frames[k].width, frames[k].height))
         return batch_fail(b, MRR_EINVAL, "frame exceeds its context's max size");
-      st = frame_masks(ctx, &frames[k], &lv[k], s);
+      st = frame_masks(ctx, &frames[k], &lv[k], s, true);
     } else {
       st = edges_impl(ctx, &frames[k], ctx->edges, s);
       if (st != MRR_OK) return batch_fail(b, st, ctx->err.c_str());

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(TX* TY) shadow_bits_kernel(EdgeParams p, const
 
 // SSM: the edge tests also compare each pixel's hard shadow with its in-image neighbours'
 // (from p.sbits, written by shadow_bits_kernel).
-template <typename NT, bool SSM>
+template <typename NT, bool SSM, bool SCALAR = false>
 __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_constant__ CUtensorMap tm_n,
                                                              const __grid_constant__ CUtensorMap tm_d, EdgeParams p,
                                                              uint8_t* __restrict__ E) {
@@ -331,24 +331,58 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
       const float3 n1 = smem_normal(sn, (ly + 1) * T::NW + cn), nd = smem_normal(sn, (ly + 2) * T::NW + cn);
       const float3 nl0 = smem_normal(sn, ly * T::NW + cn - 1), nr0 = smem_normal(sn, ly * T::NW + cn + 1);
       const float3 nl1 = smem_normal(sn, (ly + 1) * T::NW + cn - 1), nr1 = smem_normal(sn, (ly + 1) * T::NW + cn + 1);
-      // n_p . n_q in the order x, y, z, one IEEE operation each
-      auto dot = [](float3 a, float3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; };
-      const float hl0 = dot(n0, nl0), hl1 = dot(n1, nl1), hr0 = dot(n0, nr0), hr1 = dot(n1, nr1);
-      const float vu0 = dot(n0, nu), vu1 = dot(n1, n0), vd0 = dot(n0, n1), vd1 = dot(n1, nd);
+      // The neighbour tests, in one of two forms that compute the same bits: scalar FP32
+      // (SCALAR: 32 registers, so 8 CTAs fill every warp slot of the SM -- the faster form
+      // for a frame rendered alone with FP32 normals) or packed FP32x2 (more registers,
+      // fewer CTAs per SM -- faster for soft shadows and FP16 normals, and for batched or
+      // served frames, whose kernels share the SMs with other streams' kernels).
       const float cosT = p.normal_cos, farp2 = farp;
       const bool hasl = x > 0, hasr = x < W - 1;
-      const bool hasu0 = y > 0, hasd1 = y + 1 < H - 1;
-      const float m2d0 = -2.0f * d0, m2d1 = -2.0f * d1;
-      const float lapx0 = (dl0 + dr0) + m2d0, lapx1 = (dl1 + dr1) + m2d1;
-      const float lapy0 = (du + d1) + m2d0, lapy1 = (d0 + dd) + m2d1;
-      const float thr0 = p.depth_rel * d0, thr1 = p.depth_rel * d1;
-      const bool hasd0 = y + 1 < H;
-      bool e0 = (hasl & ((dl0 >= farp2) | (hl0 < cosT))) | (hasr & ((dr0 >= farp2) | (hr0 < cosT))) |
-                (hasu0 & ((du >= farp2) | (vu0 < cosT))) | (hasd0 & ((d1 >= farp2) | (vd0 < cosT))) |
-                (hasl & hasr & (fabsf(lapx0) > thr0)) | (hasu0 & hasd0 & (fabsf(lapy0) > thr0));
-      bool e1 = (hasl & ((dl1 >= farp2) | (hl1 < cosT))) | (hasr & ((dr1 >= farp2) | (hr1 < cosT))) |
-                ((d0 >= farp2) | (vu1 < cosT)) | (hasd1 & ((dd >= farp2) | (vd1 < cosT))) |
-                (hasl & hasr & (fabsf(lapx1) > thr1)) | (hasd1 & (fabsf(lapy1) > thr1));
+      const bool hasu0 = y > 0, hasd0 = y + 1 < H, hasd1 = y + 1 < H - 1;
+      bool e0, e1;
+      if constexpr (SCALAR) {
+        // n_p . n_q in the order x, y, z, one IEEE operation each
+        auto dot = [](float3 a, float3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; };
+        const float hl0 = dot(n0, nl0), hl1 = dot(n1, nl1), hr0 = dot(n0, nr0), hr1 = dot(n1, nr1);
+        const float vu0 = dot(n0, nu), vu1 = dot(n1, n0), vd0 = dot(n0, n1), vd1 = dot(n1, nd);
+        const float m2d0 = -2.0f * d0, m2d1 = -2.0f * d1;
+        const float lapx0 = (dl0 + dr0) + m2d0, lapx1 = (dl1 + dr1) + m2d1;
+        const float lapy0 = (du + d1) + m2d0, lapy1 = (d0 + dd) + m2d1;
+        const float thr0 = p.depth_rel * d0, thr1 = p.depth_rel * d1;
+        e0 = (hasl & ((dl0 >= farp2) | (hl0 < cosT))) | (hasr & ((dr0 >= farp2) | (hr0 < cosT))) |
+                  (hasu0 & ((du >= farp2) | (vu0 < cosT))) | (hasd0 & ((d1 >= farp2) | (vd0 < cosT))) |
+                  (hasl & hasr & (fabsf(lapx0) > thr0)) | (hasu0 & hasd0 & (fabsf(lapy0) > thr0));
+        e1 = (hasl & ((dl1 >= farp2) | (hl1 < cosT))) | (hasr & ((dr1 >= farp2) | (hr1 < cosT))) |
+                  ((d0 >= farp2) | (vu1 < cosT)) | (hasd1 & ((dd >= farp2) | (vd1 < cosT))) |
+                  (hasl & hasr & (fabsf(lapx1) > thr1)) | (hasd1 & (fabsf(lapy1) > thr1));
+      } else {
+        // n_p . n_q for both pixels at once (two independent IEEE products and sums in the
+        // order x, y, z -- the same bits as the scalar expression, products commuting)
+        const float2 N0x = make_float2(n0.x, n1.x), N0y = make_float2(n0.y, n1.y), N0z = make_float2(n0.z, n1.z);
+        auto dot2 = [&](float3 a, float3 b) {
+          const float2 px = __fmul2_rn(N0x, make_float2(a.x, b.x));
+          const float2 py = __fmul2_rn(N0y, make_float2(a.y, b.y));
+          const float2 pz = __fmul2_rn(N0z, make_float2(a.z, b.z));
+          return __fadd2_rn(__fadd2_rn(px, py), pz);
+        };
+        const float2 hl = dot2(nl0, nl1), hr = dot2(nr0, nr1), vu = dot2(nu, n0), vd = dot2(n1, nd);
+        // Laplacians along x for both rows and along y
+        // a - b is a + (-b) exactly; -2 d is exact
+        const float2 m2d = __fmul2_rn(make_float2(-2.0f, -2.0f), make_float2(d0, d1));
+        const float2 lapx = __fadd2_rn(__fadd2_rn(make_float2(dl0, dl1), make_float2(dr0, dr1)), m2d);
+        const float2 lapy = __fadd2_rn(__fadd2_rn(make_float2(du, d0), make_float2(d1, dd)), m2d);
+        const float2 thr = __fmul2_rn(make_float2(p.depth_rel, p.depth_rel), make_float2(d0, d1));
+        // The decisions combine with non-short-circuit & and | (every operand is already in
+        // a register, so nothing is saved by skipping one): branch-free predicate logic.
+        // pixel 0: up neighbour row r0 - 1, down neighbour pixel 1
+        e0 = (hasl & ((dl0 >= farp2) | (hl.x < cosT))) | (hasr & ((dr0 >= farp2) | (hr.x < cosT))) |
+                  (hasu0 & ((du >= farp2) | (vu.x < cosT))) | (hasd0 & ((d1 >= farp2) | (vd.x < cosT))) |
+                  (hasl & hasr & (fabsf(lapx.x) > thr.x)) | (hasu0 & hasd0 & (fabsf(lapy.x) > thr.x));
+        // pixel 1: up neighbour pixel 0, down neighbour row r0 + 2
+        e1 = (hasl & ((dl1 >= farp2) | (hl.y < cosT))) | (hasr & ((dr1 >= farp2) | (hr.y < cosT))) |
+                  ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
+                  (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
+      }
       if constexpr (SSM) {
         // hard-shadow bits of rows y - 1 .. y + 2 (clamped; the has flags drop rows and
         // columns outside the image), the words left and right of the tile's word
@@ -390,16 +424,17 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
   }
 }
 
-template <typename NT, bool SSM>
+template <typename NT, bool SSM, bool SCALAR = false>
 int edges_tma_grid() {
   static int blocks = 0;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(edges_tma_kernel<NT, SSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(edges_tma_kernel<NT, SSM, SCALAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)edges_tma_smem<NT>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_tma_kernel<NT, SSM>, ETHREADS, edges_tma_smem<NT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_tma_kernel<NT, SSM, SCALAR>, ETHREADS,
+                                                  edges_tma_smem<NT>());
     blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   }
   return blocks;
@@ -425,7 +460,7 @@ bool edge_maps(const EdgeParams& p, const float* depth, const void* normal, CUte
 
 // The TMA path: false (nothing launched) when the frame's layout does not allow it.  For
 // soft shadows (SMT: the shadow map's storage) the hard-shadow bits are written first.
-template <typename NT, typename SMT = void>
+template <typename NT, typename SMT = void, bool SCALAR = false>
 bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* normal, const void* smap, uint8_t* E,
                       cudaStream_t s) {
   constexpr bool SSM = !std::is_void<SMT>::value;
@@ -437,8 +472,8 @@ bool launch_edges_tma(const EdgeParams& p, const float* depth, const void* norma
     count_launches(1);
   }
   const int tiles = ((p.v.W + ETW - 1) / ETW) * ((p.v.H + ETH - 1) / ETH);
-  const int grid = min(tiles, edges_tma_grid<NT, SSM>());
-  edges_tma_kernel<NT, SSM><<<grid, ETHREADS, edges_tma_smem<NT>(), s>>>(tn, td, p, E);
+  const int grid = min(tiles, edges_tma_grid<NT, SSM, SCALAR>());
+  edges_tma_kernel<NT, SSM, SCALAR><<<grid, ETHREADS, edges_tma_smem<NT>(), s>>>(tn, td, p, E);
   return true;
 }
 
@@ -465,6 +500,7 @@ cudaError_t launch_check_wait(uint32_t* fault, cudaStream_t s) {
 }
 
 void edges_prepare() {
+  edges_tma_grid<float4, false, true>();
   edges_tma_grid<float4, false>();
   edges_tma_grid<half4, false>();
   edges_tma_grid<float4, true>();
@@ -475,8 +511,9 @@ cudaError_t launch_edges(const EdgeParams& p, const float* depth, const void* no
                          const float* smap, uint8_t* E, cudaStream_t s) {
   dim3 block(TX, TY), grid((p.v.W + TX - 1) / TX, (p.v.H + TY - 1) / TY);
   if (!p.ssm) {
-    const bool tma = half_normal ? launch_edges_tma<half4>(p, depth, normal, nullptr, E, s)
-                                 : launch_edges_tma<float4>(p, depth, normal, nullptr, E, s);
+    const bool tma = half_normal   ? launch_edges_tma<half4>(p, depth, normal, nullptr, E, s)
+                     : p.concurrent ? launch_edges_tma<float4>(p, depth, normal, nullptr, E, s)
+                                    : launch_edges_tma<float4, void, true>(p, depth, normal, nullptr, E, s);
     if (!tma) {
       dim3 dgrid((p.v.W + TX - 1) / TX, (p.v.H + TY * ER - 1) / (TY * ER));
       if (half_normal) edges_direct_kernel<half4><<<dgrid, block, 0, s>>>(p, depth, (const half4*)normal, E);

@@ -78,6 +78,9 @@ struct EdgeParams {
   // Non-null lets a frame whose rows allow TMA take the two-pass path (shadow bits, then
   // the TMA edge kernel); null keeps the one-pass staged kernel.
   uint32_t* sbits;
+  // 1: the frame is one of a batch or a served stream, whose kernels share the SMs with
+  // other streams' kernels (selects the edge kernel's form that does better there)
+  int concurrent;
 };
 
 // Mask stage of all levels in one launch (k_masks.cu).  Level i: mode 0 = blur,
