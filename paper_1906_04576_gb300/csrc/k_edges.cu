@@ -350,11 +350,11 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
         const float lapy0 = (du + d1) + m2d0, lapy1 = (d0 + dd) + m2d1;
         const float thr0 = p.depth_rel * d0, thr1 = p.depth_rel * d1;
         e0 = (hasl & ((dl0 >= farp2) | (hl0 < cosT))) | (hasr & ((dr0 >= farp2) | (hr0 < cosT))) |
-                  (hasu0 & ((du >= farp2) | (vu0 < cosT))) | (hasd0 & ((d1 >= farp2) | (vd0 < cosT))) |
-                  (hasl & hasr & (fabsf(lapx0) > thr0)) | (hasu0 & hasd0 & (fabsf(lapy0) > thr0));
+             (hasu0 & ((du >= farp2) | (vu0 < cosT))) | (hasd0 & ((d1 >= farp2) | (vd0 < cosT))) |
+             (hasl & hasr & (fabsf(lapx0) > thr0)) | (hasu0 & hasd0 & (fabsf(lapy0) > thr0));
         e1 = (hasl & ((dl1 >= farp2) | (hl1 < cosT))) | (hasr & ((dr1 >= farp2) | (hr1 < cosT))) |
-                  ((d0 >= farp2) | (vu1 < cosT)) | (hasd1 & ((dd >= farp2) | (vd1 < cosT))) |
-                  (hasl & hasr & (fabsf(lapx1) > thr1)) | (hasd1 & (fabsf(lapy1) > thr1));
+             ((d0 >= farp2) | (vu1 < cosT)) | (hasd1 & ((dd >= farp2) | (vd1 < cosT))) |
+             (hasl & hasr & (fabsf(lapx1) > thr1)) | (hasd1 & (fabsf(lapy1) > thr1));
       } else {
         // n_p . n_q for both pixels at once (two independent IEEE products and sums in the
         // order x, y, z -- the same bits as the scalar expression, products commuting)
@@ -376,12 +376,12 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
         // a register, so nothing is saved by skipping one): branch-free predicate logic.
         // pixel 0: up neighbour row r0 - 1, down neighbour pixel 1
         e0 = (hasl & ((dl0 >= farp2) | (hl.x < cosT))) | (hasr & ((dr0 >= farp2) | (hr.x < cosT))) |
-                  (hasu0 & ((du >= farp2) | (vu.x < cosT))) | (hasd0 & ((d1 >= farp2) | (vd.x < cosT))) |
-                  (hasl & hasr & (fabsf(lapx.x) > thr.x)) | (hasu0 & hasd0 & (fabsf(lapy.x) > thr.x));
+             (hasu0 & ((du >= farp2) | (vu.x < cosT))) | (hasd0 & ((d1 >= farp2) | (vd.x < cosT))) |
+             (hasl & hasr & (fabsf(lapx.x) > thr.x)) | (hasu0 & hasd0 & (fabsf(lapy.x) > thr.x));
         // pixel 1: up neighbour pixel 0, down neighbour row r0 + 2
         e1 = (hasl & ((dl1 >= farp2) | (hl.y < cosT))) | (hasr & ((dr1 >= farp2) | (hr.y < cosT))) |
-                  ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
-                  (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
+             ((d0 >= farp2) | (vu.y < cosT)) | (hasd1 & ((dd >= farp2) | (vd.y < cosT))) |
+             (hasl & hasr & (fabsf(lapx.y) > thr.y)) | (hasd1 & (fabsf(lapy.y) > thr.y));
       }
       if constexpr (SSM) {
         // hard-shadow bits of rows y - 1 .. y + 2 (clamped; the has flags drop rows and
