@@ -283,14 +283,17 @@ __global__ void __launch_bounds__(ETHREADS) edges_tma_kernel(const __grid_consta
     mbar_fence_init();
   }
   __syncthreads();
-  // thread 0: start the loads of the k-th tile of this CTA into stage k % ESTAGES
+  // thread 0: start the loads of the k-th tile of this CTA into stage k % ESTAGES.  The
+  // normals are read once per frame here, while the shading launch later gathers the depth
+  // again: their lines are marked first to be evicted from L2, so that the depth rather
+  // than the normals is what L2 still holds when the shading launch runs.
   auto issue = [&](int k) {
     const int s = k % ESTAGES;
     const int t = (int)blockIdx.x + k * (int)gridDim.x;
     const int x0 = (t % gx) * ETW, y0 = (t / gx) * ETH;
     unsigned char* st = sbase + s * SB;
     mbar_arrive_expect_tx(&full[s], T::NBYTES + DBYTES);
-    tma_load_2d(st, &tm_n, &full[s], (x0 - T::NOFF) * 4, y0 - 1);
+    tma_load_2d_hint(st, &tm_n, &full[s], (x0 - T::NOFF) * 4, y0 - 1, l2_evict_first_policy());
     tma_load_2d(st + NP, &tm_d, &full[s], x0 - DOFF, y0 - 1);
   };
   if (threadIdx.x == 0)
