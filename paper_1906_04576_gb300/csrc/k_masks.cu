@@ -223,10 +223,13 @@ __device__ __forceinline__ void blur_bits(const MaskParams& m, MaskSmem& sm, int
   if (lane < DN) {
     float* hs = I == 1 ? &sm.H1[0][0] : &sm.H2[0][0];
     const float* lut = m.lut[I];
+    // the table's lookups all requested at once; without a table, the sums one by one
+    if (lut) {
 #pragma unroll
-    for (int c = 0; c < Ti; ++c) {
-      const uint32_t win = (d >> c) & WMASK;
-      hs[c * HP + lane] = lut ? __ldg(lut + win) : window_sum(win, sm.g[I]);
+      for (int c = 0; c < Ti; ++c) hs[c * HP + lane] = __ldg(lut + ((d >> c) & WMASK));
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < Ti; ++c) hs[c * HP + lane] = window_sum((d >> c) & WMASK, sm.g[I]);
     }
   }
   uint32_t h = 0u;
@@ -346,14 +349,18 @@ __device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int
   constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
   const int b = EX - R + c;  // first staged column of the texel's window
   const int k = b >> 5, sh = b & 31;
-  float s = 0.0f;
-#pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) {
+  auto win_at = [&](int t) {
     const uint4 row = sm.E[MG + r - R + t];
     const uint32_t lo = k == 0 ? row.x : row.y, hi = k == 0 ? row.y : row.z;
-    const uint32_t win = __funnelshift_r(lo, hi, sh) & WMASK;
-    const float h = use_lut ? sm.lut[win] : window_sum(win, sm.g[0]);
-    s = fmaf(sm.g[0][t], h, s);
+    return __funnelshift_r(lo, hi, sh) & WMASK;
+  };
+  float s = 0.0f;
+  if (use_lut) {
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[0][t], sm.lut[win_at(t)], s);
+  } else {
+#pragma unroll 1
+    for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[0][t], window_sum(win_at(t), sm.g[0]), s);
   }
   return s;
 }
