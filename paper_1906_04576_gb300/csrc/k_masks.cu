@@ -341,11 +341,12 @@ __device__ __forceinline__ void disjoint_bits(const MaskParams& m, MaskSmem& sm)
 // ---- a_i at one texel, from the same horizontal sums and the same fused multiply-adds
 // in ascending tap order as the definition: h(t) = the ascending sum of the taps over the
 // set bits of the (2R+1)-bit window (a table of the exact window sums where one is given),
-// a = fma(g_2R, h(2R), ... fma(g_0, h(0), 0)).
+// a = fma(g_2R, h(2R), ... fma(g_0, h(0), 0)).  The vertical taps g_t come straight from the
+// kernel's parameters (constant operands once the loop is unrolled), not from shared memory.
 
 // Level 0, tile texel (r, c): windows from the staged edge rows.
 template <int R>
-__device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int r, int c) {
+__device__ __forceinline__ float alpha0_at(const MaskParams& m, const MaskSmem& sm, bool use_lut, int r, int c) {
   constexpr uint32_t WMASK = (1u << (2 * R + 1)) - 1u;
   const int b = EX - R + c;  // first staged column of the texel's window
   const int k = b >> 5, sh = b & 31;
@@ -357,21 +358,21 @@ __device__ __forceinline__ float alpha0_at(const MaskSmem& sm, bool use_lut, int
   float s = 0.0f;
   if (use_lut) {
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[0][t], sm.lut[win_at(t)], s);
+    for (int t = 0; t <= 2 * R; ++t) s = fmaf(m.g[0][t], sm.lut[win_at(t)], s);
   } else {
 #pragma unroll 1
-    for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[0][t], window_sum(win_at(t), sm.g[0]), s);
+    for (int t = 0; t <= 2 * R; ++t) s = fmaf(m.g[0][t], window_sum(win_at(t), sm.g[0]), s);
   }
   return s;
 }
 
 // Level I >= 1, tile texel (r, c): the horizontal sums of rows r .. r + 2R of the D region.
 template <int I, int R>
-__device__ __forceinline__ float alpha_at(const MaskSmem& sm, int r, int c) {
+__device__ __forceinline__ float alpha_at(const MaskParams& m, const MaskSmem& sm, int r, int c) {
   const float* h = I == 1 ? &sm.H1[c][r] : &sm.H2[c][r];
   float s = 0.0f;
 #pragma unroll
-  for (int t = 0; t <= 2 * R; ++t) s = fmaf(sm.g[I][t], h[t], s);
+  for (int t = 0; t <= 2 * R; ++t) s = fmaf(m.g[I][t], h[t], s);
   return s;
 }
 
@@ -410,7 +411,7 @@ __device__ __forceinline__ void write_level0(const MaskParams& m, MaskSmem& sm, 
     __syncwarp();
     for (int k = lane; k < qn; k += 32) {
       const int r = q[k] >> 5, c = q[k] & 31;
-      const float a = alpha0_at<R>(sm, use_lut, r, c);
+      const float a = alpha0_at<R>(m, sm, use_lut, r, c);
       const size_t pos = (size_t)sm.excl[0] + sm.rowpre[0][r] + __popc(sm.S[0][r] & ((1u << c) - 1u));
       if (pos < cap) m.a0c[pos] = a;
     }
@@ -422,7 +423,7 @@ __device__ __forceinline__ void write_level0(const MaskParams& m, MaskSmem& sm, 
     const bool on = (bits >> lane) & 1u;
     if (y >= m.H || x >= m.W || !m.alpha[0]) continue;
     float a = 0.0f;
-    if (on) a = mode == 0 ? alpha0_at<R>(sm, use_lut, r, lane) : 1.0f;
+    if (on) a = mode == 0 ? alpha0_at<R>(m, sm, use_lut, r, lane) : 1.0f;
     m.alpha[0][(size_t)y * m.W + x] = a;
     m.stencil[0][(size_t)y * m.W + x] = on ? 1 : 0;
   }
@@ -445,7 +446,7 @@ __device__ __forceinline__ void write_level(const MaskParams& m, const MaskSmem&
     const bool st = (srow >> c) & 1u;
     float a = 0.0f;
     if (mode == 1) a = 1.0f;
-    else if (mode == 0 && ((sm.B[I][r] >> c) & 1u)) a = alpha_at<I, R>(sm, r, c);
+    else if (mode == 0 && ((sm.B[I][r] >> c) & 1u)) a = alpha_at<I, R>(m, sm, r, c);
     const size_t q = (size_t)qy * Wi + qx;
     m.alpha[I][q] = a;
     m.stencil[I][q] = st ? 1 : 0;
