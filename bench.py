@@ -100,6 +100,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clocks_rejected(clocks):
+    """A timed region whose clock record shows a hardware or thermal slowdown, or SM clocks
+    well below their maximum with no reason reported (a clock lock left behind), is not a
+    valid measurement and is taken again once; sw_power_cap alone is kept and noted."""
+    reasons = set(clocks.get("reasons") or [])
+    if reasons & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    sm, smax = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    return bool(sm and smax and not reasons and sm < 0.9 * smax)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -487,19 +498,25 @@ def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
             dist.barrier()
         return [s_.elapsed_time(e_) for s_, e_ in ev]
 
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    sampler = ClockSampler(vis.split(",")[int(os.environ.get("LOCAL_RANK", "0"))].strip() if vis
-                           else torch.cuda.current_device())
-    sampler.start()
-    time.sleep(0.3)
-    l0 = mrr.mrr_kernel_launches()
-    t_b = timed(step, args.steps)
-    launches = mrr.mrr_kernel_launches() - l0
-    t_f = timed(step_full, args.steps)
-    clocks = sampler.stop()
-
     def max_over_ranks(x):
         return max_reduce(dist, x)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    first_clocks = None
+    for attempt in range(2):
+        sampler = ClockSampler(vis.split(",")[int(os.environ.get("LOCAL_RANK", "0"))].strip() if vis
+                               else torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        l0 = mrr.mrr_kernel_launches()
+        t_b = timed(step, args.steps)
+        launches = mrr.mrr_kernel_launches() - l0
+        t_f = timed(step_full, args.steps)
+        clocks = sampler.stop()
+        # a rejected clock record on any rank: the whole timed region once more
+        if attempt == 1 or max_over_ranks(1.0 if clocks_rejected(clocks) else 0.0) == 0.0:
+            break
+        first_clocks = clocks
 
     # quality gate per effect: the worst scene's RMSE (and the mean) over the 24 scenes
     per_scene = [[], []]
@@ -533,6 +550,7 @@ def run_batch(args, mrr, sg, wl, cfg, rank, world, dist):
                          "p99_ms": round(pct(t_f, 0.99), 5)},
             "speedup_vs_full_res": round(value / fvalue, 4), "rmse_vs_full_res": rmse, "rmse_mean": rmse_mean,
             "gpu_launches": int(launches), "tuning": tune, "clocks": clocks,
+            **({"remeasured": {"first_clocks": first_clocks}} if first_clocks is not None else {}),
         }
         print(json.dumps(line), flush=True)
     mrr.mrr_batch_destroy(b)
@@ -636,33 +654,40 @@ def main():
     torch.cuda.synchronize()
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    sampler = ClockSampler(vis.split(",")[local].strip() if vis else torch.cuda.current_device())
-    sampler.start()
-    time.sleep(0.3)
-    l0 = mrr.mrr_kernel_launches()
-    t_multi = timed(render, args.steps)
-    launches = mrr.mrr_kernel_launches() - l0
-    t_full = timed(render_full, args.steps)
+    first_clocks = None
+    for attempt in range(2):
+        sampler = ClockSampler(vis.split(",")[local].strip() if vis else torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        l0 = mrr.mrr_kernel_launches()
+        t_multi = timed(render, args.steps)
+        launches = mrr.mrr_kernel_launches() - l0
+        t_full = timed(render_full, args.steps)
 
-    # dominant kernel: the frame path's work-list shading launch, timed inside whole frames
-    # of scene 0 (L2 flushed before each, as in the timed loop) with CUDA events that the
-    # library records on the launching stream around that launch (mrr_trace_shading)
-    load_scene(0)
-    edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
-    levels = mrr.alloc_levels(W, H, cfg["num_levels"], with_label=False)
-    mrr.mrr_edges(ctx, dev, edges, stream)
-    mrr.mrr_masks(ctx, edges, levels, stream)
-    tb, te = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mrr.mrr_trace_shading(ctx, tb, te)
-    k_times = []
-    for _ in range(max(10, args.steps // 4)):
-        flush.zero_()
-        mrr.mrr_render(ctx, dev, out, stream)
-        stream.synchronize()
-        k_times.append(tb.elapsed_time(te))
-    mrr.mrr_trace_shading(ctx)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
+        # dominant kernel: the frame path's work-list shading launch, timed inside whole
+        # frames of scene 0 (L2 flushed before each, as in the timed loop) with CUDA events
+        # that the library records on the launching stream around that launch
+        # (mrr_trace_shading)
+        load_scene(0)
+        edges = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        levels = mrr.alloc_levels(W, H, cfg["num_levels"], with_label=False)
+        mrr.mrr_edges(ctx, dev, edges, stream)
+        mrr.mrr_masks(ctx, edges, levels, stream)
+        tb, te = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        mrr.mrr_trace_shading(ctx, tb, te)
+        k_times = []
+        for _ in range(max(10, args.steps // 4)):
+            flush.zero_()
+            mrr.mrr_render(ctx, dev, out, stream)
+            stream.synchronize()
+            k_times.append(tb.elapsed_time(te))
+        mrr.mrr_trace_shading(ctx)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        # a rejected clock record on any rank: the whole timed region once more
+        if attempt == 1 or max_over_ranks(1.0 if clocks_rejected(clocks) else 0.0) == 0.0:
+            break
+        first_clocks = clocks
     k_ms = statistics.mean(k_times)
 
     # e2e: host G-buffer in, host image out, through the public host API: the pipelined
@@ -803,6 +828,7 @@ def main():
             "gpu_launches": int(launches),
             "tuning": tuning,
             "clocks": clocks,
+            **({"remeasured": {"first_clocks": first_clocks}} if first_clocks is not None else {}),
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(sg, wl, args.workload)

@@ -1,6 +1,7 @@
-"""bench.py's roofline bookkeeping on CPU: the algorithmic bytes per shaded texel, the
-committed DRAM-traffic record (used only while the shading sources are unchanged) and the
-HBM peak (the measured file, else the labelled fallback)."""
+"""bench.py's bookkeeping on CPU: the algorithmic bytes per shaded texel, the committed
+DRAM-traffic record (used only while the shading sources are unchanged), the HBM peak (the
+measured file, else the labelled fallback) and the clock-record check that decides whether
+a timed region is taken again."""
 import json
 
 import pytest
@@ -59,3 +60,18 @@ def test_peak_is_measured_file_else_labelled_fallback(monkeypatch, tmp_path):
     assert bench.measured_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6793.1, "bf16_tflops": 1900.0}))
     assert bench.measured_peaks() == (6793.1, "measured")
+
+
+def test_clock_records_rejected_as_the_timing_rules_say():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 8}
+    assert not bench.clocks_rejected(ok)
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    # the power cap alone is kept, even with lower clocks
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1650.0, reasons=["sw_power_cap"]))
+    # clocks stuck well below the maximum with no reason: a leftover clock lock
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1400.0))
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1980.0))
+    # no clock record at all (no nvidia-smi): nothing to reject on
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                                      "samples": 0})
